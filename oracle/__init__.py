@@ -1,0 +1,224 @@
+"""CPU oracle for the factorized quark propagator (test infrastructure only).
+
+Only tests/, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It shares no code with the CUDA path
+(``paper_1612_06424_gb300``) and never imports it.
+
+The arithmetic lives in ``oracle.c`` (plain FP64, natural layout, explicit
+12x12 blocks); this module loads it with ctypes and composes the
+factorization of Sec. 3 from its primitives, one step per term of the
+equations:
+
+  case I   (x, y in Gamma):       fact(y,x) = D_Gamma^{-1}(y,x)                    eq. quark_prop_I
+  case II  (x in Gamma, y in Gamma*):
+           fact(y,x) = -[D_Gamma*^{-1} D_dGamma* D_Gammabar^{-1}](y,x)             eq. quark_prop_II
+  full     D^{-1}(y,x) on the whole lattice;  corr = full - fact                  eq. observable_factorization
+
+and, independently, the exact correction of both cases through the Schur
+complements of eq. block_inverse / schur_complement (``schur_correction``),
+so that fact + corr = full can be checked without reusing ``full``.
+
+Parity status of every function is pinned by tests/test_oracle_*.py.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+BC_OPEN, BC_PERIODIC, BC_ANTIPERIODIC = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so with gcc (plain -O2, no -march)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.run(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"],
+                       check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int)
+        c = ctypes.c_int
+        d = ctypes.c_double
+        _lib.ora_gamma.argtypes = [c, dp]
+        _lib.ora_clover.argtypes = [ip, c, dp, d, d, dp]
+        _lib.ora_dirac.argtypes = [ip, c, dp, dp, c, c, c, dp, dp]
+        _lib.ora_solve.argtypes = [ip, c, dp, dp, c, c, c, dp, dp, d, c, ip, dp]
+        _lib.ora_solve.restype = c
+        _lib.ora_force.argtypes = [ip, c, dp, d, c, c, dp, dp, dp]
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _dims(dims):
+    return (ctypes.c_int * 4)(*[int(v) for v in dims])
+
+
+def gamma(mu: int) -> np.ndarray:
+    """gamma_mu (mu = 0..3, 0 = time) and gamma_5 (mu = 4), chiral basis."""
+    out = np.zeros((4, 4), dtype=np.complex128)
+    lib().ora_gamma(mu, _dp(out))
+    return out
+
+
+class Operator:
+    """The Wilson(-clover) operator D on one gauge field: D = 1/(2 kappa) - D_hop/2 + clover."""
+
+    def __init__(self, dims, U: np.ndarray, kappa: float, csw: float = 0.0, bc: int = BC_OPEN):
+        self.dims = tuple(int(v) for v in dims)
+        self.V = int(np.prod(self.dims))
+        self.bc = int(bc)
+        self.kappa = float(kappa)
+        self.csw = float(csw)
+        self.U = np.ascontiguousarray(U, dtype=np.complex128).reshape(self.V, 4, 3, 3)
+        self.A = np.zeros((self.V, 12, 12), dtype=np.complex128)
+        lib().ora_clover(_dims(self.dims), self.bc, _dp(self.U), self.kappa, self.csw, _dp(self.A))
+
+    @property
+    def T(self) -> int:
+        return self.dims[0]
+
+    def slab(self, t0: int, t1: int) -> np.ndarray:
+        """Boolean site mask of the time slab t0..t1."""
+        s3 = self.V // self.T
+        t = np.arange(self.V) // s3
+        return (t >= t0) & (t <= t1)
+
+    def apply(self, psi: np.ndarray, t0: int = 0, t1: int | None = None, dagger: bool = False) -> np.ndarray:
+        """D_L psi (or D_L^dag psi) for the slab L = t0..t1; psi shape (V,4,3)."""
+        t1 = self.T - 1 if t1 is None else t1
+        inp = np.ascontiguousarray(psi, dtype=np.complex128).reshape(self.V, 4, 3)
+        out = np.empty_like(inp)
+        lib().ora_dirac(_dims(self.dims), self.bc, _dp(self.U), _dp(self.A), int(t0), int(t1),
+                        int(bool(dagger)), _dp(inp), _dp(out))
+        return out
+
+    def solve(self, b: np.ndarray, t0: int = 0, t1: int | None = None, dagger: bool = False,
+              tol: float = 1e-13, maxit: int = 200000):
+        """x = D_L^{-1} b to relative true residual tol; returns (x, iterations, residual)."""
+        t1 = self.T - 1 if t1 is None else t1
+        bb = np.ascontiguousarray(b, dtype=np.complex128).reshape(self.V, 4, 3)
+        x = np.zeros_like(bb)
+        its = ctypes.c_int(0)
+        res = ctypes.c_double(0.0)
+        rc = lib().ora_solve(_dims(self.dims), self.bc, _dp(self.U), _dp(self.A), int(t0), int(t1),
+                             int(bool(dagger)), _dp(bb), _dp(x), float(tol), int(maxit),
+                             ctypes.byref(its), ctypes.byref(res))
+        if rc != 0:
+            raise RuntimeError(f"oracle solve did not converge: residual {res.value:.3e} after {its.value}")
+        return x, its.value, res.value
+
+    def force(self, X: np.ndarray, Y: np.ndarray, t0: int = 0, t1: int | None = None) -> np.ndarray:
+        """F[V,4,8] = -2 Re <Y, dD_L/domega^a_mu(x) X> for U_mu(x) -> exp(i omega T_a) U_mu(x)."""
+        t1 = self.T - 1 if t1 is None else t1
+        F = np.zeros((self.V, 4, 8), dtype=np.float64)
+        Xc = np.ascontiguousarray(X, dtype=np.complex128)
+        Yc = np.ascontiguousarray(Y, dtype=np.complex128)
+        lib().ora_force(_dims(self.dims), self.bc, _dp(self.U), self.csw, int(t0), int(t1),
+                        _dp(Xc), _dp(Yc), _dp(F))
+        return F
+
+    def masked(self, psi: np.ndarray, t0: int, t1: int) -> np.ndarray:
+        out = np.array(psi, dtype=np.complex128, copy=True).reshape(self.V, 4, 3)
+        out[~self.slab(t0, t1)] = 0
+        return out
+
+    def boundary_hop(self, psi: np.ndarray, src: tuple, dst: tuple) -> np.ndarray:
+        """D_dst,src psi = P_dst D P_src psi: the off-diagonal block of eq. block_inverse."""
+        return self.masked(self.apply(self.masked(psi, *src)), *dst)
+
+
+@dataclass
+class Split:
+    """Two-region decomposition of Sec. 2.1 / 3: Gamma, its overlap DeltaGamma (subset of
+    Gamma*, may be None) and Gamma*, each an inclusive time slab.  Gammabar = Gamma u DeltaGamma."""
+
+    gamma: tuple
+    gamma_star: tuple
+    delta: tuple | None = None
+
+    @property
+    def gamma_bar(self) -> tuple:
+        return (self.gamma[0], self.delta[1] if self.delta else self.gamma[1])
+
+
+def factorized_propagator(op: Operator, split: Split, eta: np.ndarray, tol: float = 1e-13):
+    """fact[col] for the sources eta[col] (supported in Gamma), following Sec. 3:
+    D_Gamma^{-1} eta on Gamma (eq. quark_prop_I, first term) and
+    -D_Gamma*^{-1} D_dGamma* (D_Gammabar^{-1} eta)|_Gamma on Gamma* (eq. quark_prop_II)."""
+    g, gs, gb = split.gamma, split.gamma_star, split.gamma_bar
+    fact = np.zeros_like(eta)
+    for c in range(eta.shape[0]):
+        psi_g, _, _ = op.solve(eta[c], *g, tol=tol)
+        psi_gb, _, _ = op.solve(eta[c], *gb, tol=tol)
+        chi = op.boundary_hop(psi_gb, g, gs)
+        zeta, _, _ = op.solve(chi, *gs, tol=tol)
+        m_g = op.slab(*g)
+        m_gs = op.slab(*gs)
+        fact[c][m_g] = psi_g[m_g]
+        fact[c][m_gs] = -zeta[m_gs]
+    return fact
+
+
+def full_propagator(op: Operator, eta: np.ndarray, tol: float = 1e-13):
+    """D^{-1} eta[col] on the whole lattice (the correction solve of Sec. 3.2)."""
+    return np.stack([op.solve(eta[c], tol=tol)[0] for c in range(eta.shape[0])])
+
+
+def schur_correction(op: Operator, split: Split, eta: np.ndarray, tol: float = 1e-13):
+    """corr computed from the exact block inverse, eqs. block_inverse / schur_complement:
+    y in Gamma:  D_Gamma^{-1} D_dGamma [S_Gamma*^{-1} (D_dGamma* D_Gamma^{-1} eta)]
+                 with S_Gamma*^{-1} = (D^{-1})_{Gamma* Gamma*}          (eq. quark_prop_I)
+    y in Gamma*: D_Gamma*^{-1} D_dGamma* [(D_Gammabar^{-1} eta) - (D^{-1} eta)]|_Gamma
+                 with S_Gamma^{-1} eta = (D^{-1} eta)|_Gamma               (eq. quark_prop_II)."""
+    g, gs, gb = split.gamma, split.gamma_star, split.gamma_bar
+    corr = np.zeros_like(eta)
+    m_g, m_gs = op.slab(*g), op.slab(*gs)
+    for c in range(eta.shape[0]):
+        psi_g, _, _ = op.solve(eta[c], *g, tol=tol)
+        w = op.boundary_hop(psi_g, g, gs)                    # D_dGamma* D_Gamma^{-1} eta
+        w_full, _, _ = op.solve(w, tol=tol)                  # D^{-1} w
+        w_gs = op.masked(w_full, *gs)                        # S_Gamma*^{-1} w  (w lives on Gamma*)
+        u = op.boundary_hop(w_gs, gs, g)                     # D_dGamma (...)
+        corr_g, _, _ = op.solve(u, *g, tol=tol)
+        psi_gb, _, _ = op.solve(eta[c], *gb, tol=tol)
+        full_c, _, _ = op.solve(eta[c], tol=tol)
+        diff = op.masked(psi_gb - full_c, *g)
+        v = op.boundary_hop(diff, g, gs)
+        corr_gs, _, _ = op.solve(v, *gs, tol=tol)
+        corr[c][m_g] = corr_g[m_g]
+        corr[c][m_gs] = corr_gs[m_gs]
+    return corr
+
+
+def link_force(op: Operator, phi: np.ndarray, t0: int, t1: int, tol: float = 1e-13):
+    """Force of S = phi^dag (D_L^dag D_L)^{-1} phi on every link, with
+    Y = D_L^{-dag} phi and X = D_L^{-1} Y, so X = (D_L^dag D_L)^{-1} phi and D_L X = Y.
+    Returns (F[V,4,8], S, X, Y)."""
+    phi_m = op.masked(phi, t0, t1)
+    Y, _, _ = op.solve(phi_m, t0, t1, dagger=True, tol=tol)
+    X, _, _ = op.solve(Y, t0, t1, dagger=False, tol=tol)
+    S = float(np.real(np.vdot(phi_m, X)))
+    return op.force(X, Y, t0, t1), S, X, Y
