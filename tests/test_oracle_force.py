@@ -52,9 +52,9 @@ def test_force_matches_finite_differences(csw, bc, slab):
         a = int(rng.integers(8))
         fd = _fd(op_args, U, phi, slab, site, mu, a, 1e-5)
         assert abs(F[site, mu, a] - fd) <= 1e-6 * abs(fd) + 1e-10, (site, mu, a, F[site, mu, a], fd)
-        assert abs(fd) > 1e-4
-        checked += 1
-    assert checked == len(t_pick)
+        checked += abs(fd) > 1e-4
+    # some picks may be links D_L does not depend on (e.g. the absent open-BC link)
+    assert checked >= 3
     if csw:
         # the clover term reaches links outside the slab
         outside = op.slab(*slab) == False  # noqa: E712
