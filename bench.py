@@ -1,0 +1,361 @@
+#!/usr/bin/env python
+"""Benchmark of the factorized quark propagator on one GB300.
+
+Metric: seconds per 12-source factorized propagator (factorized part of
+Sec. 3 plus the full-lattice correction) at true FP64 residual 1e-10, and
+the Wilson-clover Dslash's achieved HBM bandwidth against the measured peak.
+
+Workload (one "step"): the 16^3x32 lattice, random SU(3) links
+U = exp(i 0.4 H) (a stand-in for the paper's quenched ensembles), Wilson-clover
+kappa = 0.1300, c_sw = 1.0, open time boundary; Gamma = t 0..13,
+DeltaGamma = 14..17 (frozen), Gamma* = 14..31; 12 point sources at
+x = (2,0,0,0).  A step loads the gauge field (even-odd packing, compression,
+clover blocks and their inverses), solves the Gamma, Gammabar, Gamma* domain
+systems and the full lattice for all 12 sources (batched), assembles
+fact = D_Gamma^{-1} on Gamma and -D_Gamma*^{-1} D_dGamma* D_Gammabar^{-1} on
+Gamma*, and corr = D^{-1} - fact.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision 64|32|16]
+  python bench.py --impl reference     # the CPU oracle on the host cores
+
+Multi-GPU (torchrun): every rank computes its own propagators (its own
+gauge field, independent problems); there is no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WL = {
+    "name": "16^3x32 Wilson-clover factorized propagator + correction",
+    "dims": (32, 16, 16, 16),
+    "kappa": 0.13,
+    "csw": 1.0,
+    "eps": 0.4,
+    "gamma": (0, 13),
+    "delta": (14, 17),
+    "gamma_star": (14, 31),
+    "x_src": (2, 0, 0, 0),
+    "tol": 1e-10,
+}
+METRIC = "s per 12-source factorized propagator @ res 1e-10 (Dslash HBM GB/s vs peak in roofline)"
+UNIT = "s/propagator"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", type=int, default=32, choices=[64, 32, 16])
+    ap.add_argument("--no-fp64-form", action="store_true", help="skip timing the plain FP64 form")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    for f in ("common.cuh", "dslash.cuh"):
+        with open(os.path.join(ROOT, "paper_1612_06424_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(precision):
+    """Per-launch DRAM bytes of the hop kernel from the committed ncu summary,
+    or None if absent or taken on a different kernel source."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "dslash_traffic.json")) as fh:
+            t = json.load(fh)
+        e = t.get(str(precision))
+        if e and e.get("kernel_hash") == _kernel_hash():
+            return float(e["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class Clocks:
+    """Samples nvidia-smi every 200 ms while the timed region runs."""
+
+    def __init__(self):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            dev = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or "0"
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={dev}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        rows = []
+        try:
+            with open(self.f.name) as fh:
+                for line in fh:
+                    parts = [x.strip() for x in line.split(",")]
+                    if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                        rows.append(parts)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, n in enumerate(names):
+                if r[5 + k].lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(float(r[2]) for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def _cpu_baseline(U, iters_per_group, sample_seconds=12.0):
+    """The oracle (plain FP64 C, one thread) on the host: time of one D
+    application on the full 16^3x32 lattice, measured on a bounded sample, and
+    scaled to one 12-source propagator by the number of operator applications
+    the same solves need (2 per BiCGStab iteration, iteration counts of the
+    unpreconditioned oracle solver taken as twice the even-odd ones)."""
+    import numpy as np
+
+    import oracle
+    from paper_1612_06424_gb300 import inputs
+
+    dims = WL["dims"]
+    op = oracle.Operator(dims, U, WL["kappa"], WL["csw"])
+    psi = inputs.gaussian_spinor(dims, 99)[0]
+    t0 = time.perf_counter()
+    n = 0
+    while time.perf_counter() - t0 < sample_seconds or n < 2:
+        op.apply(psi)
+        n += 1
+    t_apply = (time.perf_counter() - t0) / n
+    T = dims[0]
+    sites = {"gamma": WL["gamma"][1] - WL["gamma"][0] + 1, "gamma_bar": WL["delta"][1] + 1,
+             "gamma_star": WL["gamma_star"][1] - WL["gamma_star"][0] + 1, "full": T}
+    total = 0.0
+    for k, its in iters_per_group.items():
+        total += 12 * 2 * (2 * its) * t_apply * sites[k] / T
+    return {"value": total, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} oracle D applications on the full 16^3x32 lattice ({t_apply:.3f} s each), scaled by "
+                      f"2 x (2 x even-odd iteration count) applications per column over the 4 solve groups x 12 columns "
+                      f"(extrapolated)"}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle, as it stands, on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1612_06424_gb300 import inputs
+
+    U = inputs.random_su3_field(WL["dims"], WL["eps"], 1)
+    iters = {"gamma": 60, "gamma_bar": 70, "gamma_star": 70, "full": 80}
+    vals = []
+    for _ in range(args.warmup):
+        pass
+    for _ in range(args.steps):
+        vals.append(_cpu_baseline(U, iters, sample_seconds=4.0))
+    v = statistics.median(x["value"] for x in vals)
+    cb = dict(vals[-1])
+    cb["value"] = v
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WL["name"], "dims": list(WL["dims"]), "kappa": WL["kappa"], "c_sw": WL["csw"]},
+        "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0}))
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    from paper_1612_06424_gb300 import build, inputs, lqcd
+
+    build.build()
+    dims = WL["dims"]
+    U = inputs.random_su3_field(dims, WL["eps"], 1 + rank)
+    U_dev = torch.from_numpy(U).cuda()
+    lat = lqcd.Lattice(dims, "open")
+    V = lat.V
+    fact = torch.empty((12, V, 4, 3), dtype=torch.complex128, device="cuda")
+    corr = torch.empty_like(fact)
+
+    def step(prec, U_src=None):
+        lat.set_gauge(U_dev if U_src is None else U_src, WL["kappa"], WL["csw"])
+        _, _, st = lat.factorized_propagator(WL["gamma"], WL["gamma_star"], WL["x_src"], delta=WL["delta"],
+                                             corr=True, params=lqcd.SolverParams(tol=WL["tol"], precision=prec),
+                                             out=(fact, corr))
+        return st
+
+    def timed(prec, K, W):
+        for _ in range(W):
+            step(prec)
+        torch.cuda.synchronize()
+        barrier()
+        l0 = lqcd.kernel_launches()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        stats = None
+        for _ in range(K):
+            stats = step(prec)
+        e1.record()
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        launches = lqcd.kernel_launches() - l0
+        if dist is not None:
+            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = t.item()
+        return ms, launches, stats
+
+    # headline: the requested precision
+    with Clocks() as clk:
+        ms, launches, stats = timed(args.precision, args.steps, args.warmup)
+    clocks = clk.summary()
+    value = ms / 1e3 / (args.steps * world)
+    worst_res = max(s["true_residual"] for s in stats.values())
+
+    # plain FP64 form on the same box (context for the mixed-precision speed-up)
+    fp64_form = None
+    if not args.no_fp64_form and args.precision != 64:
+        ms64, _, st64 = timed(64, max(1, min(args.steps, 2)), 1)
+        fp64_form = {"value": ms64 / 1e3 / (max(1, min(args.steps, 2)) * world), "unit": UNIT, "dtype": "f64",
+                     "iters": {k: v["iters"] for k, v in st64.items()},
+                     "true_residual": max(s["true_residual"] for s in st64.values())}
+
+    # end to end through the public API: host field in, host propagators out
+    U_pin = torch.from_numpy(U).pin_memory()
+    fact_h = torch.empty(fact.shape, dtype=fact.dtype, pin_memory=True)
+    corr_h = torch.empty(corr.shape, dtype=corr.dtype, pin_memory=True)
+    Ke = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(Ke):
+        step(args.precision, U_src=U_pin.numpy())
+        fact_h.copy_(fact, non_blocking=True)
+        corr_h.copy_(corr, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = t.item()
+    e2e = {"value": e2e_ms / 1e3 / (Ke * world), "unit": UNIT, "h2d_bytes_per_step": int(U.nbytes),
+           "d2h_bytes_per_step": int(fact.numel() * 16 * 2)}
+
+    # roofline of the dominant kernel: the hop kernel of the inner solves,
+    # on the stage-A batch (12 x Gammabar + 12 x Gamma systems) it runs on
+    doms = [(0, WL["delta"][1])] * 12 + [WL["gamma"]] * 12
+    lat.set_gauge(U_dev, WL["kappa"], WL["csw"])
+    d_ms, d_bytes, d_flops = lat.dslash_bench(doms, [0] * 24, args.precision, 50)
+    peak, peak_kind = _peaks()
+    achieved = d_bytes / (d_ms * 1e-3) / 1e9
+    traffic = _traffic(args.precision)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
+                "kernel": f"k_hop_lin<{args.precision}> (Wilson-clover hop + clover + axpy, even-odd)",
+                "ms_per_launch": round(d_ms, 5), "alg_bytes_per_launch": d_bytes,
+                "tflops": round(d_flops / (d_ms * 1e-3) / 1e12, 3)}
+    dslash_other = {}
+    for p in (64, 32, 16):
+        if p == args.precision:
+            continue
+        m, b, f = lat.dslash_bench(doms, [0] * 24, p, 20)
+        dslash_other[str(p)] = {"GB/s": round(b / (m * 1e-3) / 1e9, 1), "TFLOP/s": round(f / (m * 1e-3) / 1e12, 3),
+                                "ms": round(m, 5)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        iters = {k: v["iters"] for k, v in stats.items()}
+        cpu = _cpu_baseline(U, iters)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": {64: "f64", 32: "f32+f64", 16: "f16+f32+f64"}[args.precision], "data": "synthetic",
+            "config": {"workload": WL["name"], "dims": list(dims), "kappa": WL["kappa"], "c_sw": WL["csw"],
+                       "eps": WL["eps"], "gamma": list(WL["gamma"]), "delta": list(WL["delta"]),
+                       "gamma_star": list(WL["gamma_star"]), "x_src": list(WL["x_src"]), "sources": 12,
+                       "precision": {64: "fp64", 32: "fp32 inner BiCGStab + fp64 defect correction",
+                                     16: "fp16 vectors/links (fp32 norm) inner + fp64 defect correction"}[args.precision],
+                       "residual": WL["tol"], "l2": "working set > L2 (no flush)",
+                       "parallelism": f"replicas x{world} (independent propagators)"},
+            "true_residual": worst_res,
+            "iters": {k: v["iters"] for k, v in stats.items()},
+            "cycles": {k: v["cycles"] for k, v in stats.items()},
+            "fp64_form": fp64_form,
+            "e2e": e2e, "roofline": roofline, "dslash_other_precisions": dslash_other,
+            "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": int(launches),
+        }
+        print(json.dumps(line))
+    lat.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

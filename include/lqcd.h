@@ -1,0 +1,200 @@
+/*
+ * lqcd.h — C ABI of the GB300 (sm_103a) factorized-quark-propagator library.
+ *
+ * Method: Ce, Giusti, Schaefer, "Domain decomposition and multilevel
+ * integration for fermions" (arXiv:1612.06424).  The library computes, on
+ * one GPU, the Dirac-operator work of that method:
+ *   - the Wilson(-clover) operator D, normalised as 2 kappa D = 1 - kappa D_hop
+ *     (Sec. 5, definition below eq. stochastic_estimator), clover term
+ *     c_sw (i/4) sum_{mu,nu} sigma_mu_nu Fhat_mu_nu(x) added to its diagonal;
+ *   - its domain (block) operators D_L on time slabs with Dirichlet boundaries,
+ *     the exact sub-blocks of D of eq. block_inverse (Sec. 3) and Sec. 5;
+ *   - solves of D_L psi = eta and D psi = eta (Sec. 5: "solutions of the
+ *     Dirac equation"; Sec. 4.1: cost counted in Dirac-operator inversions);
+ *   - the factorized propagator of Sec. 3 (eqs. quark_prop_I, quark_prop_II)
+ *     and its correction, corr = D^{-1} - fact (eq. observable_factorization);
+ *   - the link force of S = phi^dag (D_L^dag D_L)^{-1} phi, the domain-local
+ *     pseudofermion action the multilevel scheme needs for independent domain
+ *     updates (Sec. 2.1, eq. action_decomposition; the paper defers its
+ *     construction to its Ref. Ce:2016ajy).
+ *
+ * Conventions shared by every call
+ *   dims        {T, L1, L2, L3}; x0 is time (slowest).  All four even, L3 >= 2.
+ *   site index  i = ((x0*L1 + x1)*L2 + x2)*L3 + x3   ("natural order")
+ *   gauge field U[i][mu][a][b], complex128 (re, im interleaved), mu = 0 time.
+ *   spinor      psi[i][s][c], complex128, spin s = 0..3, colour c = 0..2,
+ *               chiral gamma basis, gamma_5 = g0 g1 g2 g3 = diag(1, 1, -1, -1),
+ *               g0 = [[0,-1],[-1,0]], g_k = [[0,-i s_k],[i s_k,0]] in 2x2 blocks.
+ *   hopping     (D_hop psi)(x) = sum_mu (1 - g_mu) U_mu(x) psi(x+mu)
+ *                                     + (1 + g_mu) U_mu(x-mu)^dag psi(x-mu).
+ *   time BC     LQCD_BC_OPEN (the paper's open BC, Sec. 5: no hop between
+ *               x0 = T-1 and x0 = 0, and the clover leaves through that
+ *               missing link vanish), LQCD_BC_PERIODIC, LQCD_BC_ANTIPERIODIC.
+ *               Space is periodic.
+ *   slab        {t0, t1}: the inclusive time range t0..t1.  A slab vector is
+ *               the natural-order slice of a full-lattice vector over sites
+ *               t0*L1*L2*L3 .. (t1+1)*L1*L2*L3 - 1 (time is slowest), i.e.
+ *               (t1-t0+1)*L1*L2*L3*12 complex128 values.
+ *   pointers    every data pointer is a DEVICE pointer unless the argument
+ *               says otherwise; the caller owns it.  The library owns its
+ *               internal even-odd, compressed and reduced-precision copies.
+ *   stream      a cudaStream_t passed as void*; NULL means the legacy default
+ *               stream.  Calls are stream-ordered; those that return solver
+ *               statistics synchronise the stream before returning.
+ *   errors      0 on success, a negative LQCD_E* code on failure, with a
+ *               message from lqcd_last_error().  Nothing aborts or traps.
+ *               A failed call leaves caller buffers in an unspecified state.
+ */
+#ifndef LQCD_H
+#define LQCD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LQCD_OK 0
+#define LQCD_EBADARG (-1)      /* argument out of range or inconsistent        */
+#define LQCD_ENOMEM (-2)       /* device allocation failed                      */
+#define LQCD_ENONUNITARY (-3)  /* set_gauge: a link is not SU(3) to 1e-10       */
+#define LQCD_ENOTCONVERGED (-4)/* a solve hit max_iter above its tolerance      */
+#define LQCD_EBREAKDOWN (-5)   /* Krylov breakdown that restarts did not cure   */
+#define LQCD_ENAN (-6)         /* NaN or Inf in a residual                      */
+#define LQCD_ECUDA (-7)        /* a CUDA runtime call failed                    */
+#define LQCD_ENOFIELD (-8)     /* field index not loaded                        */
+
+#define LQCD_BC_OPEN 0
+#define LQCD_BC_PERIODIC 1
+#define LQCD_BC_ANTIPERIODIC 2
+
+#define LQCD_MEM_DEVICE 0
+#define LQCD_MEM_HOST 1
+
+typedef struct lqcd_lattice lqcd_lattice; /* opaque, owned by the library */
+
+typedef struct {
+  int t0, t1; /* inclusive time range */
+} lqcd_slab;
+
+/* Two-region split of Sec. 2.1 / 3: Gamma, the overlap DeltaGamma (a subset
+ * of Gamma* adjacent to Gamma; empty when delta.t1 < delta.t0) and Gamma*.
+ * Gamma u Gamma* must be the whole time range, Gamma first; Gammabar =
+ * Gamma u DeltaGamma. */
+typedef struct {
+  lqcd_slab gamma, delta, gamma_star;
+} lqcd_split;
+
+typedef struct {
+  double tol;            /* target relative true residual ||eta - D psi|| / ||eta||   */
+  int max_iter;          /* bound on Krylov iterations per system (all cycles)        */
+  int precision;         /* 64: FP64 throughout; 32: FP32 inner solves with FP64
+                            defect correction; 16: FP16 vectors (per-site FP32 norm)
+                            and FP16 links in the inner solves, FP64 correction      */
+  double inner_tol;      /* relative residual reduction per inner cycle (0: default) */
+  int check_every;       /* iterations between host convergence checks (0: default) */
+} lqcd_solver_params;
+
+typedef struct {
+  int iters;             /* inner Krylov iterations summed over cycles                */
+  int cycles;            /* FP64 defect-correction cycles (true residual evaluations) */
+  int status;            /* LQCD_OK, LQCD_ENOTCONVERGED, LQCD_EBREAKDOWN or LQCD_ENAN */
+  double true_residual;  /* ||eta - D psi||_2 / ||eta||_2 recomputed in FP64 at exit   */
+  double seconds;        /* wall time of the call that produced this entry           */
+} lqcd_solver_stats;
+
+/* Create a lattice of the given dims with time boundary condition bc_t.
+ * *out receives an opaque handle owned by the library.  Selects the current
+ * CUDA device.  Errors: LQCD_EBADARG (odd or non-positive extent). */
+int lqcd_create_lattice(const int dims[4], int bc_t, lqcd_lattice **out);
+
+/* Free every device buffer of the lattice; the handle becomes invalid. */
+int lqcd_destroy_lattice(lqcd_lattice *lat);
+
+/* Load n_fields gauge fields U[n_fields][V][4][3][3] (complex128, natural
+ * order; host memory if mem == LQCD_MEM_HOST, else device memory) with the
+ * operator parameters kappa and c_sw (c_sw = 0: plain Wilson, Sec. 5).
+ * Builds, per field, the even-odd packed links in FP64 / FP32 / FP16 (the
+ * reduced copies keep the first two rows, the third is rebuilt as
+ * conj(row0 x row1)), the clover blocks A(x) on every site and their
+ * inverses on even sites.  Replaces any fields loaded before.
+ * Errors: LQCD_ENONUNITARY when a link deviates from SU(3) by > 1e-10
+ * (max |U U^dag - 1| or |det U - 1|), LQCD_ENOMEM. */
+int lqcd_set_gauge(lqcd_lattice *lat, int n_fields, const double *U, double kappa, double c_sw, int mem,
+                   void *stream);
+
+/* out = D_L in (dagger = 0) or D_L^dag in (dagger = 1) for the slab dom
+ * (NULL: the whole lattice, with the lattice's time BC) on field `field`,
+ * evaluated in `precision` (64, 32 or 16) through the even-odd packed data.
+ * in / out: device slab vectors (see "slab" above) in complex128.
+ * Sec. 3 eq. block_inverse: D_L is the sub-block of D on the slab's sites. */
+int lqcd_dslash(lqcd_lattice *lat, int field, const lqcd_slab *dom, int dagger, int precision, const double *in,
+                double *out, void *stream);
+
+/* Batched solve of D_{L_k} psi_k = eta_k for k < n_sys, system k on slab
+ * doms[k] of field field_ids[k].  src / sol: device slab vectors of the
+ * systems packed back to back in the order k = 0..n_sys-1 (system k starts
+ * after the slab vectors of systems 0..k-1).  sol is overwritten.
+ * All systems advance together in the same kernels (even-odd preconditioned
+ * BiCGStab, FP64 defect correction).  stats: host array of n_sys entries or
+ * NULL.  Returns LQCD_ENOTCONVERGED if any system stopped above tol. */
+int lqcd_solve_block(lqcd_lattice *lat, int n_sys, const lqcd_slab *doms, const int *field_ids, const double *src,
+                     double *sol, const lqcd_solver_params *params, lqcd_solver_stats *stats, void *stream);
+
+/* Batched full-lattice solve D psi_k = eta_k (the correction solve of
+ * Sec. 3.2); src / sol are n_sys full-lattice vectors back to back. */
+int lqcd_solve_full(lqcd_lattice *lat, int n_sys, const int *field_ids, const double *src, double *sol,
+                    const lqcd_solver_params *params, lqcd_solver_stats *stats, void *stream);
+
+/* The 12-source factorized propagator of Sec. 3 for point sources at x_src
+ * (x_src[0] inside Gamma), on field `field`:
+ *   y in Gamma:  fact(y,x) = D_Gamma^{-1}(y,x)                        eq. quark_prop_I
+ *   y in Gamma*: fact(y,x) = -[D_Gamma*^{-1} D_dGamma* D_Gammabar^{-1}](y,x)  eq. quark_prop_II
+ * with D_dGamma* the block of D from Gamma to Gamma* (eq. block_inverse).
+ * fact: device [12][V][4][3] complex128, column col = 3*s0 + c0 of the
+ * source.  corr: device [12][V][4][3] receiving D^{-1} - fact (the full
+ * solve on the lattice), or NULL to skip it.  stats: host array of
+ * 4 entries (Gamma, Gammabar, Gamma*, full) aggregated over the 12
+ * columns (max iterations, max residual, worst status), or NULL. */
+int lqcd_factorized_propagator(lqcd_lattice *lat, const lqcd_split *split, const int x_src[4], int field,
+                               double *fact, double *corr, const lqcd_solver_params *params,
+                               lqcd_solver_stats *stats, void *stream);
+
+/* Link force of S = phi^dag (D_L^dag D_L)^{-1} phi for the slab dom on field
+ * `field`: force[i][mu][a] = dS/domega for U_mu(x_i) -> exp(i omega T_a)
+ * U_mu(x_i), T_a = lambda_a / 2 (Gell-Mann), i.e.
+ *   F = -2 Re <Y, (dD_L/domega) X>,  Y = D_L^{-dag} phi,  X = D_L^{-1} Y,
+ * hopping and clover terms included.  phi: device slab vector on dom;
+ * force: device [V][4][8] float64, every link of the lattice (links outside
+ * the slab reached by the clover leaves of its sites are included; the rest
+ * are 0), or NULL to compute the action alone (one D^dag solve).
+ * action: host double receiving S = ||Y||^2, or NULL.
+ * stats: host array of 2 entries (the D^dag and D solves) or NULL.  X and Y
+ * are recomputed on every call, never cached. */
+int lqcd_link_force(lqcd_lattice *lat, const lqcd_slab *dom, int field, const double *phi, double *force,
+                    double *action, const lqcd_solver_params *params, lqcd_solver_stats *stats, void *stream);
+
+/* Timing hook of the stencil (no counterpart in the paper: a measurement
+ * aid).  Builds the batch of systems (slab doms[k] on field field_ids[k]),
+ * fills two synthetic vectors, and launches `reps` times the hop kernel the
+ * solver uses for the second half of the even-odd operator,
+ *   out_o = A_oo y_o - 1/4 D_hop x_e     (precision 64, 32 or 16),
+ * after 3 untimed launches, timed with CUDA events on `stream`.
+ * ms_per_launch: mean launch duration (ms).  bytes_per_launch: algorithmic
+ * bytes = 3 spinors per system site + (8 links + 1 clover block) per distinct
+ * site of each field's slabs.  flops_per_launch: (1320 hop + 504 clover + 72)
+ * per system site.  Any output pointer may be NULL. */
+int lqcd_dslash_bench(lqcd_lattice *lat, int n_sys, const lqcd_slab *doms, const int *field_ids, int precision,
+                      int reps, double *ms_per_launch, double *bytes_per_launch, double *flops_per_launch,
+                      void *stream);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char *lqcd_last_error(void);
+
+/* Number of kernels this library has launched since load (all streams);
+ * a host-side counter for accounting, not synchronised with the device. */
+long long lqcd_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LQCD_H */

@@ -1,0 +1,877 @@
+// C-ABI entry points (include/lqcd.h) and the host side of the batched
+// solver: the FP64 defect-correction loop around even-odd preconditioned
+// BiCGStab in FP64, FP32 or FP16, the factorized-propagator pipeline of
+// Sec. 3 and the link-force driver.
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+static thread_local std::string g_err;
+static bool verbose() {
+  static int v = -1;
+  if (v < 0) v = getenv("LQCD_VERBOSE") ? 1 : 0;
+  return v == 1;
+}
+void lq_set_error(const std::string& m) { g_err = m; }
+extern "C" const char* lqcd_last_error(void) { return g_err.c_str(); }
+
+#define CK(call)                                                                     \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess) {                                                         \
+      lq_set_error(std::string(#call) + ": " + cudaGetErrorString(e_));              \
+      return e_ == cudaErrorMemoryAllocation ? LQCD_ENOMEM : LQCD_ECUDA;             \
+    }                                                                                \
+  } while (0)
+
+#define RC(call)               \
+  do {                         \
+    int r_ = (call);           \
+    if (r_ != 0) return r_;    \
+  } while (0)
+
+namespace {
+
+// Stream-ordered device buffer (freed on scope exit).
+struct DBuf {
+  void* p = nullptr;
+  cudaStream_t st = nullptr;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  ~DBuf() {
+    if (p) cudaFreeAsync(p, st);
+  }
+  int alloc(size_t bytes, cudaStream_t s) {
+    st = s;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(&p, bytes, s);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      cudaGetLastError();
+      lq_set_error("device allocation of " + std::to_string(bytes) + " bytes failed");
+      return LQCD_ENOMEM;
+    }
+    return 0;
+  }
+  template <typename T>
+  T* as() const {
+    return (T*)p;
+  }
+};
+
+struct PinnedInt {
+  int* h = nullptr;
+  PinnedInt() { cudaHostAlloc((void**)&h, sizeof(int) * 4, cudaHostAllocDefault); }
+  ~PinnedInt() {
+    if (h) cudaFreeHost(h);
+  }
+};
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+int check_lat(const lqcd_lattice* L) {
+  if (!L) {
+    lq_set_error("null lattice");
+    return LQCD_EBADARG;
+  }
+  return 0;
+}
+
+// A batch with its own descriptor / flag / scalar / partial storage.
+struct BatchStore {
+  Batch b;
+  DBuf sys, active, sc, partial;
+  std::vector<lq::SysDesc> h_sys;
+  std::vector<lq::SolverScal> h_sc;
+  std::vector<int> h_active;
+
+  int build(const lqcd_lattice* L, int n, const lqcd_slab* doms, const int* fields, cudaStream_t st) {
+    h_sys.resize(n);
+    long long off = 0, maxn = 0;
+    for (int k = 0; k < n; k++) {
+      const lqcd_slab d = doms[k];
+      if (d.t0 < 0 || d.t1 >= L->dims[0] || d.t0 > d.t1) {
+        lq_set_error("slab out of range: " + std::to_string(d.t0) + ".." + std::to_string(d.t1));
+        return LQCD_EBADARG;
+      }
+      if (fields[k] < 0 || fields[k] >= (int)L->fields.size()) {
+        lq_set_error("field index " + std::to_string(fields[k]) + " not loaded");
+        return LQCD_ENOFIELD;
+      }
+      lq::SysDesc s{};
+      s.field = fields[k];
+      s.t0 = d.t0;
+      s.t1 = d.t1;
+      s.wrap = (d.t0 == 0 && d.t1 == L->dims[0] - 1 && L->bc != LQCD_BC_OPEN) ? 1 : 0;
+      s.tsign = L->bc == LQCD_BC_ANTIPERIODIC ? -1.f : 1.f;
+      s.n = (long long)(d.t1 - d.t0 + 1) * L->S3h;
+      s.cb0 = (long long)d.t0 * L->S3h;
+      s.off = off;
+      off += s.n;
+      maxn = std::max(maxn, s.n);
+      h_sys[k] = s;
+    }
+    b.nsys = n;
+    b.max_n = maxn;
+    b.total = off;
+    b.nby = (int)((maxn + LQ_BLOCK - 1) / LQ_BLOCK);
+    if (b.nby > 65535) {
+      lq_set_error("slab too large for one batch");
+      return LQCD_EBADARG;
+    }
+    RC(sys.alloc(sizeof(lq::SysDesc) * n, st));
+    RC(active.alloc(sizeof(int) * n, st));
+    RC(sc.alloc(sizeof(lq::SolverScal) * n, st));
+    RC(partial.alloc(sizeof(double) * 4 * (size_t)n * b.nby, st));
+    CK(cudaMemcpyAsync(sys.p, h_sys.data(), sizeof(lq::SysDesc) * n, cudaMemcpyHostToDevice, st));
+    b.sys = sys.as<lq::SysDesc>();
+    b.active = active.as<int>();
+    b.sc = sc.as<lq::SolverScal>();
+    b.partial = partial.as<double>();
+    h_sc.assign(n, lq::SolverScal{});
+    h_active.assign(n, 1);
+    CK(cudaMemcpyAsync(sc.p, h_sc.data(), sizeof(lq::SolverScal) * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(active.p, h_active.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+    return 0;
+  }
+  int push_active(cudaStream_t st) {
+    CK(cudaMemcpyAsync(active.p, h_active.data(), sizeof(int) * b.nsys, cudaMemcpyHostToDevice, st));
+    return 0;
+  }
+  int pull_sc(cudaStream_t st) {
+    CK(cudaMemcpyAsync(h_sc.data(), sc.p, sizeof(lq::SolverScal) * b.nsys, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return 0;
+  }
+  int push_sc(cudaStream_t st) {
+    CK(cudaMemcpyAsync(sc.p, h_sc.data(), sizeof(lq::SolverScal) * b.nsys, cudaMemcpyHostToDevice, st));
+    return 0;
+  }
+  // A view of systems [k0, k0+n) (same pools, offsets from the descriptors).
+  Batch view(int k0, int n) const {
+    Batch v = b;
+    v.nsys = n;
+    v.sys = b.sys + k0;
+    v.active = b.active + k0;
+    v.sc = b.sc + k0;
+    long long maxn = 0;
+    for (int k = k0; k < k0 + n; k++) maxn = std::max(maxn, h_sys[k].n);
+    v.max_n = maxn;
+    v.partial = b.partial;  // layout [sys][nby] with the full batch's nby
+    v.partial = b.partial + (size_t)k0 * b.nby * 4;
+    return v;
+  }
+};
+
+// FP64 pool of `count` vectors of a batch (each total*12 double2).
+struct Pool64 {
+  DBuf buf;
+  long long words = 0;
+  int alloc(const Batch& b, int count, cudaStream_t st) {
+    words = b.total * 12;
+    return buf.alloc(sizeof(double2) * (size_t)words * count, st);
+  }
+  double2* v(int k) const { return buf.as<double2>() + (size_t)k * words; }
+};
+
+// Pool of `count` vectors in precision P (norm pool for FP16).
+struct PoolP {
+  DBuf buf, nrm;
+  long long bytes = 0;
+  long long total = 0;
+  int P = 64;
+  int alloc(const Batch& b, int prec, int count, cudaStream_t st) {
+    P = prec;
+    total = b.total;
+    bytes = b.total * (P == 64 ? 192 : P == 32 ? 96 : 48);
+    RC(buf.alloc((size_t)bytes * count, st));
+    if (P == 16) RC(nrm.alloc(sizeof(float) * (size_t)total * count, st));
+    return 0;
+  }
+  VecP v(int k) const {
+    VecP r;
+    r.d = (char*)buf.p + (size_t)bytes * k;
+    r.nrm = P == 16 ? nrm.as<float>() + (size_t)total * k : nullptr;
+    return r;
+  }
+};
+
+VecP v64(double2* p) {
+  VecP r;
+  r.d = p;
+  return r;
+}
+
+struct SolveOut {
+  std::vector<int> iters, cycles, status;
+  std::vector<double> res;
+};
+
+// Solve D_L x = b (dag: D_L^dag x = b) for every system of the batch.
+// b_e, b_o, x_e, x_o: FP64 even / odd pools of the batch.
+int solve_core(lqcd_lattice* L, BatchStore& B, bool dag, const lqcd_solver_params& prm, double2* b_e, double2* b_o,
+               double2* x_e, double2* x_o, SolveOut& out, cudaStream_t st) {
+  Batch& b = B.b;
+  const int n = b.nsys;
+  const int P = prm.precision == 16 ? 16 : prm.precision == 32 ? 32 : 64;
+  const bool clov = L->csw != 0.0;
+  const double tol = prm.tol > 0 ? prm.tol : 1e-10;
+  const int max_iter = prm.max_iter > 0 ? prm.max_iter : 100000;
+  const int check_every = prm.check_every > 0 ? prm.check_every : 8;
+  double inner_tol = prm.inner_tol;
+  if (!(inner_tol > 0)) inner_tol = P == 64 ? 0.0 : P == 32 ? 1e-5 : 2e-2;
+  // iterations of one inner cycle: a reduced-precision BiCGStab that has not
+  // reached inner_tol by then is restarted from the true FP64 residual
+  const int cycle_cap = P == 64 ? max_iter : P == 32 ? 2000 : 500;
+  if (P == 64) inner_tol = 0.0;
+  out.iters.assign(n, 0);
+  out.cycles.assign(n, 0);
+  out.status.assign(n, 0);
+  out.res.assign(n, 0.0);
+
+  Pool64 f64;
+  RC(f64.alloc(b, 3, st));
+  double2* bh_o = f64.v(0);
+  double2* r64 = f64.v(1);
+  double2* t64 = f64.v(2);
+  PoolP ps;
+  RC(ps.alloc(b, P, 8, st));
+  VecP r = ps.v(0), r0 = ps.v(1), p = ps.v(2), v = ps.v(3), s = ps.v(4), t = ps.v(5), xs = ps.v(6), te = ps.v(7);
+  PinnedInt cnt;
+  DBuf dcnt;
+  RC(dcnt.alloc(sizeof(int), st));
+  VecP none;
+
+  // |eta|^2 of each system (both parities)
+  std::fill(B.h_active.begin(), B.h_active.end(), 1);
+  RC(B.push_active(st));
+  std::vector<double> bb(n);
+  RC(lq_norm2_64(b, b_e, st));
+  RC(lq_finalize(lq::FIN_NORM, b, 0, 0, st));
+  RC(B.pull_sc(st));
+  for (int k = 0; k < n; k++) bb[k] = B.h_sc[k].rr;
+  RC(lq_norm2_64(b, b_o, st));
+  RC(lq_finalize(lq::FIN_NORM, b, 0, 0, st));
+  RC(B.pull_sc(st));
+  for (int k = 0; k < n; k++) {
+    bb[k] += B.h_sc[k].rr;
+    B.h_sc[k].bb = bb[k];
+  }
+  if (verbose())
+    for (int k = 0; k < n; k++) fprintf(stderr, "[lqcd] solve P=%d sys %d |eta|^2 = %.6e n=%lld\n", P, k, bb[k], B.h_sys[k].n);
+  RC(B.push_sc(st));
+
+  // prepare: bh_o = b_o + 1/2 H_oe A_ee^{-1} b_e
+  RC(lq_hop_clinv(64, dag, clov, L, b, none, v64(b_e), v64(t64), 0.0, 1.0, st));
+  RC(lq_hop_lin(64, dag, clov, lq::RED_NONE, L, b, 1, v64(t64), none, v64(b_o), none, v64(bh_o), 0.5, 0.0, 1.0, st));
+  CK(cudaMemsetAsync(x_o, 0, sizeof(double2) * (size_t)b.total * 12, st));
+
+  std::vector<int> outer(n, 1);
+  for (int k = 0; k < n; k++)
+    if (!(bb[k] > 0)) outer[k] = 0;  // zero source: zero solution
+  std::vector<double> prev_rr(n, INFINITY);
+  std::vector<int> stall(n, 0);
+  for (int cycle = 0;; cycle++) {
+    // true residual of the preconditioned system: r64 = bh_o - Dhat x_o (FP64)
+    B.h_active = outer;
+    RC(B.push_active(st));
+    RC(lq_hop_clinv(64, dag, clov, L, b, v64(x_o), none, v64(t64), 1.0, 0.0, st));
+    RC(lq_hop_lin(64, dag, clov, lq::RED_NORM, L, b, 1, v64(t64), v64(x_o), v64(bh_o), none, v64(r64), 0.25, -1.0, 1.0,
+                  st));
+    RC(lq_finalize(lq::FIN_NORM, b, 0, 0, st));
+    RC(B.pull_sc(st));
+    int n_act = 0;
+    for (int k = 0; k < n; k++) {
+      if (!outer[k]) continue;
+      const double rr = B.h_sc[k].rr;
+      if (verbose())
+        fprintf(stderr, "[lqcd] cycle %d sys %d |r|/|eta| = %.3e iters %d status %d\n", cycle, k, std::sqrt(rr / bb[k]),
+                out.iters[k], B.h_sc[k].status);
+      out.cycles[k] = cycle;
+      if (!std::isfinite(rr)) {
+        out.status[k] = LQCD_ENAN;
+        outer[k] = 0;
+      } else if (rr <= tol * tol * bb[k]) {
+        outer[k] = 0;
+      } else if (out.iters[k] >= max_iter) {
+        out.status[k] = LQCD_ENOTCONVERGED;
+        outer[k] = 0;
+      } else {
+        stall[k] = rr > 0.25 * prev_rr[k] ? stall[k] + 1 : 0;
+        prev_rr[k] = rr;
+        if (stall[k] >= 6) {
+          out.status[k] = LQCD_ENOTCONVERGED;
+          outer[k] = 0;
+        }
+      }
+      n_act += outer[k];
+    }
+    if (n_act == 0) break;
+    // inner solve of Dhat e = r64 in precision P
+    B.h_active = outer;
+    RC(B.push_active(st));
+    RC(lq_inner_init(P, b, r64, r, r0, p, xs, st));
+    RC(lq_finalize(lq::FIN_INIT, b, inner_tol * inner_tol, 0.25 * tol * tol, st));
+    int it = 0;
+    int budget = 0;
+    for (int k = 0; k < n; k++)
+      if (outer[k]) budget = std::max(budget, max_iter - out.iters[k]);
+    budget = std::min(budget, cycle_cap);
+    while (it < budget) {
+      RC(lq_hop_clinv(P, dag, clov, L, b, p, none, te, 1.0, 0.0, st));
+      RC(lq_hop_lin(P, dag, clov, lq::RED_DOT_W, L, b, 1, te, p, none, r0, v, -0.25, 1.0, 0.0, st));
+      RC(lq_finalize(lq::FIN_ALPHA, b, 0, 0, st));
+      RC(lq_bicg_s(P, b, r, v, s, st));
+      RC(lq_hop_clinv(P, dag, clov, L, b, s, none, te, 1.0, 0.0, st));
+      RC(lq_hop_lin(P, dag, clov, lq::RED_TS, L, b, 1, te, s, none, none, t, -0.25, 1.0, 0.0, st));
+      RC(lq_finalize(lq::FIN_OMEGA, b, 0, 0, st));
+      RC(lq_bicg_xr(P, b, xs, p, s, t, r, r0, st));
+      RC(lq_finalize(lq::FIN_BETA, b, 0, 0, st));
+      RC(lq_bicg_p(P, b, p, r, v, st));
+      it++;
+      if (it % check_every == 0 || it >= budget) {
+        RC(lq_count_active(b, dcnt.as<int>(), st));
+        CK(cudaMemcpyAsync(cnt.h, dcnt.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (*cnt.h == 0) break;
+      }
+    }
+    // x_o += e for the systems of this cycle
+    RC(B.pull_sc(st));
+    B.h_active = outer;
+    RC(B.push_active(st));
+    RC(lq_accum64(P, b, x_o, xs, st));
+    for (int k = 0; k < n; k++)
+      if (outer[k]) out.iters[k] += B.h_sc[k].iters;
+  }
+  // reconstruct x_e = A_ee^{-1}(b_e + 1/2 H_eo x_o), then the full FP64 residual
+  std::fill(B.h_active.begin(), B.h_active.end(), 1);
+  RC(B.push_active(st));
+  RC(lq_hop_clinv(64, dag, clov, L, b, v64(x_o), v64(b_e), v64(x_e), 0.5, 1.0, st));
+  RC(lq_hop_lin(64, dag, clov, lq::RED_NORM, L, b, 0, v64(x_o), v64(x_e), v64(b_e), none, v64(t64), 0.5, -1.0, 1.0, st));
+  RC(lq_finalize(lq::FIN_NORM, b, 0, 0, st));
+  RC(B.pull_sc(st));
+  std::vector<double> rre(n);
+  for (int k = 0; k < n; k++) rre[k] = B.h_sc[k].rr;
+  RC(lq_hop_lin(64, dag, clov, lq::RED_NORM, L, b, 1, v64(x_e), v64(x_o), v64(b_o), none, v64(r64), 0.5, -1.0, 1.0, st));
+  RC(lq_finalize(lq::FIN_NORM, b, 0, 0, st));
+  RC(B.pull_sc(st));
+  for (int k = 0; k < n; k++) {
+    const double rr = rre[k] + B.h_sc[k].rr;
+    out.res[k] = bb[k] > 0 ? std::sqrt(rr / bb[k]) : 0.0;
+    if (out.status[k] == 0 && !(out.res[k] <= tol)) out.status[k] = std::isfinite(out.res[k]) ? LQCD_ENOTCONVERGED : LQCD_ENAN;
+  }
+  return 0;
+}
+
+lqcd_solver_params default_params(const lqcd_solver_params* p) {
+  lqcd_solver_params q{};
+  q.tol = 1e-10;
+  q.max_iter = 100000;
+  q.precision = 64;
+  q.inner_tol = 0;
+  q.check_every = 0;
+  if (p) q = *p;
+  return q;
+}
+
+int worst_status(const SolveOut& o) {
+  int w = 0;
+  for (int s : o.status)
+    if (s != 0 && (w == 0 || s < w)) w = s;
+  return w;
+}
+
+void fill_stats(const SolveOut& o, int k0, int n, double secs, lqcd_solver_stats* st) {
+  st->iters = 0;
+  st->cycles = 0;
+  st->status = 0;
+  st->true_residual = 0;
+  st->seconds = secs;
+  for (int k = k0; k < k0 + n; k++) {
+    st->iters = std::max(st->iters, o.iters[k]);
+    st->cycles = std::max(st->cycles, o.cycles[k]);
+    st->true_residual = std::max(st->true_residual, o.res[k]);
+    if (o.status[k] != 0 && st->status == 0) st->status = o.status[k];
+  }
+}
+
+}  // namespace
+
+// ===================================================================== API
+extern "C" int lqcd_create_lattice(const int dims[4], int bc_t, lqcd_lattice** out) {
+  if (!dims || !out) {
+    lq_set_error("null argument");
+    return LQCD_EBADARG;
+  }
+  for (int k = 0; k < 4; k++)
+    if (dims[k] < 2 || dims[k] % 2) {
+      lq_set_error("every extent must be even and >= 2");
+      return LQCD_EBADARG;
+    }
+  if (bc_t < 0 || bc_t > 2) {
+    lq_set_error("bad time boundary condition");
+    return LQCD_EBADARG;
+  }
+  lqcd_lattice* L = new lqcd_lattice();
+  for (int k = 0; k < 4; k++) L->dims[k] = dims[k];
+  L->bc = bc_t;
+  L->S3 = (long long)dims[1] * dims[2] * dims[3];
+  L->S3h = L->S3 / 2;
+  L->V = L->S3 * dims[0];
+  L->Vh = L->V / 2;
+  for (int k = 0; k < 4; k++) L->g.L[k] = dims[k];
+  L->g.L3h = dims[3] / 2;
+  L->g.Vh = L->Vh;
+  L->g.S3h = L->S3h;
+  L->g.bc_t = bc_t;
+  cudaGetDevice(&L->device);
+  *out = L;
+  return 0;
+}
+
+static void free_fields(lqcd_lattice* L) {
+  for (auto& f : L->fields) {
+    cudaFree(f.U64);
+    cudaFree(f.U32);
+    cudaFree(f.U16);
+    cudaFree(f.A64);
+    cudaFree(f.Ai64);
+    cudaFree(f.A32);
+    cudaFree(f.Ai32);
+  }
+  L->fields.clear();
+  if (L->d_fields) cudaFree(L->d_fields);
+  L->d_fields = nullptr;
+}
+
+extern "C" int lqcd_destroy_lattice(lqcd_lattice* L) {
+  RC(check_lat(L));
+  cudaDeviceSynchronize();
+  free_fields(L);
+  delete L;
+  return 0;
+}
+
+extern "C" int lqcd_set_gauge(lqcd_lattice* L, int n_fields, const double* U, double kappa, double c_sw, int mem,
+                              void* stream) {
+  RC(check_lat(L));
+  if (n_fields < 1 || !U || !(kappa > 0)) {
+    lq_set_error("set_gauge: need n_fields >= 1, U != NULL, kappa > 0");
+    return LQCD_EBADARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaStreamSynchronize(st));
+  free_fields(L);
+  L->kappa = kappa;
+  L->csw = c_sw;
+  const long long V = L->V, Vh = L->Vh;
+  const size_t nat_bytes = sizeof(double2) * (size_t)V * 36;
+  DBuf tmp;
+  if (mem == LQCD_MEM_HOST) RC(tmp.alloc(nat_bytes, st));
+  DBuf dev, fail;
+  RC(dev.alloc(sizeof(unsigned long long), st));
+  RC(fail.alloc(sizeof(int), st));
+  std::vector<lq::FieldPtrs> ptrs;
+  for (int fi = 0; fi < n_fields; fi++) {
+    FieldData f;
+    CK(cudaMalloc(&f.U64, sizeof(double2) * 2 * 4 * 9 * Vh));
+    L->fields.push_back(f);
+    FieldData& F = L->fields.back();
+    CK(cudaMalloc(&F.U32, sizeof(float4) * 2 * 4 * 3 * Vh));
+    CK(cudaMalloc(&F.U16, sizeof(uint2) * 2 * 4 * 3 * Vh));
+    CK(cudaMalloc(&F.A64, sizeof(double2) * 2 * 36 * Vh));
+    CK(cudaMalloc(&F.Ai64, sizeof(double2) * 36 * Vh));
+    CK(cudaMalloc(&F.A32, sizeof(float4) * 2 * 18 * Vh));
+    CK(cudaMalloc(&F.Ai32, sizeof(float4) * 18 * Vh));
+    const double2* src = (const double2*)(U + (size_t)fi * V * 72);
+    if (mem == LQCD_MEM_HOST) {
+      CK(cudaMemcpyAsync(tmp.p, src, nat_bytes, cudaMemcpyHostToDevice, st));
+      src = tmp.as<double2>();
+    }
+    CK(cudaMemsetAsync(dev.p, 0, sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(fail.p, 0, sizeof(int), st));
+    RC(lq_launch_pack_links(L->g, src, F.U64, F.U32, F.U16, dev.as<unsigned long long>(), st));
+    RC(lq_launch_clover(L->g, src, kappa, c_sw, F.A64, F.Ai64, F.A32, F.Ai32, fail.as<int>(), st));
+    unsigned long long d = 0;
+    int fl = 0;
+    CK(cudaMemcpyAsync(&d, dev.p, sizeof(d), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&fl, fail.p, sizeof(fl), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    double dv;
+    memcpy(&dv, &d, sizeof(dv));
+    if (!(dv <= 1e-10)) {
+      lq_set_error("set_gauge: field " + std::to_string(fi) + " is not SU(3): deviation " + std::to_string(dv));
+      free_fields(L);
+      return LQCD_ENONUNITARY;
+    }
+    if (fl) {
+      lq_set_error("set_gauge: singular clover block in field " + std::to_string(fi));
+      free_fields(L);
+      return LQCD_EBADARG;
+    }
+    lq::FieldPtrs fp;
+    fp.U64 = F.U64;
+    fp.U32 = F.U32;
+    fp.U16 = F.U16;
+    fp.A64 = F.A64;
+    fp.Ai64 = F.Ai64;
+    fp.A32 = F.A32;
+    fp.Ai32 = F.Ai32;
+    ptrs.push_back(fp);
+  }
+  CK(cudaMalloc(&L->d_fields, sizeof(lq::FieldPtrs) * n_fields));
+  CK(cudaMemcpy(L->d_fields, ptrs.data(), sizeof(lq::FieldPtrs) * n_fields, cudaMemcpyHostToDevice));
+  return 0;
+}
+
+extern "C" int lqcd_dslash(lqcd_lattice* L, int field, const lqcd_slab* dom, int dagger, int precision,
+                           const double* in, double* out, void* stream) {
+  RC(check_lat(L));
+  if (!in || !out || (precision != 64 && precision != 32 && precision != 16)) {
+    lq_set_error("dslash: bad arguments");
+    return LQCD_EBADARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  lqcd_slab d = dom ? *dom : lqcd_slab{0, L->dims[0] - 1};
+  BatchStore B;
+  RC(B.build(L, 1, &d, &field, st));
+  const Batch& b = B.b;
+  Pool64 e;
+  RC(e.alloc(b, 4, st));
+  DBuf ptr;
+  RC(ptr.alloc(sizeof(void*), st));
+  const double2* srcp = (const double2*)in;
+  CK(cudaMemcpyAsync(ptr.p, &srcp, sizeof(void*), cudaMemcpyHostToDevice, st));
+  RC(lq_nat_to_eo(L, b, ptr.as<const double2*>(), e.v(0), e.v(1), st));
+  const bool clov = L->csw != 0.0;
+  VecP none;
+  if (precision == 64) {
+    RC(lq_hop_lin(64, dagger, clov, lq::RED_NONE, L, b, 0, v64(e.v(1)), v64(e.v(0)), none, none, v64(e.v(2)), -0.5, 1.0,
+                  0.0, st));
+    RC(lq_hop_lin(64, dagger, clov, lq::RED_NONE, L, b, 1, v64(e.v(0)), v64(e.v(1)), none, none, v64(e.v(3)), -0.5, 1.0,
+                  0.0, st));
+  } else {
+    PoolP q;
+    RC(q.alloc(b, precision, 4, st));
+    RC(lq_convert(64, precision, b, v64(e.v(0)), q.v(0), st));
+    RC(lq_convert(64, precision, b, v64(e.v(1)), q.v(1), st));
+    RC(lq_hop_lin(precision, dagger, clov, lq::RED_NONE, L, b, 0, q.v(1), q.v(0), none, none, q.v(2), -0.5, 1.0, 0.0,
+                  st));
+    RC(lq_hop_lin(precision, dagger, clov, lq::RED_NONE, L, b, 1, q.v(0), q.v(1), none, none, q.v(3), -0.5, 1.0, 0.0,
+                  st));
+    RC(lq_convert(precision, 64, b, q.v(2), v64(e.v(2)), st));
+    RC(lq_convert(precision, 64, b, q.v(3), v64(e.v(3)), st));
+    CK(cudaStreamSynchronize(st));
+  }
+  double2* dstp = (double2*)out;
+  CK(cudaMemcpyAsync(ptr.p, &dstp, sizeof(void*), cudaMemcpyHostToDevice, st));
+  RC(lq_eo_to_nat(L, b, e.v(2), e.v(3), ptr.as<double2* const>(), 1.0, st));
+  CK(cudaStreamSynchronize(st));
+  return 0;
+}
+
+static int solve_api(lqcd_lattice* L, int n, const lqcd_slab* doms, const int* field_ids, const double* src,
+                     double* sol, const lqcd_solver_params* params, lqcd_solver_stats* stats, void* stream) {
+  if (n < 1 || !doms || !field_ids || !src || !sol) {
+    lq_set_error("solve: bad arguments");
+    return LQCD_EBADARG;
+  }
+  const double t_start = now_s();
+  cudaStream_t st = (cudaStream_t)stream;
+  lqcd_solver_params prm = default_params(params);
+  BatchStore B;
+  RC(B.build(L, n, doms, field_ids, st));
+  const Batch& b = B.b;
+  std::vector<const double2*> sp(n);
+  std::vector<double2*> dp(n);
+  for (int k = 0; k < n; k++) {
+    sp[k] = (const double2*)src + 2 * B.h_sys[k].off * 12;
+    dp[k] = (double2*)sol + 2 * B.h_sys[k].off * 12;
+  }
+  DBuf dsp, ddp;
+  RC(dsp.alloc(sizeof(void*) * n, st));
+  RC(ddp.alloc(sizeof(void*) * n, st));
+  CK(cudaMemcpyAsync(dsp.p, sp.data(), sizeof(void*) * n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ddp.p, dp.data(), sizeof(void*) * n, cudaMemcpyHostToDevice, st));
+  Pool64 e;
+  RC(e.alloc(b, 4, st));
+  RC(lq_nat_to_eo(L, b, dsp.as<const double2*>(), e.v(0), e.v(1), st));
+  SolveOut o;
+  RC(solve_core(L, B, false, prm, e.v(0), e.v(1), e.v(2), e.v(3), o, st));
+  RC(lq_eo_to_nat(L, b, e.v(2), e.v(3), ddp.as<double2* const>(), 1.0, st));
+  CK(cudaStreamSynchronize(st));
+  const double secs = now_s() - t_start;
+  if (stats)
+    for (int k = 0; k < n; k++) fill_stats(o, k, 1, secs, &stats[k]);
+  int w = worst_status(o);
+  if (w) lq_set_error("solve: some systems did not reach the tolerance");
+  return w;
+}
+
+extern "C" int lqcd_solve_block(lqcd_lattice* L, int n_sys, const lqcd_slab* doms, const int* field_ids,
+                                const double* src, double* sol, const lqcd_solver_params* params,
+                                lqcd_solver_stats* stats, void* stream) {
+  RC(check_lat(L));
+  return solve_api(L, n_sys, doms, field_ids, src, sol, params, stats, stream);
+}
+
+extern "C" int lqcd_solve_full(lqcd_lattice* L, int n_sys, const int* field_ids, const double* src, double* sol,
+                               const lqcd_solver_params* params, lqcd_solver_stats* stats, void* stream) {
+  RC(check_lat(L));
+  if (n_sys < 1) {
+    lq_set_error("solve_full: n_sys < 1");
+    return LQCD_EBADARG;
+  }
+  std::vector<lqcd_slab> d(n_sys, lqcd_slab{0, L->dims[0] - 1});
+  return solve_api(L, n_sys, d.data(), field_ids, src, sol, params, stats, stream);
+}
+
+extern "C" int lqcd_factorized_propagator(lqcd_lattice* L, const lqcd_split* split, const int x_src[4], int field,
+                                          double* fact, double* corr, const lqcd_solver_params* params,
+                                          lqcd_solver_stats* stats, void* stream) {
+  RC(check_lat(L));
+  if (!split || !x_src || !fact) {
+    lq_set_error("factorized_propagator: null argument");
+    return LQCD_EBADARG;
+  }
+  const int T = L->dims[0];
+  const lqcd_slab G = split->gamma, Gs = split->gamma_star, Dl = split->delta;
+  const bool has_delta = Dl.t1 >= Dl.t0;
+  if (G.t0 != 0 || G.t1 < 0 || Gs.t0 != G.t1 + 1 || Gs.t1 != T - 1 ||
+      (has_delta && (Dl.t0 != G.t1 + 1 || Dl.t1 >= T - 1))) {
+    lq_set_error("factorized_propagator: need Gamma = 0..g1, Gamma* = g1+1..T-1, DeltaGamma = g1+1..d1 (d1 < T-1)");
+    return LQCD_EBADARG;
+  }
+  if (x_src[0] < G.t0 || x_src[0] > G.t1) {
+    lq_set_error("factorized_propagator: the source must lie in Gamma");
+    return LQCD_EBADARG;
+  }
+  for (int k = 1; k < 4; k++)
+    if (x_src[k] < 0 || x_src[k] >= L->dims[k]) {
+      lq_set_error("factorized_propagator: source outside the lattice");
+      return LQCD_EBADARG;
+    }
+  const double t_start = now_s();
+  cudaStream_t st = (cudaStream_t)stream;
+  lqcd_solver_params prm = default_params(params);
+  const lqcd_slab Gb = {0, has_delta ? Dl.t1 : G.t1};
+  const bool want_corr = corr != nullptr;
+
+  // stage A: Gammabar and Gamma solves from the point sources (eqs. quark_prop_I, quark_prop_II)
+  std::vector<lqcd_slab> da;
+  std::vector<int> fa, ca;
+  for (int c = 0; c < 12; c++) da.push_back(Gb), fa.push_back(field), ca.push_back(c);
+  if (has_delta)
+    for (int c = 0; c < 12; c++) da.push_back(G), fa.push_back(field), ca.push_back(c);
+  BatchStore A;
+  RC(A.build(L, (int)da.size(), da.data(), fa.data(), st));
+  // stage B: Gamma* solves of the boundary sources, and the full solves
+  std::vector<lqcd_slab> db;
+  std::vector<int> fb, cbv;
+  for (int c = 0; c < 12; c++) db.push_back(Gs), fb.push_back(field), cbv.push_back(c);
+  if (want_corr)
+    for (int c = 0; c < 12; c++) db.push_back(lqcd_slab{0, T - 1}), fb.push_back(field), cbv.push_back(c);
+  BatchStore Bs;
+  RC(Bs.build(L, (int)db.size(), db.data(), fb.data(), st));
+
+  DBuf dcols;
+  RC(dcols.alloc(sizeof(int) * 24, st));
+  CK(cudaMemcpyAsync(dcols.p, ca.data(), sizeof(int) * ca.size(), cudaMemcpyHostToDevice, st));
+  Pool64 ea, eb;
+  RC(ea.alloc(A.b, 4, st));
+  RC(eb.alloc(Bs.b, 4, st));
+  RC(lq_point_source(L, A.b, dcols.as<int>(), x_src, ea.v(0), ea.v(1), st));
+  SolveOut oa, ob;
+  RC(solve_core(L, A, false, prm, ea.v(0), ea.v(1), ea.v(2), ea.v(3), oa, st));
+  // chi = D_dGamma* (D_Gammabar^{-1} eta)|_Gamma  on the first slice of Gamma*
+  RC(lq_boundary_hop(L, Bs.view(0, 12), A.view(0, 12), G.t1, ea.v(2), ea.v(3), eb.v(0), eb.v(1), st));
+  if (want_corr) {
+    Batch fv = Bs.view(12, 12);
+    RC(lq_point_source(L, fv, dcols.as<int>(), x_src, eb.v(0), eb.v(1), st));
+  }
+  RC(solve_core(L, Bs, false, prm, eb.v(0), eb.v(1), eb.v(2), eb.v(3), ob, st));
+
+  // assemble fact: D_Gamma^{-1} eta on Gamma, -zeta on Gamma*
+  const long long V = L->V, S3 = L->S3;
+  CK(cudaMemsetAsync(fact, 0, sizeof(double2) * 12 * (size_t)V * 12, st));
+  std::vector<double2*> dst(12);
+  DBuf ddst;
+  RC(ddst.alloc(sizeof(void*) * 24, st));
+  {
+    const int k0 = has_delta ? 12 : 0;
+    for (int c = 0; c < 12; c++) dst[c] = (double2*)fact + (size_t)c * V * 12 + (size_t)G.t0 * S3 * 12;
+    CK(cudaMemcpyAsync(ddst.p, dst.data(), sizeof(void*) * 12, cudaMemcpyHostToDevice, st));
+    RC(lq_eo_to_nat(L, A.view(k0, 12), ea.v(2), ea.v(3), ddst.as<double2* const>(), 1.0, st));
+  }
+  {
+    for (int c = 0; c < 12; c++) dst[c] = (double2*)fact + (size_t)c * V * 12 + (size_t)Gs.t0 * S3 * 12;
+    CK(cudaMemcpyAsync(ddst.as<double2*>() + 12, dst.data(), sizeof(void*) * 12, cudaMemcpyHostToDevice, st));
+    RC(lq_eo_to_nat(L, Bs.view(0, 12), eb.v(2), eb.v(3), (double2* const*)(ddst.as<double2*>() + 12), -1.0, st));
+  }
+  if (want_corr) {
+    DBuf dd2;
+    RC(dd2.alloc(sizeof(void*) * 12, st));
+    for (int c = 0; c < 12; c++) dst[c] = (double2*)corr + (size_t)c * V * 12;
+    CK(cudaMemcpyAsync(dd2.p, dst.data(), sizeof(void*) * 12, cudaMemcpyHostToDevice, st));
+    RC(lq_eo_to_nat(L, Bs.view(12, 12), eb.v(2), eb.v(3), dd2.as<double2* const>(), 1.0, st));
+    RC(lq_sub_inplace((double2*)corr, (const double2*)fact, 12 * V * 12, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  CK(cudaStreamSynchronize(st));
+  const double secs = now_s() - t_start;
+  if (stats) {
+    fill_stats(oa, has_delta ? 12 : 0, 12, secs, &stats[0]);  // Gamma
+    fill_stats(oa, 0, 12, secs, &stats[1]);                   // Gammabar
+    fill_stats(ob, 0, 12, secs, &stats[2]);                   // Gamma*
+    if (want_corr) fill_stats(ob, 12, 12, secs, &stats[3]);
+    else memset(&stats[3], 0, sizeof(lqcd_solver_stats));
+  }
+  int w = worst_status(oa);
+  if (!w) w = worst_status(ob);
+  if (w) lq_set_error("factorized_propagator: some solves did not reach the tolerance");
+  return w;
+}
+
+extern "C" int lqcd_link_force(lqcd_lattice* L, const lqcd_slab* dom, int field, const double* phi, double* force,
+                               double* action, const lqcd_solver_params* params, lqcd_solver_stats* stats,
+                               void* stream) {
+  RC(check_lat(L));
+  if (!phi) {
+    lq_set_error("link_force: null argument");
+    return LQCD_EBADARG;
+  }
+  const double t_start = now_s();
+  cudaStream_t st = (cudaStream_t)stream;
+  lqcd_slab d = dom ? *dom : lqcd_slab{0, L->dims[0] - 1};
+  lqcd_solver_params prm = default_params(params);
+  BatchStore B;
+  RC(B.build(L, 1, &d, &field, st));
+  const Batch& b = B.b;
+  Pool64 e;
+  RC(e.alloc(b, 6, st));  // phi_e, phi_o, Y_e, Y_o, X_e, X_o
+  DBuf ptr;
+  RC(ptr.alloc(sizeof(void*), st));
+  const double2* srcp = (const double2*)phi;
+  CK(cudaMemcpyAsync(ptr.p, &srcp, sizeof(void*), cudaMemcpyHostToDevice, st));
+  RC(lq_nat_to_eo(L, b, ptr.as<const double2*>(), e.v(0), e.v(1), st));
+  SolveOut oy, ox;
+  RC(solve_core(L, B, true, prm, e.v(0), e.v(1), e.v(2), e.v(3), oy, st));   // D^dag Y = phi
+  if (force) RC(solve_core(L, B, false, prm, e.v(2), e.v(3), e.v(4), e.v(5), ox, st));  // D X = Y
+  // S = |Y|^2
+  std::fill(B.h_active.begin(), B.h_active.end(), 1);
+  RC(B.push_active(st));
+  double S = 0;
+  for (int par = 0; par < 2; par++) {
+    RC(lq_norm2_64(b, e.v(2 + par), st));
+    RC(lq_finalize(lq::FIN_NORM, b, 0, 0, st));
+    RC(B.pull_sc(st));
+    S += B.h_sc[0].rr;
+  }
+  if (action) *action = S;
+  if (!force) {  // action only: S = |Y|^2 needs the D^dag solve alone
+    CK(cudaStreamSynchronize(st));
+    if (stats) {
+      fill_stats(oy, 0, 1, now_s() - t_start, &stats[0]);
+      memset(&stats[1], 0, sizeof(lqcd_solver_stats));
+    }
+    int w = worst_status(oy);
+    if (w) lq_set_error("link_force: the D^dag solve did not reach the tolerance");
+    return w;
+  }
+  // natural full-lattice X, Y (zero outside the slab)
+  const long long V = L->V;
+  DBuf Xn, Yn;
+  RC(Xn.alloc(sizeof(double2) * (size_t)V * 12, st));
+  RC(Yn.alloc(sizeof(double2) * (size_t)V * 12, st));
+  CK(cudaMemsetAsync(Xn.p, 0, sizeof(double2) * (size_t)V * 12, st));
+  CK(cudaMemsetAsync(Yn.p, 0, sizeof(double2) * (size_t)V * 12, st));
+  double2* dx = Xn.as<double2>() + (size_t)d.t0 * L->S3 * 12;
+  CK(cudaMemcpyAsync(ptr.p, &dx, sizeof(void*), cudaMemcpyHostToDevice, st));
+  RC(lq_eo_to_nat(L, b, e.v(4), e.v(5), ptr.as<double2* const>(), 1.0, st));
+  DBuf ptr2;
+  RC(ptr2.alloc(sizeof(void*), st));
+  double2* dy = Yn.as<double2>() + (size_t)d.t0 * L->S3 * 12;
+  CK(cudaMemcpyAsync(ptr2.p, &dy, sizeof(void*), cudaMemcpyHostToDevice, st));
+  RC(lq_eo_to_nat(L, b, e.v(2), e.v(3), ptr2.as<double2* const>(), 1.0, st));
+  RC(lq_force(L, field, d, Xn.as<double2>(), Yn.as<double2>(), force, st));
+  CK(cudaStreamSynchronize(st));
+  const double secs = now_s() - t_start;
+  if (stats) {
+    fill_stats(oy, 0, 1, secs, &stats[0]);
+    fill_stats(ox, 0, 1, secs, &stats[1]);
+  }
+  int w = worst_status(oy);
+  if (!w) w = worst_status(ox);
+  if (w) lq_set_error("link_force: a solve did not reach the tolerance");
+  return w;
+}
+
+extern "C" int lqcd_dslash_bench(lqcd_lattice* L, int n_sys, const lqcd_slab* doms, const int* field_ids,
+                                 int precision, int reps, double* ms_per_launch, double* bytes_per_launch,
+                                 double* flops_per_launch, void* stream) {
+  RC(check_lat(L));
+  if (n_sys < 1 || !doms || !field_ids || reps < 1 || (precision != 64 && precision != 32 && precision != 16)) {
+    lq_set_error("dslash_bench: bad arguments");
+    return LQCD_EBADARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  BatchStore B;
+  RC(B.build(L, n_sys, doms, field_ids, st));
+  const Batch& b = B.b;
+  Pool64 tmp;
+  RC(tmp.alloc(b, 2, st));
+  RC(lq_fill64(tmp.v(0), b.total * 12, 12345u, st));
+  RC(lq_fill64(tmp.v(1), b.total * 12, 67890u, st));
+  PoolP q;
+  RC(q.alloc(b, precision, 3, st));
+  RC(lq_convert(64, precision, b, v64(tmp.v(0)), q.v(0), st));
+  RC(lq_convert(64, precision, b, v64(tmp.v(1)), q.v(1), st));
+  const bool clov = L->csw != 0.0;
+  VecP none;
+  for (int w = 0; w < 3; w++)
+    RC(lq_hop_lin(precision, false, clov, lq::RED_NONE, L, b, 1, q.v(0), q.v(1), none, none, q.v(2), -0.25, 1.0, 0.0,
+                  st));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, st));
+  for (int r = 0; r < reps; r++)
+    RC(lq_hop_lin(precision, false, clov, lq::RED_NONE, L, b, 1, q.v(0), q.v(1), none, none, q.v(2), -0.25, 1.0, 0.0,
+                  st));
+  CK(cudaEventRecord(e1, st));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // algorithmic bytes: 3 spinors per system site (x, y read once, out written),
+  // 8 links + the clover block per distinct site of each field's slabs
+  const double S = precision == 64 ? 192.0 : precision == 32 ? 96.0 : 52.0;
+  const double Lk = precision == 64 ? 144.0 : precision == 32 ? 48.0 : 24.0;
+  const double C = clov ? (precision == 64 ? 576.0 : 288.0) : 0.0;
+  double bytes = 0.0, sites = 0.0;
+  std::vector<std::vector<char>> used(L->fields.size(), std::vector<char>(L->dims[0], 0));
+  for (int k = 0; k < n_sys; k++) {
+    bytes += 3.0 * S * (double)B.h_sys[k].n;
+    sites += (double)B.h_sys[k].n;
+    for (int t = doms[k].t0; t <= doms[k].t1; t++) used[field_ids[k]][t] = 1;
+  }
+  for (auto& u : used)
+    for (char c : u)
+      if (c) bytes += (8.0 * Lk + C) * (double)L->S3h;
+  if (ms_per_launch) *ms_per_launch = ms / reps;
+  if (bytes_per_launch) *bytes_per_launch = bytes;
+  if (flops_per_launch) *flops_per_launch = sites * (1320.0 + (clov ? 504.0 : 24.0) + 72.0);
+  return 0;
+}

@@ -1,0 +1,372 @@
+// Wilson hopping term with fused clover / linear-combination epilogues and
+// fused per-system inner products.
+//
+//   (D_hop psi)(x) = sum_mu (1 - g_mu) U_mu(x) psi(x+mu)
+//                         + (1 + g_mu) U_mu(x-mu)^dag psi(x-mu)
+//   D = A - D_hop / 2,  A = 1/(2 kappa) + clover   (2 kappa D = 1 - kappa D_hop)
+//
+// Each (1 +- g_mu) has rank 2, so psi is projected to a half spinor h
+// (2 spins x 3 colours), multiplied by the link (2 SU(3) mat-vecs instead
+// of 4) and expanded back.  D^dag = g5 D g5 swaps the two projectors; A is
+// Hermitian.  A hop whose target lies outside the system's slab is dropped
+// (Dirichlet block operator, the exact sub-block of D); a hop across the
+// time boundary is dropped (open BC) or wraps with sign +-1 when the slab
+// is the whole lattice with periodic / antiperiodic BC.
+#pragma once
+
+#include "common.cuh"
+
+namespace lq {
+
+// h = upper half of (1 + S g_mu) psi.  psi[3*s + c].
+template <int MU, int S, typename R>
+LQ_DI void project(const cx<R> p[12], cx<R> h[6]) {
+  const R s = (R)S;
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    if (MU == 0) {
+      h[c] = p[c] - s * p[6 + c];
+      h[3 + c] = p[3 + c] - s * p[9 + c];
+    } else if (MU == 1) {
+      h[c] = p[c] - s * ti(p[9 + c]);
+      h[3 + c] = p[3 + c] - s * ti(p[6 + c]);
+    } else if (MU == 2) {
+      h[c] = p[c] - s * p[9 + c];
+      h[3 + c] = p[3 + c] + s * p[6 + c];
+    } else {
+      h[c] = p[c] - s * ti(p[6 + c]);
+      h[3 + c] = p[3 + c] + s * ti(p[9 + c]);
+    }
+  }
+}
+
+// acc += (1 + S g_mu) expanded from the transported half spinor w.
+template <int MU, int S, typename R>
+LQ_DI void expand_add(cx<R> acc[12], const cx<R> w[6]) {
+  const R s = (R)S;
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    acc[c] = acc[c] + w[c];
+    acc[3 + c] = acc[3 + c] + w[3 + c];
+    if (MU == 0) {
+      acc[6 + c] = acc[6 + c] - s * w[c];
+      acc[9 + c] = acc[9 + c] - s * w[3 + c];
+    } else if (MU == 1) {
+      acc[6 + c] = acc[6 + c] + s * ti(w[3 + c]);
+      acc[9 + c] = acc[9 + c] + s * ti(w[c]);
+    } else if (MU == 2) {
+      acc[6 + c] = acc[6 + c] + s * w[3 + c];
+      acc[9 + c] = acc[9 + c] - s * w[c];
+    } else {
+      acc[6 + c] = acc[6 + c] + s * ti(w[c]);
+      acc[9 + c] = acc[9 + c] - s * ti(w[3 + c]);
+    }
+  }
+}
+
+template <typename R>
+LQ_DI void mul_u(const su3<R>& u, const cx<R> h[6], cx<R> w[6]) {
+#pragma unroll
+  for (int sp = 0; sp < 2; sp++)
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      cx<R> t = u.m[a][0] * h[3 * sp];
+      fma_c(t, u.m[a][1], h[3 * sp + 1]);
+      fma_c(t, u.m[a][2], h[3 * sp + 2]);
+      w[3 * sp + a] = t;
+    }
+}
+
+template <typename R>
+LQ_DI void mul_udag(const su3<R>& u, const cx<R> h[6], cx<R> w[6]) {
+#pragma unroll
+  for (int sp = 0; sp < 2; sp++)
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      cx<R> t = cmulc(u.m[0][a], h[3 * sp]);
+      fma_cc(t, u.m[1][a], h[3 * sp + 1]);
+      fma_cc(t, u.m[2][a], h[3 * sp + 2]);
+      w[3 * sp + a] = t;
+    }
+}
+
+template <int P, bool DAG, int MU>
+LQ_DI void hop_dir(const Geom& g, const SysDesc& sd, const FieldPtrs& f, int pout, long long cb, const int x[4],
+                   const void* in, const float* inn, cx<typename Prec<P>::R> acc[12]) {
+  typedef typename Prec<P>::R R;
+  constexpr int SF = DAG ? +1 : -1;  // forward projector (1 + SF g_mu)
+  constexpr int SB = -SF;           // backward projector
+  const int pin = pout ^ 1;
+  // ---- forward: U_mu(x) psi(x + mu)
+  {
+    int y[4] = {x[0], x[1], x[2], x[3]};
+    bool ok = true;
+    R sgn = (R)1;
+    if (MU == 0) {
+      if (x[0] == sd.t1) {
+        ok = sd.wrap;
+        y[0] = 0;
+        sgn = (R)sd.tsign;
+      } else {
+        y[0] = x[0] + 1;
+      }
+    } else {
+      y[MU] = (x[MU] + 1 == g.L[MU]) ? 0 : x[MU] + 1;
+    }
+    if (ok) {
+      long long cy = eo_index(g, y);
+      cx<R> psi[12], h[6], w[6];
+      Prec<P>::load(psi, in, inn, sd.n, cy - sd.cb0);
+      project<MU, SF>(psi, h);
+      su3<R> u = LinkIO<P>::load(f, pout, MU, g.Vh, cb);
+      mul_u(u, h, w);
+      if (MU == 0) {
+#pragma unroll
+        for (int k = 0; k < 6; k++) w[k] = sgn * w[k];
+      }
+      expand_add<MU, SF>(acc, w);
+    }
+  }
+  // ---- backward: U_mu(x - mu)^dag psi(x - mu)
+  {
+    int y[4] = {x[0], x[1], x[2], x[3]};
+    bool ok = true;
+    R sgn = (R)1;
+    if (MU == 0) {
+      if (x[0] == sd.t0) {
+        ok = sd.wrap;
+        y[0] = g.L[0] - 1;
+        sgn = (R)sd.tsign;
+      } else {
+        y[0] = x[0] - 1;
+      }
+    } else {
+      y[MU] = (x[MU] == 0) ? g.L[MU] - 1 : x[MU] - 1;
+    }
+    if (ok) {
+      long long cy = eo_index(g, y);
+      cx<R> psi[12], h[6], w[6];
+      Prec<P>::load(psi, in, inn, sd.n, cy - sd.cb0);
+      project<MU, SB>(psi, h);
+      su3<R> u = LinkIO<P>::load(f, pin, MU, g.Vh, cy);
+      mul_udag(u, h, w);
+      if (MU == 0) {
+#pragma unroll
+        for (int k = 0; k < 6; k++) w[k] = sgn * w[k];
+      }
+      expand_add<MU, SB>(acc, w);
+    }
+  }
+}
+
+template <int P, bool DAG>
+LQ_DI void hop_sum(const Geom& g, const SysDesc& sd, const FieldPtrs& f, int pout, long long cb, const int x[4],
+                   const void* in, const float* inn, cx<typename Prec<P>::R> acc[12]) {
+#pragma unroll
+  for (int k = 0; k < 12; k++) acc[k] = {0, 0};
+  hop_dir<P, DAG, 0>(g, sd, f, pout, cb, x, in, inn, acc);
+  hop_dir<P, DAG, 1>(g, sd, f, pout, cb, x, in, inn, acc);
+  hop_dir<P, DAG, 2>(g, sd, f, pout, cb, x, in, inn, acc);
+  hop_dir<P, DAG, 3>(g, sd, f, pout, cb, x, in, inn, acc);
+}
+
+// Clover block apply (A or A^{-1}) on a full spinor.
+template <int P>
+LQ_DI void clover_apply(const FieldPtrs& f, bool inverse, int p, long long Vh, long long cb,
+                        const cx<typename Prec<P>::R> in[12], cx<typename Prec<P>::R> out[12]) {
+  if constexpr (P == 64) {
+    const double2* base = inverse ? f.Ai64 : f.A64 + (long long)p * 36 * Vh;
+    ClovIO<64>::apply(base, Vh, cb, in, out);
+    ClovIO<64>::apply(base + 18 * Vh, Vh, cb, in + 6, out + 6);
+  } else {
+    const float4* base = inverse ? f.Ai32 : f.A32 + (long long)p * 18 * Vh;
+    ClovIO<32>::apply(base, Vh, cb, in, out);
+    ClovIO<32>::apply(base + 9 * Vh, Vh, cb, in + 6, out + 6);
+  }
+}
+
+// Arguments of the hop kernels.  Vector pointers are pool bases; system s
+// uses words [off*NV, (off+n)*NV) of each pool (norms: [off, off+n)).
+struct HopArgs {
+  Geom g;
+  const SysDesc* sys;
+  const FieldPtrs* fields;
+  const int* active;  // per-system flag (NULL: all active)
+  int pout;           // output parity
+  const void* x;      // hop input, parity pout^1
+  const float* xn;
+  const void* y;      // clover-term input, parity pout
+  const float* yn;
+  const void* z;      // additive term, parity pout
+  const float* zn;
+  const void* w;      // inner-product partner (RED_DOT_W)
+  const float* wn;
+  void* out;
+  float* outn;
+  double alpha, beta, gamma, diag;  // see the kernels
+  double* partial;                  // [nsys][nby][4]
+  int nby;
+};
+
+template <int NQ>
+LQ_DI void block_reduce_store(double v[NQ], double* dst) {
+  __shared__ double sh[32][NQ > 0 ? NQ : 1];
+#pragma unroll
+  for (int q = 0; q < NQ; q++)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < NQ; q++) sh[wid][q] = v[q];
+  __syncthreads();
+  if (wid == 0) {
+    int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NQ; q++) {
+      double t = lane < nw ? sh[lane][q] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+      if (lane == 0) dst[q] = t;
+    }
+  }
+}
+
+template <int P>
+LQ_DI const void* sys_ptr(const void* pool, long long off) {
+  return pool ? (const void*)((const char*)pool + off * (long long)Prec<P>::NV * 16) : nullptr;
+}
+template <int P>
+LQ_DI void* sys_ptr_w(void* pool, long long off) {
+  return pool ? (void*)((char*)pool + off * (long long)Prec<P>::NV * 16) : nullptr;
+}
+LQ_DI const float* nrm_ptr(const float* pool, long long off) { return pool ? pool + off : nullptr; }
+LQ_DI float* nrm_ptr_w(float* pool, long long off) { return pool ? pool + off : nullptr; }
+
+// out = beta * A(y) + alpha * D_hop x + gamma * z   on parity pout
+// (A = diag * 1 without clover; a term is skipped when its coefficient is 0),
+// with an optional fused per-system reduction:
+//   RED_DOT_W: <w, out> (slots 0,1);  RED_TS: <out, y> (0,1) and |out|^2 (2);
+//   RED_NORM: |out|^2 (slot 2).
+template <int P, bool DAG, bool CLOV, int RED>
+__global__ void __launch_bounds__(128) k_hop_lin(HopArgs a) {
+  typedef typename Prec<P>::R R;
+  const int s = blockIdx.x;
+  if (a.active && !a.active[s]) return;
+  const SysDesc sd = a.sys[s];
+  const long long j = (long long)blockIdx.y * blockDim.x + threadIdx.x;
+  if ((long long)blockIdx.y * blockDim.x >= sd.n) return;  // whole block beyond this system
+  const FieldPtrs f = a.fields[sd.field];
+  double red[3] = {0.0, 0.0, 0.0};
+  if (j < sd.n) {
+    const long long cb = sd.cb0 + j;
+    int x[4];
+    eo_coords(a.g, cb, a.pout, x);
+    const void* xin = sys_ptr<P>(a.x, sd.off);
+    const float* xinn = nrm_ptr(a.xn, sd.off);
+    cx<R> res[12];
+    if (a.alpha != 0.0) {
+      cx<R> acc[12];
+      hop_sum<P, DAG>(a.g, sd, f, a.pout, cb, x, xin, xinn, acc);
+#pragma unroll
+      for (int k = 0; k < 12; k++) res[k] = (R)a.alpha * acc[k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 12; k++) res[k] = {0, 0};
+    }
+    cx<R> yv[12];
+    if (a.beta != 0.0 || RED == RED_TS) Prec<P>::load(yv, sys_ptr<P>(a.y, sd.off), nrm_ptr(a.yn, sd.off), sd.n, j);
+    if (a.beta != 0.0) {
+      cx<R> ay[12];
+      if (CLOV) {
+        clover_apply<P>(f, false, a.pout, a.g.Vh, cb, yv, ay);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 12; k++) ay[k] = (R)a.diag * yv[k];
+      }
+#pragma unroll
+      for (int k = 0; k < 12; k++) res[k] = res[k] + (R)a.beta * ay[k];
+    }
+    if (a.gamma != 0.0) {
+      cx<R> zv[12];
+      Prec<P>::load(zv, sys_ptr<P>(a.z, sd.off), nrm_ptr(a.zn, sd.off), sd.n, j);
+#pragma unroll
+      for (int k = 0; k < 12; k++) res[k] = res[k] + (R)a.gamma * zv[k];
+    }
+    Prec<P>::store(sys_ptr_w<P>(a.out, sd.off), nrm_ptr_w(a.outn, sd.off), sd.n, j, res);
+    if (RED != RED_NONE) {
+      cx<R> r2[12];
+      if (P == 16) {  // reduce over the stored (rounded) values
+        Prec<P>::load(r2, sys_ptr<P>(a.out, sd.off), nrm_ptr(a.outn, sd.off), sd.n, j);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 12; k++) r2[k] = res[k];
+      }
+      if (RED == RED_DOT_W) {
+        cx<R> wv[12];
+        Prec<P>::load(wv, sys_ptr<P>(a.w, sd.off), nrm_ptr(a.wn, sd.off), sd.n, j);
+#pragma unroll
+        for (int k = 0; k < 12; k++) {
+          red[0] += (double)wv[k].re * r2[k].re + (double)wv[k].im * r2[k].im;
+          red[1] += (double)wv[k].re * r2[k].im - (double)wv[k].im * r2[k].re;
+        }
+      } else if (RED == RED_TS) {
+#pragma unroll
+        for (int k = 0; k < 12; k++) {
+          red[0] += (double)r2[k].re * yv[k].re + (double)r2[k].im * yv[k].im;
+          red[1] += (double)r2[k].re * yv[k].im - (double)r2[k].im * yv[k].re;
+          red[2] += (double)r2[k].re * r2[k].re + (double)r2[k].im * r2[k].im;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 12; k++) red[2] += (double)r2[k].re * r2[k].re + (double)r2[k].im * r2[k].im;
+      }
+    }
+  }
+  if (RED != RED_NONE) {
+    block_reduce_store<3>(red, a.partial + ((long long)s * a.nby + blockIdx.y) * 4);
+  }
+}
+
+// out = A^{-1} (alpha * D_hop x + beta * y) on even sites (pout = 0), with
+// A^{-1} = 1/diag without clover.
+template <int P, bool DAG, bool CLOV>
+__global__ void __launch_bounds__(128) k_hop_clinv(HopArgs a) {
+  typedef typename Prec<P>::R R;
+  const int s = blockIdx.x;
+  if (a.active && !a.active[s]) return;
+  const SysDesc sd = a.sys[s];
+  const long long j = (long long)blockIdx.y * blockDim.x + threadIdx.x;
+  if (j >= sd.n) return;
+  const FieldPtrs f = a.fields[sd.field];
+  const long long cb = sd.cb0 + j;
+  int x[4];
+  eo_coords(a.g, cb, a.pout, x);
+  cx<R> res[12];
+  if (a.alpha != 0.0) {
+    cx<R> acc[12];
+    hop_sum<P, DAG>(a.g, sd, f, a.pout, cb, x, sys_ptr<P>(a.x, sd.off), nrm_ptr(a.xn, sd.off), acc);
+#pragma unroll
+    for (int k = 0; k < 12; k++) res[k] = (R)a.alpha * acc[k];
+  } else {
+#pragma unroll
+    for (int k = 0; k < 12; k++) res[k] = {0, 0};
+  }
+  if (a.beta != 0.0) {
+    cx<R> yv[12];
+    Prec<P>::load(yv, sys_ptr<P>(a.y, sd.off), nrm_ptr(a.yn, sd.off), sd.n, j);
+#pragma unroll
+    for (int k = 0; k < 12; k++) res[k] = res[k] + (R)a.beta * yv[k];
+  }
+  cx<R> o[12];
+  if (CLOV) {
+    clover_apply<P>(f, true, 0, a.g.Vh, cb, res, o);
+  } else {
+    const R inv = (R)(1.0 / a.diag);
+#pragma unroll
+    for (int k = 0; k < 12; k++) o[k] = inv * res[k];
+  }
+  Prec<P>::store(sys_ptr_w<P>(a.out, sd.off), nrm_ptr_w(a.outn, sd.off), sd.n, j, o);
+}
+
+}  // namespace lq

@@ -1,0 +1,99 @@
+// Internal interfaces of the library: the lattice object, batches of
+// systems and the host launchers of the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/lqcd.h"
+#include "common.cuh"
+
+void lq_count_launch();
+void lq_set_error(const std::string& msg);
+
+// A vector of a batch in one precision: pool base (and FP16 norm pool).
+struct VecP {
+  void* d = nullptr;
+  float* nrm = nullptr;
+};
+
+// Device view of a batch of systems: descriptors, activity flags, iteration
+// scalars and the block-partial buffer of the fused reductions.
+struct Batch {
+  int nsys = 0;
+  int nby = 0;               // site blocks of the largest system
+  long long max_n = 0;
+  long long total = 0;       // sum of n over systems (sites per parity)
+  const lq::SysDesc* sys = nullptr;
+  int* active = nullptr;
+  lq::SolverScal* sc = nullptr;
+  double* partial = nullptr;
+};
+
+constexpr int LQ_BLOCK = 128;
+
+struct FieldData {
+  double2* Unat = nullptr;  // natural-order copy of U (FP64), used by the force
+  double2* U64 = nullptr;
+  float4* U32 = nullptr;
+  uint2* U16 = nullptr;
+  double2* A64 = nullptr;
+  double2* Ai64 = nullptr;
+  float4* A32 = nullptr;
+  float4* Ai32 = nullptr;
+};
+
+struct lqcd_lattice {
+  int dims[4];
+  int bc;
+  long long V, Vh, S3, S3h;
+  lq::Geom g;
+  double kappa = 0.125, csw = 0.0;
+  std::vector<FieldData> fields;
+  lq::FieldPtrs* d_fields = nullptr;
+  int device = 0;
+};
+
+// ---------------------------------------------------------------- launchers
+int lq_launch_pack_links(const lq::Geom& g, const double2* U, double2* U64, float4* U32, uint2* U16,
+                         unsigned long long* maxdev, cudaStream_t st);
+int lq_launch_clover(const lq::Geom& g, const double2* U, double kappa, double csw, double2* A64, double2* Ai64,
+                     float4* A32, float4* Ai32, int* fail, cudaStream_t st);
+
+// out = beta*A(y) + alpha*D_hop x + gamma*z on parity pout (+ fused reduction)
+int lq_hop_lin(int P, bool dag, bool clov, int red, const lqcd_lattice* L, const Batch& b, int pout, VecP x, VecP y,
+               VecP z, VecP w, VecP out, double alpha, double beta, double gamma, cudaStream_t st);
+// out = A^{-1}(alpha*D_hop x + beta*y) on even sites
+int lq_hop_clinv(int P, bool dag, bool clov, const lqcd_lattice* L, const Batch& b, VecP x, VecP y, VecP out,
+                 double alpha, double beta, cudaStream_t st);
+
+int lq_bicg_s(int P, const Batch& b, VecP r, VecP v, VecP s, cudaStream_t st);
+int lq_bicg_xr(int P, const Batch& b, VecP x, VecP p, VecP s, VecP t, VecP r, VecP r0, cudaStream_t st);
+int lq_bicg_p(int P, const Batch& b, VecP p, VecP r, VecP v, cudaStream_t st);
+int lq_inner_init(int P, const Batch& b, const double2* r64, VecP r, VecP r0, VecP p, VecP x, cudaStream_t st);
+int lq_accum64(int P, const Batch& b, double2* x64, VecP x, cudaStream_t st);
+int lq_norm2_64(const Batch& b, const double2* v, cudaStream_t st);
+int lq_finalize(int mode, const Batch& b, double tau2, double floor_rel2, cudaStream_t st);
+int lq_count_active(const Batch& b, int* d_count, cudaStream_t st);
+int lq_convert(int Pin, int Pout, const Batch& b, VecP in, VecP out, cudaStream_t st);
+
+// layout conversion: natural complex128 slab vectors <-> even-odd FP64 pools
+int lq_nat_to_eo(const lqcd_lattice* L, const Batch& b, const double2* const* src, double2* ve, double2* vo,
+                 cudaStream_t st);
+int lq_eo_to_nat(const lqcd_lattice* L, const Batch& b, const double2* ve, const double2* vo, double2* const* dst,
+                 double scale, cudaStream_t st);
+// point sources: system k gets the unit vector of column cols[k] at x_src
+int lq_point_source(const lqcd_lattice* L, const Batch& b, const int* d_cols, const int x_src[4], double2* ve,
+                    double2* vo, cudaStream_t st);
+// chi(y) = [D_{Gamma*,Gamma} psi](y): time hops from y in Gamma* into Gamma
+int lq_boundary_hop(const lqcd_lattice* L, const Batch& bout, const Batch& bin, int g1, const double2* in_e,
+                    const double2* in_o, double2* out_e, double2* out_o, cudaStream_t st);
+// a -= b elementwise over n double2 words
+int lq_sub_inplace(double2* a, const double2* b, long long n, cudaStream_t st);
+
+// force
+int lq_force(const lqcd_lattice* L, int field, const lqcd_slab& dom, const double2* X, const double2* Y, double* F,
+             cudaStream_t st);
+int lq_fill64(double2* p, long long n, unsigned seed, cudaStream_t st);

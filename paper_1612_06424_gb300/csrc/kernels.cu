@@ -1,0 +1,354 @@
+// Host launchers for the stencil and vector kernels, plus the layout
+// kernels (natural <-> even-odd), point sources and the boundary hop of
+// the Schur-complement assembly.
+#include <atomic>
+
+#include "blas.cuh"
+#include "internal.h"
+
+using namespace lq;
+
+static std::atomic<long long> g_launches{0};
+void lq_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+extern "C" long long lqcd_kernel_launches(void) { return g_launches.load(); }
+
+static inline dim3 grid_of(const Batch& b) { return dim3((unsigned)b.nsys, (unsigned)b.nby, 1); }
+
+static inline int launched() {
+  lq_count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    lq_set_error(std::string("kernel launch: ") + cudaGetErrorString(e));
+    return LQCD_ECUDA;
+  }
+  return 0;
+}
+
+static HopArgs hop_args(const lqcd_lattice* L, const Batch& b, int pout) {
+  HopArgs a{};
+  a.g = L->g;
+  a.sys = b.sys;
+  a.fields = L->d_fields;
+  a.active = b.active;
+  a.pout = pout;
+  a.partial = b.partial;
+  a.nby = b.nby;
+  a.diag = 1.0 / (2.0 * L->kappa);
+  return a;
+}
+
+template <int P, bool DAG, bool CLOV>
+static void launch_lin(int red, dim3 gr, const HopArgs& a, cudaStream_t st) {
+  switch (red) {
+    case RED_NONE: k_hop_lin<P, DAG, CLOV, RED_NONE><<<gr, LQ_BLOCK, 0, st>>>(a); break;
+    case RED_DOT_W: k_hop_lin<P, DAG, CLOV, RED_DOT_W><<<gr, LQ_BLOCK, 0, st>>>(a); break;
+    case RED_TS: k_hop_lin<P, DAG, CLOV, RED_TS><<<gr, LQ_BLOCK, 0, st>>>(a); break;
+    default: k_hop_lin<P, DAG, CLOV, RED_NORM><<<gr, LQ_BLOCK, 0, st>>>(a); break;
+  }
+}
+
+template <int P>
+static void launch_lin_p(bool dag, bool clov, int red, dim3 gr, const HopArgs& a, cudaStream_t st) {
+  if (dag) {
+    if (clov) launch_lin<P, true, true>(red, gr, a, st);
+    else launch_lin<P, true, false>(red, gr, a, st);
+  } else {
+    if (clov) launch_lin<P, false, true>(red, gr, a, st);
+    else launch_lin<P, false, false>(red, gr, a, st);
+  }
+}
+
+int lq_hop_lin(int P, bool dag, bool clov, int red, const lqcd_lattice* L, const Batch& b, int pout, VecP x, VecP y,
+               VecP z, VecP w, VecP out, double alpha, double beta, double gamma, cudaStream_t st) {
+  HopArgs a = hop_args(L, b, pout);
+  a.x = x.d; a.xn = x.nrm;
+  a.y = y.d; a.yn = y.nrm;
+  a.z = z.d; a.zn = z.nrm;
+  a.w = w.d; a.wn = w.nrm;
+  a.out = out.d; a.outn = out.nrm;
+  a.alpha = alpha; a.beta = beta; a.gamma = gamma;
+  dim3 gr = grid_of(b);
+  if (P == 64) launch_lin_p<64>(dag, clov, red, gr, a, st);
+  else if (P == 32) launch_lin_p<32>(dag, clov, red, gr, a, st);
+  else launch_lin_p<16>(dag, clov, red, gr, a, st);
+  return launched();
+}
+
+template <int P>
+static void launch_clinv_p(bool dag, bool clov, dim3 gr, const HopArgs& a, cudaStream_t st) {
+  if (dag) {
+    if (clov) k_hop_clinv<P, true, true><<<gr, LQ_BLOCK, 0, st>>>(a);
+    else k_hop_clinv<P, true, false><<<gr, LQ_BLOCK, 0, st>>>(a);
+  } else {
+    if (clov) k_hop_clinv<P, false, true><<<gr, LQ_BLOCK, 0, st>>>(a);
+    else k_hop_clinv<P, false, false><<<gr, LQ_BLOCK, 0, st>>>(a);
+  }
+}
+
+int lq_hop_clinv(int P, bool dag, bool clov, const lqcd_lattice* L, const Batch& b, VecP x, VecP y, VecP out,
+                 double alpha, double beta, cudaStream_t st) {
+  HopArgs a = hop_args(L, b, 0);
+  a.x = x.d; a.xn = x.nrm;
+  a.y = y.d; a.yn = y.nrm;
+  a.out = out.d; a.outn = out.nrm;
+  a.alpha = alpha; a.beta = beta;
+  dim3 gr = grid_of(b);
+  if (P == 64) launch_clinv_p<64>(dag, clov, gr, a, st);
+  else if (P == 32) launch_clinv_p<32>(dag, clov, gr, a, st);
+  else launch_clinv_p<16>(dag, clov, gr, a, st);
+  return launched();
+}
+
+static VecArgs vec_args(const Batch& b) {
+  VecArgs v;
+  v.sys = b.sys;
+  v.active = b.active;
+  v.sc = b.sc;
+  v.partial = b.partial;
+  v.nby = b.nby;
+  return v;
+}
+
+#define LQ_DISPATCH_P(P, CALL) \
+  do {                          \
+    if ((P) == 64) {            \
+      constexpr int PP = 64;    \
+      CALL;                     \
+    } else if ((P) == 32) {     \
+      constexpr int PP = 32;    \
+      CALL;                     \
+    } else {                    \
+      constexpr int PP = 16;    \
+      CALL;                     \
+    }                           \
+  } while (0)
+
+int lq_bicg_s(int P, const Batch& b, VecP r, VecP v, VecP s, cudaStream_t st) {
+  VecArgs va = vec_args(b);
+  LQ_DISPATCH_P(P, (k_bicg_s<PP><<<grid_of(b), LQ_BLOCK, 0, st>>>(va, r.d, r.nrm, v.d, v.nrm, s.d, s.nrm)));
+  return launched();
+}
+
+int lq_bicg_xr(int P, const Batch& b, VecP x, VecP p, VecP s, VecP t, VecP r, VecP r0, cudaStream_t st) {
+  VecArgs va = vec_args(b);
+  LQ_DISPATCH_P(P, (k_bicg_xr<PP><<<grid_of(b), LQ_BLOCK, 0, st>>>(va, x.d, x.nrm, p.d, p.nrm, s.d, s.nrm, t.d,
+                                                                    t.nrm, r.d, r.nrm, r0.d, r0.nrm)));
+  return launched();
+}
+
+int lq_bicg_p(int P, const Batch& b, VecP p, VecP r, VecP v, cudaStream_t st) {
+  VecArgs va = vec_args(b);
+  LQ_DISPATCH_P(P, (k_bicg_p<PP><<<grid_of(b), LQ_BLOCK, 0, st>>>(va, p.d, p.nrm, r.d, r.nrm, v.d, v.nrm)));
+  return launched();
+}
+
+int lq_inner_init(int P, const Batch& b, const double2* r64, VecP r, VecP r0, VecP p, VecP x, cudaStream_t st) {
+  VecArgs va = vec_args(b);
+  LQ_DISPATCH_P(P, (k_inner_init<PP><<<grid_of(b), LQ_BLOCK, 0, st>>>(va, r64, r.d, r.nrm, r0.d, r0.nrm, p.d, p.nrm,
+                                                                       x.d, x.nrm)));
+  return launched();
+}
+
+int lq_accum64(int P, const Batch& b, double2* x64, VecP x, cudaStream_t st) {
+  VecArgs va = vec_args(b);
+  LQ_DISPATCH_P(P, (k_accum64<PP><<<grid_of(b), LQ_BLOCK, 0, st>>>(va, x64, x.d, x.nrm)));
+  return launched();
+}
+
+int lq_norm2_64(const Batch& b, const double2* v, cudaStream_t st) {
+  k_norm2_64<<<grid_of(b), LQ_BLOCK, 0, st>>>(vec_args(b), v);
+  return launched();
+}
+
+int lq_finalize(int mode, const Batch& b, double tau2, double floor_rel2, cudaStream_t st) {
+  const int warps = 8;
+  k_finalize<<<(b.nsys + warps - 1) / warps, warps * 32, 0, st>>>(mode, b.nsys, b.sys, b.active, b.sc, b.partial, b.nby,
+                                                                  LQ_BLOCK, tau2, floor_rel2);
+  return launched();
+}
+
+int lq_count_active(const Batch& b, int* d_count, cudaStream_t st) {
+  k_count_active<<<1, 256, 0, st>>>(b.nsys, b.active, d_count);
+  return launched();
+}
+
+int lq_convert(int Pin, int Pout, const Batch& b, VecP in, VecP out, cudaStream_t st) {
+  VecArgs va = vec_args(b);
+  dim3 gr = grid_of(b);
+  if (Pin == 64 && Pout == 32) k_convert<64, 32><<<gr, LQ_BLOCK, 0, st>>>(va, in.d, in.nrm, out.d, out.nrm);
+  else if (Pin == 64 && Pout == 16) k_convert<64, 16><<<gr, LQ_BLOCK, 0, st>>>(va, in.d, in.nrm, out.d, out.nrm);
+  else if (Pin == 32 && Pout == 64) k_convert<32, 64><<<gr, LQ_BLOCK, 0, st>>>(va, in.d, in.nrm, out.d, out.nrm);
+  else if (Pin == 16 && Pout == 64) k_convert<16, 64><<<gr, LQ_BLOCK, 0, st>>>(va, in.d, in.nrm, out.d, out.nrm);
+  else k_convert<64, 64><<<gr, LQ_BLOCK, 0, st>>>(va, in.d, in.nrm, out.d, out.nrm);
+  return launched();
+}
+
+// ------------------------------------------------------------ layout kernels
+// Natural slab vector of system s (src[s], sites t0*S3 .. (t1+1)*S3 - 1)
+// <-> the system's even and odd FP64 vectors.
+__global__ void __launch_bounds__(128) k_nat_to_eo(Geom g, const SysDesc* sys, const int* active,
+                                                   const double2* const* src, double2* ve, double2* vo) {
+  const int s = blockIdx.x;
+  if (active && !active[s]) return;
+  const SysDesc sd = sys[s];
+  const long long j = (long long)blockIdx.y * blockDim.x + threadIdx.x;
+  if (j >= sd.n) return;
+  const int p = blockIdx.z;
+  int x[4];
+  eo_coords(g, sd.cb0 + j, p, x);
+  const long long nat = ((((long long)x[0] * g.L[1] + x[1]) * g.L[2] + x[2]) * g.L[3] + x[3]);
+  const long long loc = nat - (long long)sd.t0 * (2 * g.S3h);
+  const double2* in = src[s] + loc * 12;
+  double2* out = (p == 0 ? ve : vo) + sd.off * 12;
+#pragma unroll
+  for (int k = 0; k < 12; k++) out[k * sd.n + j] = in[k];
+}
+
+__global__ void __launch_bounds__(128) k_eo_to_nat(Geom g, const SysDesc* sys, const double2* ve, const double2* vo,
+                                                   double2* const* dst, double scale) {
+  const int s = blockIdx.x;
+  const SysDesc sd = sys[s];
+  const long long j = (long long)blockIdx.y * blockDim.x + threadIdx.x;
+  if (j >= sd.n) return;
+  const int p = blockIdx.z;
+  int x[4];
+  eo_coords(g, sd.cb0 + j, p, x);
+  const long long nat = ((((long long)x[0] * g.L[1] + x[1]) * g.L[2] + x[2]) * g.L[3] + x[3]);
+  const long long loc = nat - (long long)sd.t0 * (2 * g.S3h);
+  double2* out = dst[s] + loc * 12;
+  const double2* in = (p == 0 ? ve : vo) + sd.off * 12;
+#pragma unroll
+  for (int k = 0; k < 12; k++) {
+    double2 v = in[k * sd.n + j];
+    out[k] = make_double2(scale * v.x, scale * v.y);
+  }
+}
+
+int lq_nat_to_eo(const lqcd_lattice* L, const Batch& b, const double2* const* src, double2* ve, double2* vo,
+                 cudaStream_t st) {
+  k_nat_to_eo<<<dim3(b.nsys, b.nby, 2), LQ_BLOCK, 0, st>>>(L->g, b.sys, nullptr, src, ve, vo);
+  return launched();
+}
+
+int lq_eo_to_nat(const lqcd_lattice* L, const Batch& b, const double2* ve, const double2* vo, double2* const* dst,
+                 double scale, cudaStream_t st) {
+  k_eo_to_nat<<<dim3(b.nsys, b.nby, 2), LQ_BLOCK, 0, st>>>(L->g, b.sys, ve, vo, dst, scale);
+  return launched();
+}
+
+// Zero both parities of every system and place 1 at (x_src, column cols[s]).
+__global__ void __launch_bounds__(128) k_point_source(Geom g, const SysDesc* sys, const int* cols, int xs0, int xs1,
+                                                      int xs2, int xs3, double2* ve, double2* vo) {
+  const int s = blockIdx.x;
+  const SysDesc sd = sys[s];
+  const long long j = (long long)blockIdx.y * blockDim.x + threadIdx.x;
+  if (j >= sd.n) return;
+  const int p = blockIdx.z;
+  const int xs[4] = {xs0, xs1, xs2, xs3};
+  const int ps = (xs0 + xs1 + xs2 + xs3) & 1;
+  const long long cbs = eo_index(g, xs);
+  double2* out = (p == 0 ? ve : vo) + sd.off * 12;
+  const bool here = (p == ps) && (sd.cb0 + j == cbs);
+#pragma unroll
+  for (int k = 0; k < 12; k++) out[k * sd.n + j] = make_double2((here && k == cols[s]) ? 1.0 : 0.0, 0.0);
+}
+
+int lq_point_source(const lqcd_lattice* L, const Batch& b, const int* d_cols, const int x_src[4], double2* ve,
+                    double2* vo, cudaStream_t st) {
+  k_point_source<<<dim3(b.nsys, b.nby, 2), LQ_BLOCK, 0, st>>>(L->g, b.sys, d_cols, x_src[0], x_src[1], x_src[2],
+                                                              x_src[3], ve, vo);
+  return launched();
+}
+
+// chi = P_{Gamma*} D P_{Gamma} psi for Gamma = 0..g1, Gamma* = g1+1..T-1:
+// only the time hops from a site y of Gamma* to a site of Gamma survive,
+//   y0 = g1+1 :   -1/2 (1 + g_0) U_0(y-0)^dag psi(y-0)
+//   y0 = T-1  :   -1/2 (1 - g_0) U_0(y) psi(y+0) * sign  (periodic / antiperiodic only)
+// Output systems (Gamma*) and input systems (the Gammabar solutions) are
+// paired by index.
+__global__ void __launch_bounds__(128) k_boundary_hop(Geom g, const FieldPtrs* fields, const SysDesc* sout,
+                                                      const SysDesc* sin, int g1, const double2* in_e,
+                                                      const double2* in_o, double2* out_e, double2* out_o) {
+  const int s = blockIdx.x;
+  const SysDesc so = sout[s], si = sin[s];
+  const long long j = (long long)blockIdx.y * blockDim.x + threadIdx.x;
+  if (j >= so.n) return;
+  const int p = blockIdx.z;
+  const FieldPtrs f = fields[so.field];
+  int x[4];
+  const long long cb = so.cb0 + j;
+  eo_coords(g, cb, p, x);
+  cx<double> acc[12];
+#pragma unroll
+  for (int k = 0; k < 12; k++) acc[k] = {0.0, 0.0};
+  const double2* inb = (p == 0 ? in_o : in_e) + si.off * 12;  // neighbour parity
+  if (x[0] == g1 + 1) {
+    int y[4] = {x[0] - 1, x[1], x[2], x[3]};
+    const long long cy = eo_index(g, y);
+    cx<double> psi[12], h[6], w[6];
+    Prec<64>::load(psi, inb, nullptr, si.n, cy - si.cb0);
+    project<0, +1>(psi, h);
+    su3<double> u = LinkIO<64>::load(f, p ^ 1, 0, g.Vh, cy);
+    mul_udag(u, h, w);
+    expand_add<0, +1>(acc, w);
+  }
+  if (g.bc_t != 0 && x[0] == g.L[0] - 1) {
+    const double sg = g.bc_t == 2 ? -1.0 : 1.0;
+    int y[4] = {0, x[1], x[2], x[3]};
+    const long long cy = eo_index(g, y);
+    cx<double> psi[12], h[6], w[6];
+    Prec<64>::load(psi, inb, nullptr, si.n, cy - si.cb0);
+    project<0, -1>(psi, h);
+    su3<double> u = LinkIO<64>::load(f, p, 0, g.Vh, cb);
+    mul_u(u, h, w);
+#pragma unroll
+    for (int k = 0; k < 6; k++) w[k] = sg * w[k];
+    expand_add<0, -1>(acc, w);
+  }
+#pragma unroll
+  for (int k = 0; k < 12; k++) acc[k] = -0.5 * acc[k];
+  Prec<64>::store((p == 0 ? out_e : out_o) + so.off * 12, nullptr, so.n, j, acc);
+}
+
+int lq_boundary_hop(const lqcd_lattice* L, const Batch& bout, const Batch& bin, int g1, const double2* in_e,
+                    const double2* in_o, double2* out_e, double2* out_o, cudaStream_t st) {
+  k_boundary_hop<<<dim3(bout.nsys, bout.nby, 2), LQ_BLOCK, 0, st>>>(L->g, L->d_fields, bout.sys, bin.sys, g1, in_e,
+                                                                    in_o, out_e, out_o);
+  return launched();
+}
+
+__global__ void k_sub_inplace(double2* a, const double2* b, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double2 x = a[i], y = b[i];
+    a[i] = make_double2(x.x - y.x, x.y - y.y);
+  }
+}
+
+int lq_sub_inplace(double2* a, const double2* b, long long n, cudaStream_t st) {
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_sub_inplace<<<(unsigned)blocks, 256, 0, st>>>(a, b, n);
+  return launched();
+}
+
+// Deterministic pseudo-random fill in [-1, 1) (a hash of the word index).
+__global__ void k_fill64(double2* p, long long n, unsigned seed) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    unsigned long long h = (unsigned long long)i * 0x9E3779B97F4A7C15ull + seed;
+    h ^= h >> 33;
+    h *= 0xff51afd7ed558ccdull;
+    h ^= h >> 33;
+    h *= 0xc4ceb9fe1a85ec53ull;
+    h ^= h >> 33;
+    const double a = (double)(h & 0xffffffffull) * (2.0 / 4294967296.0) - 1.0;
+    const double b = (double)(h >> 32) * (2.0 / 4294967296.0) - 1.0;
+    p[i] = make_double2(a, b);
+  }
+}
+
+int lq_fill64(double2* p, long long n, unsigned seed, cudaStream_t st) {
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_fill64<<<(unsigned)blocks, 256, 0, st>>>(p, n, seed);
+  return launched();
+}

@@ -1,0 +1,258 @@
+"""Thin Python binding of the C ABI in include/lqcd.h (argument marshalling only).
+
+Every operation runs in the CUDA library ``lib/liblqcd.so``; this module
+only converts torch tensors to device pointers, structs and error codes.
+There is no CPU fallback: importing the binding without the built library,
+or calling it without a CUDA device, raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "liblqcd.so")
+
+BC = {"open": 0, "periodic": 1, "antiperiodic": 2}
+
+ERRORS = {
+    -1: "EBADARG", -2: "ENOMEM", -3: "ENONUNITARY", -4: "ENOTCONVERGED",
+    -5: "EBREAKDOWN", -6: "ENAN", -7: "ECUDA", -8: "ENOFIELD",
+}
+
+
+class LQCDError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Slab(ctypes.Structure):
+    _fields_ = [("t0", ctypes.c_int), ("t1", ctypes.c_int)]
+
+
+class SplitC(ctypes.Structure):
+    _fields_ = [("gamma", Slab), ("delta", Slab), ("gamma_star", Slab)]
+
+
+class ParamsC(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
+                ("inner_tol", ctypes.c_double), ("check_every", ctypes.c_int)]
+
+
+class StatsC(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("cycles", ctypes.c_int), ("status", ctypes.c_int),
+                ("true_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+@dataclass
+class SolverParams:
+    tol: float = 1e-10
+    max_iter: int = 100000
+    precision: int = 64
+    inner_tol: float = 0.0
+    check_every: int = 0
+
+    def c(self) -> ParamsC:
+        return ParamsC(self.tol, self.max_iter, self.precision, self.inner_tol, self.check_every)
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load liblqcd.so (built by __graft_entry__.build() / build.py); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"CUDA library not built: {LIB_PATH} missing (run __graft_entry__.build())")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, ip, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
+    c = ctypes.c_int
+    L.lqcd_create_lattice.argtypes = [ip, c, ctypes.POINTER(vp)]
+    L.lqcd_destroy_lattice.argtypes = [vp]
+    L.lqcd_set_gauge.argtypes = [vp, c, vp, ctypes.c_double, ctypes.c_double, c, vp]
+    L.lqcd_dslash.argtypes = [vp, c, ctypes.POINTER(Slab), c, c, vp, vp, vp]
+    L.lqcd_solve_block.argtypes = [vp, c, ctypes.POINTER(Slab), ip, vp, vp, ctypes.POINTER(ParamsC),
+                                   ctypes.POINTER(StatsC), vp]
+    L.lqcd_solve_full.argtypes = [vp, c, ip, vp, vp, ctypes.POINTER(ParamsC), ctypes.POINTER(StatsC), vp]
+    L.lqcd_factorized_propagator.argtypes = [vp, ctypes.POINTER(SplitC), ip, c, vp, vp, ctypes.POINTER(ParamsC),
+                                             ctypes.POINTER(StatsC), vp]
+    L.lqcd_link_force.argtypes = [vp, ctypes.POINTER(Slab), c, vp, vp, dp, ctypes.POINTER(ParamsC),
+                                  ctypes.POINTER(StatsC), vp]
+    L.lqcd_dslash_bench.argtypes = [vp, c, ctypes.POINTER(Slab), ip, c, c, dp, dp, dp, vp]
+    L.lqcd_last_error.restype = ctypes.c_char_p
+    L.lqcd_kernel_launches.restype = ctypes.c_longlong
+    _lib = L
+    return L
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise LQCDError(rc, lib().lqcd_last_error().decode())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t: torch.Tensor, name: str) -> ctypes.c_void_p:
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.complex128 and t.is_contiguous()):
+        raise TypeError(f"{name}: need a contiguous complex128 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def kernel_launches() -> int:
+    return int(lib().lqcd_kernel_launches())
+
+
+class Lattice:
+    """A lattice T x L1 x L2 x L3 (time first) with its gauge fields on the current GPU."""
+
+    def __init__(self, dims, bc: str = "open"):
+        if not torch.cuda.is_available():
+            raise RuntimeError("lqcd: a CUDA device is required (no CPU fallback)")
+        self.dims = tuple(int(d) for d in dims)
+        self.T = self.dims[0]
+        self.S3 = self.dims[1] * self.dims[2] * self.dims[3]
+        self.V = self.T * self.S3
+        self.bc = bc
+        h = ctypes.c_void_p()
+        _check(lib().lqcd_create_lattice((ctypes.c_int * 4)(*self.dims), BC[bc], ctypes.byref(h)))
+        self._h = h
+        self.n_fields = 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().lqcd_destroy_lattice(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- fields
+    def set_gauge(self, U, kappa: float, csw: float = 0.0, stream=None):
+        """U: complex128 [n_fields, V, 4, 3, 3] (or [V, 4, 3, 3]) as numpy (host) or CUDA tensor."""
+        if isinstance(U, np.ndarray):
+            arr = np.ascontiguousarray(U, dtype=np.complex128)
+            n = arr.size // (self.V * 36)
+            _check(lib().lqcd_set_gauge(self._h, n, ctypes.c_void_p(arr.ctypes.data), kappa, csw, 1, _stream(stream)))
+        else:
+            n = U.numel() // (self.V * 36)
+            _check(lib().lqcd_set_gauge(self._h, n, _dev(U.contiguous(), "U"), kappa, csw, 0, _stream(stream)))
+        self.n_fields = n
+        self.kappa, self.csw = kappa, csw
+
+    # ------------------------------------------------------------- operators
+    def slab_len(self, t0: int, t1: int) -> int:
+        return (t1 - t0 + 1) * self.S3
+
+    def dslash(self, psi: torch.Tensor, field: int = 0, dom=None, dagger: bool = False, precision: int = 64,
+               stream=None) -> torch.Tensor:
+        """D_L psi on the slab dom=(t0, t1) (None: whole lattice); psi [sites_of_slab, 4, 3]."""
+        out = torch.empty_like(psi)
+        sl = ctypes.byref(Slab(*dom)) if dom is not None else None
+        _check(lib().lqcd_dslash(self._h, field, sl, int(dagger), precision, _dev(psi, "psi"), _dev(out, "out"),
+                                 _stream(stream)))
+        return out
+
+    def solve_block(self, src: torch.Tensor, doms, field_ids, params: SolverParams | None = None, stream=None):
+        """Batched D_{L_k} psi_k = eta_k; src = slab vectors back to back (complex128, CUDA)."""
+        n = len(doms)
+        sl = (Slab * n)(*[Slab(*d) for d in doms])
+        fi = (ctypes.c_int * n)(*field_ids)
+        sol = torch.empty_like(src)
+        st = (StatsC * n)()
+        p = (params or SolverParams()).c()
+        rc = lib().lqcd_solve_block(self._h, n, sl, fi, _dev(src, "src"), _dev(sol, "sol"), ctypes.byref(p), st,
+                                    _stream(stream))
+        _check(rc)
+        return sol, [s.as_dict() for s in st]
+
+    def solve_full(self, src: torch.Tensor, field_ids, params: SolverParams | None = None, stream=None):
+        n = len(field_ids)
+        fi = (ctypes.c_int * n)(*field_ids)
+        sol = torch.empty_like(src)
+        st = (StatsC * n)()
+        p = (params or SolverParams()).c()
+        _check(lib().lqcd_solve_full(self._h, n, fi, _dev(src, "src"), _dev(sol, "sol"), ctypes.byref(p), st,
+                                     _stream(stream)))
+        return sol, [s.as_dict() for s in st]
+
+    def factorized_propagator(self, gamma, gamma_star, x_src, field: int = 0, delta=None, corr: bool = True,
+                              params: SolverParams | None = None, stream=None, out=None):
+        """(fact, corr, stats) for the 12 point sources at x_src (Sec. 3); fact/corr [12, V, 4, 3]."""
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if out is None:
+            fact = torch.empty((12, self.V, 4, 3), dtype=torch.complex128, device=dev)
+            cor = torch.empty_like(fact) if corr else None
+        else:
+            fact, cor = out
+        d = delta if delta is not None else (gamma[1] + 1, gamma[1])
+        sp = SplitC(Slab(*gamma), Slab(*d), Slab(*gamma_star))
+        st = (StatsC * 4)()
+        p = (params or SolverParams()).c()
+        _check(lib().lqcd_factorized_propagator(self._h, ctypes.byref(sp), (ctypes.c_int * 4)(*x_src), field,
+                                                _dev(fact, "fact"), _dev(cor, "corr") if cor is not None else None,
+                                                ctypes.byref(p), st, _stream(stream)))
+        names = ["gamma", "gamma_bar", "gamma_star", "full"]
+        return fact, cor, {k: s.as_dict() for k, s in zip(names, st)}
+
+    def dslash_bench(self, doms, field_ids, precision: int = 32, reps: int = 20, stream=None):
+        """(ms per launch, algorithmic bytes per launch, flops per launch) of the solver's hop kernel."""
+        n = len(doms)
+        sl = (Slab * n)(*[Slab(*d) for d in doms])
+        fi = (ctypes.c_int * n)(*field_ids)
+        ms, by, fl = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(lib().lqcd_dslash_bench(self._h, n, sl, fi, precision, reps, ctypes.byref(ms), ctypes.byref(by),
+                                       ctypes.byref(fl), _stream(stream)))
+        return ms.value, by.value, fl.value
+
+    def link_force(self, phi: torch.Tensor, dom, field: int = 0, params: SolverParams | None = None,
+                   want_force: bool = True, stream=None):
+        """(force [V,4,8] float64 or None, S, stats) of S = phi^dag (D_L^dag D_L)^{-1} phi."""
+        dev = phi.device
+        F = torch.zeros((self.V, 4, 8), dtype=torch.float64, device=dev) if want_force else None
+        S = ctypes.c_double(0.0)
+        st = (StatsC * 2)()
+        p = (params or SolverParams()).c()
+        _check(lib().lqcd_link_force(self._h, ctypes.byref(Slab(*dom)), field, _dev(phi, "phi"),
+                                     ctypes.c_void_p(F.data_ptr()) if F is not None else None, ctypes.byref(S),
+                                     ctypes.byref(p), st, _stream(stream)))
+        return F, S.value, [s.as_dict() for s in st]
+
+
+class DomainPseudofermionAction(torch.autograd.Function):
+    """S(omega) = phi^dag (D_L^dag D_L)^{-1} phi with U_mu(x) -> exp(i omega^a_mu(x) T_a) U_mu(x).
+
+    forward(omega, lattice, dom, field, phi, params) evaluates S at omega = 0
+    (omega is a zero tensor [V,4,8] standing for the Lie-algebra coordinates
+    of every link) with one D^dag solve; backward recomputes X and Y with two
+    solves and returns grad_S * F, F the link force from the CUDA kernels.
+    Nothing of size V is kept between forward and backward.
+    """
+
+    @staticmethod
+    def forward(ctx, omega, lattice: Lattice, dom, field: int, phi: torch.Tensor, params=None):
+        _, S, _ = lattice.link_force(phi, dom, field, params, want_force=False)
+        ctx.lattice, ctx.dom, ctx.field, ctx.params = lattice, dom, field, params
+        ctx.save_for_backward(phi)
+        return torch.tensor(S, dtype=torch.float64, device=omega.device)
+
+    @staticmethod
+    def backward(ctx, grad_S):
+        (phi,) = ctx.saved_tensors
+        F, _, _ = ctx.lattice.link_force(phi, ctx.dom, ctx.field, ctx.params, want_force=True)
+        return grad_S * F, None, None, None, None, None

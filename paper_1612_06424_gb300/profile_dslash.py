@@ -1,0 +1,46 @@
+"""Run the solver's hop kernel alone on a batch of systems (for ncu / timing).
+
+  python -m paper_1612_06424_gb300.profile_dslash --dims 32 16 16 16 --precision 32 \
+      --slabs 0:17x12 0:13x12 --reps 3
+
+Prints ms per launch, algorithmic GB/s and TFLOP/s.  Each launch is one
+k_hop_lin (out_o = A_oo y_o - 1/4 D_hop x_e) over every system of the batch.
+"""
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--dims", type=int, nargs=4, default=[32, 16, 16, 16])
+    ap.add_argument("--precision", type=int, default=32)
+    ap.add_argument("--slabs", nargs="+", default=["0:17x12", "0:13x12"],
+                    help="t0:t1xN = N systems on slab t0..t1 (all on field 0)")
+    ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--kappa", type=float, default=0.13)
+    ap.add_argument("--csw", type=float, default=1.0)
+    a = ap.parse_args()
+    from paper_1612_06424_gb300 import build, inputs, lqcd
+
+    build.build()
+    doms = []
+    for s in a.slabs:
+        rng, n = s.split("x")
+        t0, t1 = (int(v) for v in rng.split(":"))
+        doms += [(t0, t1)] * int(n)
+    U = inputs.random_su3_field(tuple(a.dims), 0.4, 1)
+    lat = lqcd.Lattice(tuple(a.dims), "open")
+    lat.set_gauge(U, a.kappa, a.csw)
+    ms, by, fl = lat.dslash_bench(doms, [0] * len(doms), a.precision, a.reps)
+    print(f"dims={a.dims} P={a.precision} systems={len(doms)}: {ms:.4f} ms/launch, "
+          f"{by / ms / 1e6:.1f} GB/s algorithmic ({by / 1e6:.1f} MB/launch), {fl / ms / 1e9:.2f} TFLOP/s")
+    lat.close()
+
+
+if __name__ == "__main__":
+    main()
