@@ -282,12 +282,18 @@ int solve_core(lqcd_lattice* L, BatchStore& B, bool dag, const lqcd_solver_param
   std::vector<double> prev_rr(n, INFINITY);
   std::vector<int> stall(n, 0);
   for (int cycle = 0;; cycle++) {
-    // true residual of the preconditioned system: r64 = bh_o - Dhat x_o (FP64)
+    // true residual of the preconditioned system: r64 = bh_o - Dhat x_o (FP64);
+    // at the first cycle x_o = 0 and r64 = bh_o needs no operator
     B.h_active = outer;
     RC(B.push_active(st));
-    RC(lq_hop_clinv(64, dag, clov, L, b, v64(x_o), none, v64(t64), 1.0, 0.0, st));
-    RC(lq_hop_lin(64, dag, clov, lq::RED_NORM, L, b, 1, v64(t64), v64(x_o), v64(bh_o), none, v64(r64), 0.25, -1.0, 1.0,
-                  st));
+    if (cycle == 0) {
+      CK(cudaMemcpyAsync(r64, bh_o, sizeof(double2) * (size_t)b.total * 12, cudaMemcpyDeviceToDevice, st));
+      RC(lq_norm2_64(b, r64, st));
+    } else {
+      RC(lq_hop_clinv(64, dag, clov, L, b, v64(x_o), none, v64(t64), 1.0, 0.0, st));
+      RC(lq_hop_lin(64, dag, clov, lq::RED_NORM, L, b, 1, v64(t64), v64(x_o), v64(bh_o), none, v64(r64), 0.25, -1.0,
+                    1.0, st));
+    }
     RC(lq_finalize(lq::FIN_NORM, b, 0, 0, st));
     RC(B.pull_sc(st));
     int n_act = 0;

@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(128) k_bicg_xr(VecArgs va, void* x, float* xn,
 #pragma unroll
     for (int k = 0; k < 12; k++) sv_[k] = sv_[k] - om * tv[k];
     Prec<P>::store(sys_ptr_w<P>(r, sd.off), nrm_ptr_w(rn, sd.off), sd.n, j, sv_);
-    if (P == 16) Prec<P>::load(sv_, sys_ptr<P>(r, sd.off), nrm_ptr(rn, sd.off), sd.n, j);
+    Prec<P>::quantize(sv_);  // the values just stored
     cx<R> w[12];
     Prec<P>::load(w, sys_ptr<P>(r0, sd.off), nrm_ptr(r0n, sd.off), sd.n, j);
 #pragma unroll
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(128) k_inner_init(VecArgs va, const double2* r
     Prec<P>::store(sys_ptr_w<P>(r0, sd.off), nrm_ptr_w(r0n, sd.off), sd.n, j, b);
     Prec<P>::store(sys_ptr_w<P>(p, sd.off), nrm_ptr_w(pn, sd.off), sd.n, j, b);
     Prec<P>::store(sys_ptr_w<P>(x, sd.off), nrm_ptr_w(xn, sd.off), sd.n, j, z);
-    if (P == 16) Prec<P>::load(b, sys_ptr<P>(r, sd.off), nrm_ptr(rn, sd.off), sd.n, j);
+    Prec<P>::quantize(b);  // the values just stored
 #pragma unroll
     for (int k = 0; k < 12; k++) red[2] += (double)b[k].re * b[k].re + (double)b[k].im * b[k].im;
   }

@@ -183,6 +183,7 @@ struct Prec<64> {
       s[k] = {v.x, v.y};
     }
   }
+  LQ_DI static void quantize(cx<double>*) {}
   LQ_DI static void store(void* base, float*, long long n, long long j, const cx<double> s[12]) {
     double2* p = (double2*)base;
 #pragma unroll
@@ -203,6 +204,7 @@ struct Prec<32> {
       s[2 * k + 1] = {v.z, v.w};
     }
   }
+  LQ_DI static void quantize(cx<float>*) {}
   LQ_DI static void store(void* base, float*, long long n, long long j, const cx<float> s[12]) {
     float4* p = (float4*)base;
 #pragma unroll
@@ -228,6 +230,18 @@ struct Prec<16> {
         float2 f = __half22float2(h);
         s[4 * k + q] = {f.x * nu, f.y * nu};
       }
+    }
+  }
+  // The values a store followed by a load would return (same rounding).
+  LQ_DI static void quantize(cx<float> s[12]) {
+    float m = 0.f;
+#pragma unroll
+    for (int k = 0; k < 12; k++) m = fmaxf(m, fmaxf(fabsf(s[k].re), fabsf(s[k].im)));
+    const float inv = m > 0.f ? 1.f / m : 0.f;
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      float2 f = __half22float2(__floats2half2_rn(s[k].re * inv, s[k].im * inv));
+      s[k] = {f.x * m, f.y * m};
     }
   }
   LQ_DI static void store(void* base, float* nrm, long long n, long long j, const cx<float> s[12]) {

@@ -295,13 +295,10 @@ __global__ void __launch_bounds__(128) k_hop_lin(HopArgs a) {
     }
     Prec<P>::store(sys_ptr_w<P>(a.out, sd.off), nrm_ptr_w(a.outn, sd.off), sd.n, j, res);
     if (RED != RED_NONE) {
-      cx<R> r2[12];
-      if (P == 16) {  // reduce over the stored (rounded) values
-        Prec<P>::load(r2, sys_ptr<P>(a.out, sd.off), nrm_ptr(a.outn, sd.off), sd.n, j);
-      } else {
+      cx<R> r2[12];  // reduce over the stored (rounded) values
 #pragma unroll
-        for (int k = 0; k < 12; k++) r2[k] = res[k];
-      }
+      for (int k = 0; k < 12; k++) r2[k] = res[k];
+      Prec<P>::quantize(r2);
       if (RED == RED_DOT_W) {
         cx<R> wv[12];
         Prec<P>::load(wv, sys_ptr<P>(a.w, sd.off), nrm_ptr(a.wn, sd.off), sd.n, j);
