@@ -16,8 +16,10 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
-OUT_DIR = os.path.join(HERE, "lib")
+OUT_DIR = os.environ.get("LQCD_BUILD_DIR") or os.path.join(HERE, "lib")
 LIB = os.path.join(OUT_DIR, "liblqcd.so")
+# extra nvcc flags (e.g. -DLQ_HOP_MINB=6 to change the register cap of the stencil kernels)
+EXTRA = os.environ.get("LQCD_NVCC_FLAGS", "").split()
 SOURCES = ["api.cu", "kernels.cu", "gauge.cu", "force.cu"]
 HEADERS = ["common.cuh", "dslash.cuh", "blas.cuh", "internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -39,7 +41,7 @@ def _digest() -> str:
             h.update(fh.read())
     with open(os.path.join(ROOT, "include", "lqcd.h"), "rb") as fh:
         h.update(fh.read())
-    h.update(" ".join(ARCH + FLAGS).encode())
+    h.update(" ".join(ARCH + FLAGS + EXTRA).encode())
     h.update(os.uname().machine.encode())
     return h.hexdigest()
 
@@ -55,7 +57,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def one(src):
         obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
-        cmd = [nvcc, *ARCH, *FLAGS, "-I", os.path.join(ROOT, "include"), "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc, *ARCH, *FLAGS, *EXTRA, "-I", os.path.join(ROOT, "include"), "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")

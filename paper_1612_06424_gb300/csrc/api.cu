@@ -97,7 +97,7 @@ struct BatchStore {
 
   int build(const lqcd_lattice* L, int n, const lqcd_slab* doms, const int* fields, cudaStream_t st) {
     h_sys.resize(n);
-    long long off = 0, maxn = 0;
+    long long off = 0, maxn = 0;  // maxn: sites per parity of the largest system
     for (int k = 0; k < n; k++) {
       const lqcd_slab d = doms[k];
       if (d.t0 < 0 || d.t1 >= L->dims[0] || d.t0 > d.t1) {
@@ -114,25 +114,26 @@ struct BatchStore {
       s.t1 = d.t1;
       s.wrap = (d.t0 == 0 && d.t1 == L->dims[0] - 1 && L->bc != LQCD_BC_OPEN) ? 1 : 0;
       s.tsign = L->bc == LQCD_BC_ANTIPERIODIC ? -1.f : 1.f;
-      s.n = (long long)(d.t1 - d.t0 + 1) * L->S3h;
-      s.cb0 = (long long)d.t0 * L->S3h;
+      s.n = (int)((d.t1 - d.t0 + 1) * L->S3h);
+      s.cb0 = (int)(d.t0 * L->S3h);
       s.off = off;
       off += s.n;
-      maxn = std::max(maxn, s.n);
+      maxn = std::max(maxn, (long long)s.n);
       h_sys[k] = s;
     }
     b.nsys = n;
     b.max_n = maxn;
     b.total = off;
     b.nby = (int)((maxn + LQ_BLOCK - 1) / LQ_BLOCK);
-    if (b.nby > 65535) {
+    b.pstride = (int)((12 * maxn + LQ_BLOCK - 1) / LQ_BLOCK);
+    if (b.pstride > 65535) {
       lq_set_error("slab too large for one batch");
       return LQCD_EBADARG;
     }
     RC(sys.alloc(sizeof(lq::SysDesc) * n, st));
     RC(active.alloc(sizeof(int) * n, st));
     RC(sc.alloc(sizeof(lq::SolverScal) * n, st));
-    RC(partial.alloc(sizeof(double) * 4 * (size_t)n * b.nby, st));
+    RC(partial.alloc(sizeof(double) * 4 * (size_t)n * b.pstride, st));
     CK(cudaMemcpyAsync(sys.p, h_sys.data(), sizeof(lq::SysDesc) * n, cudaMemcpyHostToDevice, st));
     b.sys = sys.as<lq::SysDesc>();
     b.active = active.as<int>();
@@ -165,10 +166,9 @@ struct BatchStore {
     v.active = b.active + k0;
     v.sc = b.sc + k0;
     long long maxn = 0;
-    for (int k = k0; k < k0 + n; k++) maxn = std::max(maxn, h_sys[k].n);
+    for (int k = k0; k < k0 + n; k++) maxn = std::max(maxn, (long long)h_sys[k].n);
     v.max_n = maxn;
-    v.partial = b.partial;  // layout [sys][nby] with the full batch's nby
-    v.partial = b.partial + (size_t)k0 * b.nby * 4;
+    v.partial = b.partial + (size_t)k0 * b.pstride * 4;  // layout [sys][pstride][4]
     return v;
   }
 };
@@ -257,18 +257,18 @@ int solve_core(lqcd_lattice* L, BatchStore& B, bool dag, const lqcd_solver_param
   RC(B.push_active(st));
   std::vector<double> bb(n);
   RC(lq_norm2_64(b, b_e, st));
-  RC(lq_finalize(lq::FIN_NORM, b, 0, 0, st));
+  RC(lq_finalize(lq::FIN_NORM, b, 0, 0, 12, st));
   RC(B.pull_sc(st));
   for (int k = 0; k < n; k++) bb[k] = B.h_sc[k].rr;
   RC(lq_norm2_64(b, b_o, st));
-  RC(lq_finalize(lq::FIN_NORM, b, 0, 0, st));
+  RC(lq_finalize(lq::FIN_NORM, b, 0, 0, 12, st));
   RC(B.pull_sc(st));
   for (int k = 0; k < n; k++) {
     bb[k] += B.h_sc[k].rr;
     B.h_sc[k].bb = bb[k];
   }
   if (verbose())
-    for (int k = 0; k < n; k++) fprintf(stderr, "[lqcd] solve P=%d sys %d |eta|^2 = %.6e n=%lld\n", P, k, bb[k], B.h_sys[k].n);
+    for (int k = 0; k < n; k++) fprintf(stderr, "[lqcd] solve P=%d sys %d |eta|^2 = %.6e n=%d\n", P, k, bb[k], B.h_sys[k].n);
   RC(B.push_sc(st));
 
   // prepare: bh_o = b_o + 1/2 H_oe A_ee^{-1} b_e
@@ -289,12 +289,13 @@ int solve_core(lqcd_lattice* L, BatchStore& B, bool dag, const lqcd_solver_param
     if (cycle == 0) {
       CK(cudaMemcpyAsync(r64, bh_o, sizeof(double2) * (size_t)b.total * 12, cudaMemcpyDeviceToDevice, st));
       RC(lq_norm2_64(b, r64, st));
+      RC(lq_finalize(lq::FIN_NORM, b, 0, 0, 12, st));
     } else {
       RC(lq_hop_clinv(64, dag, clov, L, b, v64(x_o), none, v64(t64), 1.0, 0.0, st));
       RC(lq_hop_lin(64, dag, clov, lq::RED_NORM, L, b, 1, v64(t64), v64(x_o), v64(bh_o), none, v64(r64), 0.25, -1.0,
                     1.0, st));
+      RC(lq_finalize(lq::FIN_NORM, b, 0, 0, 1, st));
     }
-    RC(lq_finalize(lq::FIN_NORM, b, 0, 0, st));
     RC(B.pull_sc(st));
     int n_act = 0;
     for (int k = 0; k < n; k++) {
@@ -327,7 +328,7 @@ int solve_core(lqcd_lattice* L, BatchStore& B, bool dag, const lqcd_solver_param
     B.h_active = outer;
     RC(B.push_active(st));
     RC(lq_inner_init(P, b, r64, r, r0, p, xs, st));
-    RC(lq_finalize(lq::FIN_INIT, b, inner_tol * inner_tol, 0.25 * tol * tol, st));
+    RC(lq_finalize(lq::FIN_INIT, b, inner_tol * inner_tol, 0.25 * tol * tol, lq_words_per_site(P), st));
     int it = 0;
     int budget = 0;
     for (int k = 0; k < n; k++)
@@ -336,13 +337,13 @@ int solve_core(lqcd_lattice* L, BatchStore& B, bool dag, const lqcd_solver_param
     while (it < budget) {
       RC(lq_hop_clinv(P, dag, clov, L, b, p, none, te, 1.0, 0.0, st));
       RC(lq_hop_lin(P, dag, clov, lq::RED_DOT_W, L, b, 1, te, p, none, r0, v, -0.25, 1.0, 0.0, st));
-      RC(lq_finalize(lq::FIN_ALPHA, b, 0, 0, st));
+      RC(lq_finalize(lq::FIN_ALPHA, b, 0, 0, 1, st));
       RC(lq_bicg_s(P, b, r, v, s, st));
       RC(lq_hop_clinv(P, dag, clov, L, b, s, none, te, 1.0, 0.0, st));
       RC(lq_hop_lin(P, dag, clov, lq::RED_TS, L, b, 1, te, s, none, none, t, -0.25, 1.0, 0.0, st));
-      RC(lq_finalize(lq::FIN_OMEGA, b, 0, 0, st));
+      RC(lq_finalize(lq::FIN_OMEGA, b, 0, 0, 1, st));
       RC(lq_bicg_xr(P, b, xs, p, s, t, r, r0, st));
-      RC(lq_finalize(lq::FIN_BETA, b, 0, 0, st));
+      RC(lq_finalize(lq::FIN_BETA, b, 0, 0, lq_words_per_site(P), st));
       RC(lq_bicg_p(P, b, p, r, v, st));
       it++;
       if (it % check_every == 0 || it >= budget) {
@@ -365,12 +366,12 @@ int solve_core(lqcd_lattice* L, BatchStore& B, bool dag, const lqcd_solver_param
   RC(B.push_active(st));
   RC(lq_hop_clinv(64, dag, clov, L, b, v64(x_o), v64(b_e), v64(x_e), 0.5, 1.0, st));
   RC(lq_hop_lin(64, dag, clov, lq::RED_NORM, L, b, 0, v64(x_o), v64(x_e), v64(b_e), none, v64(t64), 0.5, -1.0, 1.0, st));
-  RC(lq_finalize(lq::FIN_NORM, b, 0, 0, st));
+  RC(lq_finalize(lq::FIN_NORM, b, 0, 0, 1, st));
   RC(B.pull_sc(st));
   std::vector<double> rre(n);
   for (int k = 0; k < n; k++) rre[k] = B.h_sc[k].rr;
   RC(lq_hop_lin(64, dag, clov, lq::RED_NORM, L, b, 1, v64(x_e), v64(x_o), v64(b_o), none, v64(r64), 0.5, -1.0, 1.0, st));
-  RC(lq_finalize(lq::FIN_NORM, b, 0, 0, st));
+  RC(lq_finalize(lq::FIN_NORM, b, 0, 0, 1, st));
   RC(B.pull_sc(st));
   for (int k = 0; k < n; k++) {
     const double rr = rre[k] + B.h_sc[k].rr;
@@ -429,6 +430,13 @@ extern "C" int lqcd_create_lattice(const int dims[4], int bc_t, lqcd_lattice** o
     lq_set_error("bad time boundary condition");
     return LQCD_EBADARG;
   }
+  {
+    const long long V = (long long)dims[0] * dims[1] * dims[2] * dims[3];
+    if (72 * (V / 2) >= (1LL << 31)) {  // 32-bit site indexing of the packed link / clover arrays
+      lq_set_error("lattice too large for one GPU field (V/2 * 72 must stay below 2^31)");
+      return LQCD_EBADARG;
+    }
+  }
   lqcd_lattice* L = new lqcd_lattice();
   for (int k = 0; k < 4; k++) L->dims[k] = dims[k];
   L->bc = bc_t;
@@ -438,8 +446,8 @@ extern "C" int lqcd_create_lattice(const int dims[4], int bc_t, lqcd_lattice** o
   L->Vh = L->V / 2;
   for (int k = 0; k < 4; k++) L->g.L[k] = dims[k];
   L->g.L3h = dims[3] / 2;
-  L->g.Vh = L->Vh;
-  L->g.S3h = L->S3h;
+  L->g.Vh = (int)L->Vh;
+  L->g.S3h = (int)L->S3h;
   L->g.bc_t = bc_t;
   cudaGetDevice(&L->device);
   *out = L;
@@ -780,7 +788,7 @@ extern "C" int lqcd_link_force(lqcd_lattice* L, const lqcd_slab* dom, int field,
   double S = 0;
   for (int par = 0; par < 2; par++) {
     RC(lq_norm2_64(b, e.v(2 + par), st));
-    RC(lq_finalize(lq::FIN_NORM, b, 0, 0, st));
+    RC(lq_finalize(lq::FIN_NORM, b, 0, 0, 12, st));
     RC(B.pull_sc(st));
     S += B.h_sc[0].rr;
   }

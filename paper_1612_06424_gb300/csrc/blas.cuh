@@ -1,10 +1,19 @@
 // Per-system vector kernels of the batched BiCGStab (van der Vorst 1992)
 // and the FP64 defect-correction loop around it, with fused inner
-// products.  Every kernel runs on a (system, site-block) grid; a block
-// whose system is inactive returns at once.  Inner products accumulate in
-// FP64 (per site, then a warp-shuffle tree, then one partial per block);
-// `k_finalize_*` sum a system's block partials in a fixed order, so every
-// result is deterministic for a given launch shape.
+// products.  Every kernel runs on a (system, block) grid; a block whose
+// system is inactive returns at once.
+//
+// FP64 / FP32 vectors are streamed one 16-byte word per thread (a system's
+// vector is a flat array of NV*n words: double2 = 1 complex, float4 = 2
+// complex), so a thread holds a few registers and every access is one
+// coalesced 128-bit load or store.  FP16 vectors carry one norm per site and
+// are processed one site per thread.
+//
+// Inner products accumulate in FP64 (per thread, then a warp-shuffle tree,
+// then one partial per block); `k_finalize` sums a system's block partials
+// in a fixed order, so every result is deterministic for a given launch
+// shape.  `wps` (words per site) tells the finalize how many blocks the
+// producing kernel used per system.
 #pragma once
 
 #include "dslash.cuh"
@@ -16,62 +25,150 @@ struct VecArgs {
   const int* active;
   SolverScal* sc;
   double* partial;
-  int nby;
+  int pstride;
 };
-
-#define LQ_VEC_PROLOGUE                                            \
-  const int s = blockIdx.x;                                        \
-  if (va.active && !va.active[s]) return;                          \
-  const SysDesc sd = va.sys[s];                                    \
-  if ((long long)blockIdx.y * blockDim.x >= sd.n) return;          \
-  const long long j = (long long)blockIdx.y * blockDim.x + threadIdx.x; \
-  const bool valid = j < sd.n;
 
 template <typename R>
 LQ_DI cx<R> c_of(double2 v) {
   return {(R)v.x, (R)v.y};
 }
 
-// s = r - alpha v
+// ---------------------------------------------------------------- word access
 template <int P>
-__global__ void __launch_bounds__(128) k_bicg_s(VecArgs va, const void* r, const float* rn, const void* v,
-                                                const float* vn, void* so, float* son) {
-  typedef typename Prec<P>::R R;
-  LQ_VEC_PROLOGUE
-  if (!valid) return;
-  const cx<R> al = c_of<R>(va.sc[s].alpha);
-  cx<R> a[12], b[12];
-  Prec<P>::load(a, sys_ptr<P>(r, sd.off), nrm_ptr(rn, sd.off), sd.n, j);
-  Prec<P>::load(b, sys_ptr<P>(v, sd.off), nrm_ptr(vn, sd.off), sd.n, j);
-#pragma unroll
-  for (int k = 0; k < 12; k++) a[k] = a[k] - al * b[k];
-  Prec<P>::store(sys_ptr_w<P>(so, sd.off), nrm_ptr_w(son, sd.off), sd.n, j, a);
+struct Word;
+template <>
+struct Word<64> {
+  typedef double2 T;
+  typedef double R;
+  static constexpr int NC = 1;  // complex numbers per word
+  LQ_DI static void get(const T* p, int i, cx<double> c[1]) {
+    T v = __ldg(p + i);
+    c[0] = {v.x, v.y};
+  }
+  LQ_DI static void put(T* p, int i, const cx<double> c[1]) { p[i] = make_double2(c[0].re, c[0].im); }
+};
+template <>
+struct Word<32> {
+  typedef float4 T;
+  typedef float R;
+  static constexpr int NC = 2;
+  LQ_DI static void get(const T* p, int i, cx<float> c[2]) {
+    T v = __ldg(p + i);
+    c[0] = {v.x, v.y};
+    c[1] = {v.z, v.w};
+  }
+  LQ_DI static void put(T* p, int i, const cx<float> c[2]) { p[i] = make_float4(c[0].re, c[0].im, c[1].re, c[1].im); }
+};
+
+template <int P>
+LQ_DI const typename Word<P>::T* wptr(const void* pool, long long off) {
+  return (const typename Word<P>::T*)pool + off * Prec<P>::NV;
+}
+template <int P>
+LQ_DI typename Word<P>::T* wptr_w(void* pool, long long off) {
+  return (typename Word<P>::T*)pool + off * Prec<P>::NV;
 }
 
-// x += alpha p + omega s ;  r = s - omega t ;  partials <r0, r>, |r|^2
+#define LQ_WORD_PROLOGUE(P)                                   \
+  const int s = blockIdx.x;                                   \
+  if (va.active && !va.active[s]) return;                     \
+  const SysDesc sd = va.sys[s];                               \
+  const int nw = sd.n * Prec<P>::NV;                          \
+  if ((int)(blockIdx.y * blockDim.x) >= nw) return;           \
+  const int i = blockIdx.y * blockDim.x + threadIdx.x;        \
+  const bool valid = i < nw;
+
+#define LQ_SITE_PROLOGUE                                      \
+  const int s = blockIdx.x;                                   \
+  if (va.active && !va.active[s]) return;                     \
+  const SysDesc sd = va.sys[s];                               \
+  if ((int)(blockIdx.y * blockDim.x) >= sd.n) return;         \
+  const int j = blockIdx.y * blockDim.x + threadIdx.x;        \
+  const bool valid = j < sd.n;
+
+// ------------------------------------------------------------ s = r - alpha v
 template <int P>
-__global__ void __launch_bounds__(128) k_bicg_xr(VecArgs va, void* x, float* xn, const void* p, const float* pn,
-                                                 const void* sv, const float* svn, const void* t, const float* tn,
-                                                 void* r, float* rn, const void* r0, const float* r0n) {
-  typedef typename Prec<P>::R R;
-  LQ_VEC_PROLOGUE
+__global__ void __launch_bounds__(128) k_bicg_s_w(VecArgs va, const void* r, const void* v, void* so) {
+  typedef Word<P> W;
+  typedef typename W::R R;
+  LQ_WORD_PROLOGUE(P)
+  if (!valid) return;
+  const cx<R> al = c_of<R>(va.sc[s].alpha);
+  cx<R> a[W::NC], b[W::NC];
+  W::get(wptr<P>(r, sd.off), i, a);
+  W::get(wptr<P>(v, sd.off), i, b);
+#pragma unroll
+  for (int k = 0; k < W::NC; k++) a[k] = a[k] - al * b[k];
+  W::put(wptr_w<P>(so, sd.off), i, a);
+}
+
+__global__ void __launch_bounds__(128) k_bicg_s_h(VecArgs va, const void* r, const float* rn, const void* v,
+                                                  const float* vn, void* so, float* son) {
+  LQ_SITE_PROLOGUE
+  if (!valid) return;
+  const cx<float> al = c_of<float>(va.sc[s].alpha);
+  cx<float> a[12], b[12];
+  Prec<16>::load(a, sys_ptr<16>(r, sd.off), nrm_ptr(rn, sd.off), sd.n, j);
+  Prec<16>::load(b, sys_ptr<16>(v, sd.off), nrm_ptr(vn, sd.off), sd.n, j);
+#pragma unroll
+  for (int k = 0; k < 12; k++) a[k] = a[k] - al * b[k];
+  Prec<16>::store(sys_ptr_w<16>(so, sd.off), nrm_ptr_w(son, sd.off), sd.n, j, a);
+}
+
+// ------------------- x += alpha p + omega s ; r = s - omega t ; <r0,r>, |r|^2
+template <int P>
+__global__ void __launch_bounds__(128) k_bicg_xr_w(VecArgs va, void* x, const void* p, const void* sv, const void* t,
+                                                   void* r, const void* r0) {
+  typedef Word<P> W;
+  typedef typename W::R R;
+  LQ_WORD_PROLOGUE(P)
   double red[3] = {0.0, 0.0, 0.0};
   if (valid) {
     const cx<R> al = c_of<R>(va.sc[s].alpha), om = c_of<R>(va.sc[s].omega);
-    cx<R> xv[12], pv[12], sv_[12], tv[12];
-    Prec<P>::load(xv, sys_ptr<P>(x, sd.off), nrm_ptr(xn, sd.off), sd.n, j);
-    Prec<P>::load(pv, sys_ptr<P>(p, sd.off), nrm_ptr(pn, sd.off), sd.n, j);
-    Prec<P>::load(sv_, sys_ptr<P>(sv, sd.off), nrm_ptr(svn, sd.off), sd.n, j);
+    cx<R> xv[W::NC], pv[W::NC], sv_[W::NC], tv[W::NC], w[W::NC];
+    W::get(wptr<P>(x, sd.off), i, xv);
+    W::get(wptr<P>(p, sd.off), i, pv);
+    W::get(wptr<P>(sv, sd.off), i, sv_);
+    W::get(wptr<P>(t, sd.off), i, tv);
+    W::get(wptr<P>(r0, sd.off), i, w);
+#pragma unroll
+    for (int k = 0; k < W::NC; k++) {
+      xv[k] = xv[k] + al * pv[k] + om * sv_[k];
+      sv_[k] = sv_[k] - om * tv[k];
+    }
+    W::put(wptr_w<P>(x, sd.off), i, xv);
+    W::put(wptr_w<P>(r, sd.off), i, sv_);
+#pragma unroll
+    for (int k = 0; k < W::NC; k++) {
+      red[0] += (double)w[k].re * sv_[k].re + (double)w[k].im * sv_[k].im;
+      red[1] += (double)w[k].re * sv_[k].im - (double)w[k].im * sv_[k].re;
+      red[2] += (double)sv_[k].re * sv_[k].re + (double)sv_[k].im * sv_[k].im;
+    }
+  }
+  block_reduce_store<3>(red, va.partial + ((long long)s * va.pstride + blockIdx.y) * 4);
+}
+
+__global__ void __launch_bounds__(128) k_bicg_xr_h(VecArgs va, void* x, float* xn, const void* p, const float* pn,
+                                                   const void* sv, const float* svn, const void* t, const float* tn,
+                                                   void* r, float* rn, const void* r0, const float* r0n) {
+  LQ_SITE_PROLOGUE
+  double red[3] = {0.0, 0.0, 0.0};
+  if (valid) {
+    const cx<float> al = c_of<float>(va.sc[s].alpha), om = c_of<float>(va.sc[s].omega);
+    cx<float> xv[12], pv[12], sv_[12], tv[12];
+    Prec<16>::load(xv, sys_ptr<16>(x, sd.off), nrm_ptr(xn, sd.off), sd.n, j);
+    Prec<16>::load(pv, sys_ptr<16>(p, sd.off), nrm_ptr(pn, sd.off), sd.n, j);
+    Prec<16>::load(sv_, sys_ptr<16>(sv, sd.off), nrm_ptr(svn, sd.off), sd.n, j);
 #pragma unroll
     for (int k = 0; k < 12; k++) xv[k] = xv[k] + al * pv[k] + om * sv_[k];
-    Prec<P>::store(sys_ptr_w<P>(x, sd.off), nrm_ptr_w(xn, sd.off), sd.n, j, xv);
-    Prec<P>::load(tv, sys_ptr<P>(t, sd.off), nrm_ptr(tn, sd.off), sd.n, j);
+    Prec<16>::store(sys_ptr_w<16>(x, sd.off), nrm_ptr_w(xn, sd.off), sd.n, j, xv);
+    Prec<16>::load(tv, sys_ptr<16>(t, sd.off), nrm_ptr(tn, sd.off), sd.n, j);
 #pragma unroll
     for (int k = 0; k < 12; k++) sv_[k] = sv_[k] - om * tv[k];
-    Prec<P>::store(sys_ptr_w<P>(r, sd.off), nrm_ptr_w(rn, sd.off), sd.n, j, sv_);
-    Prec<P>::quantize(sv_);  // the values just stored
-    cx<R> w[12];
-    Prec<P>::load(w, sys_ptr<P>(r0, sd.off), nrm_ptr(r0n, sd.off), sd.n, j);
+    Prec<16>::store(sys_ptr_w<16>(r, sd.off), nrm_ptr_w(rn, sd.off), sd.n, j, sv_);
+    Prec<16>::quantize(sv_);  // the values just stored
+    cx<float> w[12];
+    Prec<16>::load(w, sys_ptr<16>(r0, sd.off), nrm_ptr(r0n, sd.off), sd.n, j);
 #pragma unroll
     for (int k = 0; k < 12; k++) {
       red[0] += (double)w[k].re * sv_[k].re + (double)w[k].im * sv_[k].im;
@@ -79,62 +176,124 @@ __global__ void __launch_bounds__(128) k_bicg_xr(VecArgs va, void* x, float* xn,
       red[2] += (double)sv_[k].re * sv_[k].re + (double)sv_[k].im * sv_[k].im;
     }
   }
-  block_reduce_store<3>(red, va.partial + ((long long)s * va.nby + blockIdx.y) * 4);
+  block_reduce_store<3>(red, va.partial + ((long long)s * va.pstride + blockIdx.y) * 4);
 }
 
-// p = r + beta (p - omega v)
+// ------------------------------------------------- p = r + beta (p - omega v)
 template <int P>
-__global__ void __launch_bounds__(128) k_bicg_p(VecArgs va, void* p, float* pn, const void* r, const float* rn,
-                                                const void* v, const float* vn) {
-  typedef typename Prec<P>::R R;
-  LQ_VEC_PROLOGUE
+__global__ void __launch_bounds__(128) k_bicg_p_w(VecArgs va, void* p, const void* r, const void* v) {
+  typedef Word<P> W;
+  typedef typename W::R R;
+  LQ_WORD_PROLOGUE(P)
   if (!valid) return;
   const cx<R> be = c_of<R>(va.sc[s].beta), om = c_of<R>(va.sc[s].omega);
-  cx<R> pv[12], rv[12], vv[12];
-  Prec<P>::load(pv, sys_ptr<P>(p, sd.off), nrm_ptr(pn, sd.off), sd.n, j);
-  Prec<P>::load(rv, sys_ptr<P>(r, sd.off), nrm_ptr(rn, sd.off), sd.n, j);
-  Prec<P>::load(vv, sys_ptr<P>(v, sd.off), nrm_ptr(vn, sd.off), sd.n, j);
+  cx<R> pv[W::NC], rv[W::NC], vv[W::NC];
+  W::get(wptr<P>(p, sd.off), i, pv);
+  W::get(wptr<P>(r, sd.off), i, rv);
+  W::get(wptr<P>(v, sd.off), i, vv);
+#pragma unroll
+  for (int k = 0; k < W::NC; k++) pv[k] = rv[k] + be * (pv[k] - om * vv[k]);
+  W::put(wptr_w<P>(p, sd.off), i, pv);
+}
+
+__global__ void __launch_bounds__(128) k_bicg_p_h(VecArgs va, void* p, float* pn, const void* r, const float* rn,
+                                                  const void* v, const float* vn) {
+  LQ_SITE_PROLOGUE
+  if (!valid) return;
+  const cx<float> be = c_of<float>(va.sc[s].beta), om = c_of<float>(va.sc[s].omega);
+  cx<float> pv[12], rv[12], vv[12];
+  Prec<16>::load(pv, sys_ptr<16>(p, sd.off), nrm_ptr(pn, sd.off), sd.n, j);
+  Prec<16>::load(rv, sys_ptr<16>(r, sd.off), nrm_ptr(rn, sd.off), sd.n, j);
+  Prec<16>::load(vv, sys_ptr<16>(v, sd.off), nrm_ptr(vn, sd.off), sd.n, j);
 #pragma unroll
   for (int k = 0; k < 12; k++) pv[k] = rv[k] + be * (pv[k] - om * vv[k]);
-  Prec<P>::store(sys_ptr_w<P>(p, sd.off), nrm_ptr_w(pn, sd.off), sd.n, j, pv);
+  Prec<16>::store(sys_ptr_w<16>(p, sd.off), nrm_ptr_w(pn, sd.off), sd.n, j, pv);
+}
+
+// Word i = q*n + j of a precision-P system vector holds the complex numbers
+// q*NC .. q*NC+NC-1 of site j; complex c of site j is FP64 word c*n + j.
+LQ_DI void split_word(int i, int n, int& q, int& j) {
+  q = i / n;
+  j = i - q * n;
 }
 
 // Start of an inner cycle: r = r0 = p = convert(r64), x = 0; partial |r|^2.
 template <int P>
-__global__ void __launch_bounds__(128) k_inner_init(VecArgs va, const double2* r64, void* r, float* rn, void* r0,
-                                                    float* r0n, void* p, float* pn, void* x, float* xn) {
-  typedef typename Prec<P>::R R;
-  LQ_VEC_PROLOGUE
+__global__ void __launch_bounds__(128) k_inner_init_w(VecArgs va, const double2* r64, void* r, void* r0, void* p,
+                                                      void* x) {
+  typedef Word<P> W;
+  typedef typename W::R R;
+  LQ_WORD_PROLOGUE(P)
+  double red[3] = {0.0, 0.0, 0.0};
+  if (valid) {
+    int q, j;
+    split_word(i, sd.n, q, j);
+    const double2* src = r64 + sd.off * 12;
+    cx<R> b[W::NC], z[W::NC];
+#pragma unroll
+    for (int k = 0; k < W::NC; k++) {
+      double2 v = __ldg(src + (q * W::NC + k) * sd.n + j);
+      b[k] = {(R)v.x, (R)v.y};
+      z[k] = {0, 0};
+      red[2] += (double)b[k].re * b[k].re + (double)b[k].im * b[k].im;
+    }
+    W::put(wptr_w<P>(r, sd.off), i, b);
+    W::put(wptr_w<P>(r0, sd.off), i, b);
+    W::put(wptr_w<P>(p, sd.off), i, b);
+    W::put(wptr_w<P>(x, sd.off), i, z);
+  }
+  block_reduce_store<3>(red, va.partial + ((long long)s * va.pstride + blockIdx.y) * 4);
+}
+
+__global__ void __launch_bounds__(128) k_inner_init_h(VecArgs va, const double2* r64, void* r, float* rn, void* r0,
+                                                      float* r0n, void* p, float* pn, void* x, float* xn) {
+  LQ_SITE_PROLOGUE
   double red[3] = {0.0, 0.0, 0.0};
   if (valid) {
     cx<double> a[12];
     Prec<64>::load(a, sys_ptr<64>(r64, sd.off), nullptr, sd.n, j);
-    cx<R> b[12], z[12];
+    cx<float> b[12], z[12];
 #pragma unroll
     for (int k = 0; k < 12; k++) {
-      b[k] = {(R)a[k].re, (R)a[k].im};
+      b[k] = {(float)a[k].re, (float)a[k].im};
       z[k] = {0, 0};
     }
-    Prec<P>::store(sys_ptr_w<P>(r, sd.off), nrm_ptr_w(rn, sd.off), sd.n, j, b);
-    Prec<P>::store(sys_ptr_w<P>(r0, sd.off), nrm_ptr_w(r0n, sd.off), sd.n, j, b);
-    Prec<P>::store(sys_ptr_w<P>(p, sd.off), nrm_ptr_w(pn, sd.off), sd.n, j, b);
-    Prec<P>::store(sys_ptr_w<P>(x, sd.off), nrm_ptr_w(xn, sd.off), sd.n, j, z);
-    Prec<P>::quantize(b);  // the values just stored
+    Prec<16>::store(sys_ptr_w<16>(r, sd.off), nrm_ptr_w(rn, sd.off), sd.n, j, b);
+    Prec<16>::store(sys_ptr_w<16>(r0, sd.off), nrm_ptr_w(r0n, sd.off), sd.n, j, b);
+    Prec<16>::store(sys_ptr_w<16>(p, sd.off), nrm_ptr_w(pn, sd.off), sd.n, j, b);
+    Prec<16>::store(sys_ptr_w<16>(x, sd.off), nrm_ptr_w(xn, sd.off), sd.n, j, z);
+    Prec<16>::quantize(b);  // the values just stored
 #pragma unroll
     for (int k = 0; k < 12; k++) red[2] += (double)b[k].re * b[k].re + (double)b[k].im * b[k].im;
   }
-  block_reduce_store<3>(red, va.partial + ((long long)s * va.nby + blockIdx.y) * 4);
+  block_reduce_store<3>(red, va.partial + ((long long)s * va.pstride + blockIdx.y) * 4);
 }
 
-// x64 += x (inner solution of precision P)
-// A cycle that ended in NaN or divergence (status 2) contributes nothing.
+// x64 += x (inner solution of precision P).  A cycle that ended in NaN or
+// divergence (status 2) contributes nothing.
 template <int P>
-__global__ void __launch_bounds__(128) k_accum64(VecArgs va, double2* x64, const void* x, const float* xn) {
-  typedef typename Prec<P>::R R;
-  LQ_VEC_PROLOGUE
+__global__ void __launch_bounds__(128) k_accum64_w(VecArgs va, double2* x64, const void* x) {
+  typedef Word<P> W;
+  LQ_WORD_PROLOGUE(P)
   if (!valid || va.sc[s].status == 2) return;
-  cx<R> e[12];
-  Prec<P>::load(e, sys_ptr<P>(x, sd.off), nrm_ptr(xn, sd.off), sd.n, j);
+  int q, j;
+  split_word(i, sd.n, q, j);
+  cx<typename W::R> e[W::NC];
+  W::get(wptr<P>(x, sd.off), i, e);
+  double2* dst = x64 + sd.off * 12;
+#pragma unroll
+  for (int k = 0; k < W::NC; k++) {
+    const int w = (q * W::NC + k) * sd.n + j;
+    double2 a = dst[w];
+    dst[w] = make_double2(a.x + (double)e[k].re, a.y + (double)e[k].im);
+  }
+}
+
+__global__ void __launch_bounds__(128) k_accum64_h(VecArgs va, double2* x64, const void* x, const float* xn) {
+  LQ_SITE_PROLOGUE
+  if (!valid || va.sc[s].status == 2) return;
+  cx<float> e[12];
+  Prec<16>::load(e, sys_ptr<16>(x, sd.off), nrm_ptr(xn, sd.off), sd.n, j);
   cx<double> a[12];
   Prec<64>::load(a, sys_ptr<64>(x64, sd.off), nullptr, sd.n, j);
 #pragma unroll
@@ -142,12 +301,39 @@ __global__ void __launch_bounds__(128) k_accum64(VecArgs va, double2* x64, const
   Prec<64>::store(sys_ptr_w<64>(x64, sd.off), nullptr, sd.n, j, a);
 }
 
-// Sum of the NQ block partials of system s, in a fixed order (one warp).
-LQ_DI void warp_sum_partials(const double* partial, int nby, int nb, int s, double out[3]) {
+// |v|^2 partials of an FP64 vector set (word-parallel).
+__global__ void __launch_bounds__(128) k_norm2_64(VecArgs va, const double2* v) {
+  LQ_WORD_PROLOGUE(64)
+  double red[3] = {0.0, 0.0, 0.0};
+  if (valid) {
+    double2 a = __ldg(v + sd.off * 12 + i);
+    red[2] = a.x * a.x + a.y * a.y;
+  }
+  block_reduce_store<3>(red, va.partial + ((long long)s * va.pstride + blockIdx.y) * 4);
+}
+
+// Precision conversion of a system vector set, one site per thread.
+template <int P1, int P2>
+__global__ void __launch_bounds__(128) k_convert(VecArgs va, const void* in, const float* inn, void* out, float* outn) {
+  typedef typename Prec<P1>::R R1;
+  typedef typename Prec<P2>::R R2;
+  LQ_SITE_PROLOGUE
+  if (!valid) return;
+  cx<R1> a[12];
+  Prec<P1>::load(a, sys_ptr<P1>(in, sd.off), nrm_ptr(inn, sd.off), sd.n, j);
+  cx<R2> b[12];
+#pragma unroll
+  for (int k = 0; k < 12; k++) b[k] = {(R2)a[k].re, (R2)a[k].im};
+  Prec<P2>::store(sys_ptr_w<P2>(out, sd.off), nrm_ptr_w(outn, sd.off), sd.n, j, b);
+}
+
+// ---------------------------------------------------------------- finalize
+// Sum of the block partials of system s, in a fixed order (one warp).
+LQ_DI void warp_sum_partials(const double* partial, int pstride, int nb, int s, double out[3]) {
   const int lane = threadIdx.x & 31;
   double v[3] = {0.0, 0.0, 0.0};
   for (int b = lane; b < nb; b += 32) {
-    const double* q = partial + ((long long)s * nby + b) * 4;
+    const double* q = partial + ((long long)s * pstride + b) * 4;
     v[0] += q[0];
     v[1] += q[1];
     v[2] += q[2];
@@ -175,15 +361,17 @@ LQ_DI bool finite2(double2 a) { return isfinite(a.x) && isfinite(a.y); }
 //             on breakdown, NaN or divergence (rr > 1e8 rr0); else
 //             beta = (rho'/rho)(alpha/omega)
 //  FIN_NORM : rr = |r|^2 only
-// tau2 / floor2 are per call (FIN_INIT); floor2 is relative to bb.
+// tau2 / floor_rel2 are per call (FIN_INIT); floor_rel2 is relative to bb.
+// wps: words per site of the kernel that wrote the partials (1: one site per
+// thread), so that the system used ceil(n * wps / bdim) blocks.
 __global__ void k_finalize(int mode, int nsys, const SysDesc* sys, int* active, SolverScal* sc, const double* partial,
-                           int nby, int bdim, double tau2, double floor_rel2) {
+                           int pstride, int wps, int bdim, double tau2, double floor_rel2) {
   const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (s >= nsys) return;
   if (active && !active[s]) return;
-  const int nb = (int)((sys[s].n + bdim - 1) / bdim);
+  const int nb = (sys[s].n * wps + bdim - 1) / bdim;
   double v[3];
-  warp_sum_partials(partial, nby, nb, s, v);
+  warp_sum_partials(partial, pstride, nb, s, v);
   if ((threadIdx.x & 31) != 0) return;
   SolverScal c = sc[s];
   const double2 d = make_double2(v[0], v[1]);
@@ -249,34 +437,6 @@ __global__ void k_count_active(int nsys, const int* active, int* count) {
   atomicAdd(&tot, c);
   __syncthreads();
   if (threadIdx.x == 0) *count = tot;
-}
-
-// Precision conversion of a system vector set: out(P2) = in(P1).
-template <int P1, int P2>
-__global__ void __launch_bounds__(128) k_convert(VecArgs va, const void* in, const float* inn, void* out, float* outn) {
-  typedef typename Prec<P1>::R R1;
-  typedef typename Prec<P2>::R R2;
-  LQ_VEC_PROLOGUE
-  if (!valid) return;
-  cx<R1> a[12];
-  Prec<P1>::load(a, sys_ptr<P1>(in, sd.off), nrm_ptr(inn, sd.off), sd.n, j);
-  cx<R2> b[12];
-#pragma unroll
-  for (int k = 0; k < 12; k++) b[k] = {(R2)a[k].re, (R2)a[k].im};
-  Prec<P2>::store(sys_ptr_w<P2>(out, sd.off), nrm_ptr_w(outn, sd.off), sd.n, j, b);
-}
-
-// |v|^2 partials (FP64 vectors)
-__global__ void __launch_bounds__(128) k_norm2_64(VecArgs va, const double2* v) {
-  LQ_VEC_PROLOGUE
-  double red[3] = {0.0, 0.0, 0.0};
-  if (valid) {
-    cx<double> a[12];
-    Prec<64>::load(a, sys_ptr<64>(v, sd.off), nullptr, sd.n, j);
-#pragma unroll
-    for (int k = 0; k < 12; k++) red[2] += a[k].re * a[k].re + a[k].im * a[k].im;
-  }
-  block_reduce_store<3>(red, va.partial + ((long long)s * va.nby + blockIdx.y) * 4);
 }
 
 }  // namespace lq

@@ -108,14 +108,14 @@ LQ_HDI void fma_cc(cx<R>& acc, cx<R> a, cx<R> b) {
 struct Geom {
   int L[4];   // T, L1, L2, L3
   int L3h;    // L3 / 2
-  long long Vh;   // sites per parity
-  long long S3h;  // sites per parity and time slice
+  int Vh;   // sites per parity
+  int S3h;  // sites per parity and time slice
   int bc_t;   // 0 open, 1 periodic, 2 antiperiodic
 };
 
 // Coordinates of checkerboard site cb of parity p.
-LQ_DI void eo_coords(const Geom& g, long long cb, int p, int x[4]) {
-  long long r = cb;
+LQ_DI void eo_coords(const Geom& g, int cb, int p, int x[4]) {
+  int r = cb;
   int x3h = (int)(r % g.L3h);
   r /= g.L3h;
   x[2] = (int)(r % g.L[2]);
@@ -125,8 +125,8 @@ LQ_DI void eo_coords(const Geom& g, long long cb, int p, int x[4]) {
   x[3] = 2 * x3h + ((x[0] + x[1] + x[2] + p) & 1);
 }
 
-LQ_DI long long eo_index(const Geom& g, const int x[4]) {
-  return ((((long long)x[0] * g.L[1] + x[1]) * g.L[2] + x[2]) * g.L[3] + x[3]) >> 1;
+LQ_DI int eo_index(const Geom& g, const int x[4]) {
+  return (((x[0] * g.L[1] + x[1]) * g.L[2] + x[2]) * g.L[3] + x[3]) >> 1;
 }
 
 // ------------------------------------------------------------ system / field
@@ -137,8 +137,8 @@ struct SysDesc {
   int wrap;        // 1: the slab is the whole lattice and time hops wrap
   float tsign;     // sign of a wrapping time hop (-1 antiperiodic)
   int pad;
-  long long n;     // sites per parity in the slab
-  long long cb0;   // first checkerboard index of the slab = t0 * S3h
+  int n;           // sites per parity in the slab
+  int cb0;         // first checkerboard index of the slab = t0 * S3h
   long long off;   // site offset of this system in the vector pools
 };
 
@@ -175,7 +175,7 @@ template <>
 struct Prec<64> {
   typedef double R;
   static constexpr int NV = 12;  // double2 words per spinor
-  LQ_DI static void load(cx<double> s[12], const void* base, const float*, long long n, long long j) {
+  LQ_DI static void load(cx<double> s[12], const void* base, const float*, int n, int j) {
     const double2* p = (const double2*)base;
 #pragma unroll
     for (int k = 0; k < 12; k++) {
@@ -184,7 +184,7 @@ struct Prec<64> {
     }
   }
   LQ_DI static void quantize(cx<double>*) {}
-  LQ_DI static void store(void* base, float*, long long n, long long j, const cx<double> s[12]) {
+  LQ_DI static void store(void* base, float*, int n, int j, const cx<double> s[12]) {
     double2* p = (double2*)base;
 #pragma unroll
     for (int k = 0; k < 12; k++) p[k * n + j] = make_double2(s[k].re, s[k].im);
@@ -195,7 +195,7 @@ template <>
 struct Prec<32> {
   typedef float R;
   static constexpr int NV = 6;  // float4 words per spinor
-  LQ_DI static void load(cx<float> s[12], const void* base, const float*, long long n, long long j) {
+  LQ_DI static void load(cx<float> s[12], const void* base, const float*, int n, int j) {
     const float4* p = (const float4*)base;
 #pragma unroll
     for (int k = 0; k < 6; k++) {
@@ -205,7 +205,7 @@ struct Prec<32> {
     }
   }
   LQ_DI static void quantize(cx<float>*) {}
-  LQ_DI static void store(void* base, float*, long long n, long long j, const cx<float> s[12]) {
+  LQ_DI static void store(void* base, float*, int n, int j, const cx<float> s[12]) {
     float4* p = (float4*)base;
 #pragma unroll
     for (int k = 0; k < 6; k++) p[k * n + j] = make_float4(s[2 * k].re, s[2 * k].im, s[2 * k + 1].re, s[2 * k + 1].im);
@@ -217,7 +217,7 @@ template <>
 struct Prec<16> {
   typedef float R;
   static constexpr int NV = 3;  // uint4 words (8 halves) per spinor
-  LQ_DI static void load(cx<float> s[12], const void* base, const float* nrm, long long n, long long j) {
+  LQ_DI static void load(cx<float> s[12], const void* base, const float* nrm, int n, int j) {
     const uint4* p = (const uint4*)base;
     float nu = __ldg(nrm + j);
 #pragma unroll
@@ -244,7 +244,7 @@ struct Prec<16> {
       s[k] = {f.x * m, f.y * m};
     }
   }
-  LQ_DI static void store(void* base, float* nrm, long long n, long long j, const cx<float> s[12]) {
+  LQ_DI static void store(void* base, float* nrm, int n, int j, const cx<float> s[12]) {
     float m = 0.f;
 #pragma unroll
     for (int k = 0; k < 12; k++) m = fmaxf(m, fmaxf(fabsf(s[k].re), fabsf(s[k].im)));
@@ -282,8 +282,8 @@ struct LinkIO;
 
 template <>
 struct LinkIO<64> {
-  LQ_DI static su3<double> load(const FieldPtrs& f, int p, int mu, long long Vh, long long cb) {
-    const double2* b = f.U64 + ((long long)(p * 4 + mu) * 9) * Vh + cb;
+  LQ_DI static su3<double> load(const FieldPtrs& f, int p, int mu, int Vh, int cb) {
+    const double2* b = f.U64 + (p * 4 + mu) * 9 * Vh + cb;
     su3<double> u;
 #pragma unroll
     for (int k = 0; k < 9; k++) {
@@ -296,8 +296,8 @@ struct LinkIO<64> {
 
 template <>
 struct LinkIO<32> {
-  LQ_DI static su3<float> load(const FieldPtrs& f, int p, int mu, long long Vh, long long cb) {
-    const float4* b = f.U32 + ((long long)(p * 4 + mu) * 3) * Vh + cb;
+  LQ_DI static su3<float> load(const FieldPtrs& f, int p, int mu, int Vh, int cb) {
+    const float4* b = f.U32 + (p * 4 + mu) * 3 * Vh + cb;
     su3<float> u;
     float4 a = __ldg(b), c = __ldg(b + Vh), d = __ldg(b + 2 * Vh);
     u.m[0][0] = {a.x, a.y};
@@ -313,8 +313,8 @@ struct LinkIO<32> {
 
 template <>
 struct LinkIO<16> {
-  LQ_DI static su3<float> load(const FieldPtrs& f, int p, int mu, long long Vh, long long cb) {
-    const uint2* b = f.U16 + ((long long)(p * 4 + mu) * 3) * Vh + cb;
+  LQ_DI static su3<float> load(const FieldPtrs& f, int p, int mu, int Vh, int cb) {
+    const uint2* b = f.U16 + (p * 4 + mu) * 3 * Vh + cb;
     su3<float> u;
 #pragma unroll
     for (int k = 0; k < 3; k++) {
@@ -334,7 +334,7 @@ template <int P>
 struct ClovIO {
   typedef float R;
   // 36 reals of block b of parity p at cb -> Hermitian 6x6 mat-vec
-  LQ_DI static void apply(const float4* base, long long Vh, long long cb, const cx<float> in[6], cx<float> out[6]) {
+  LQ_DI static void apply(const float4* base, int Vh, int cb, const cx<float> in[6], cx<float> out[6]) {
     float a[36];
 #pragma unroll
     for (int k = 0; k < 9; k++) {
@@ -366,7 +366,7 @@ struct ClovIO {
 template <>
 struct ClovIO<64> {
   typedef double R;
-  LQ_DI static void apply(const double2* base, long long Vh, long long cb, const cx<double> in[6], cx<double> out[6]) {
+  LQ_DI static void apply(const double2* base, int Vh, int cb, const cx<double> in[6], cx<double> out[6]) {
     double a[36];
 #pragma unroll
     for (int k = 0; k < 18; k++) {

@@ -91,7 +91,7 @@ LQ_DI void mul_udag(const su3<R>& u, const cx<R> h[6], cx<R> w[6]) {
 }
 
 template <int P, bool DAG, int MU>
-LQ_DI void hop_dir(const Geom& g, const SysDesc& sd, const FieldPtrs& f, int pout, long long cb, const int x[4],
+LQ_DI void hop_dir(const Geom& g, const SysDesc& sd, const FieldPtrs& f, int pout, int cb, const int x[4],
                    const void* in, const float* inn, cx<typename Prec<P>::R> acc[12]) {
   typedef typename Prec<P>::R R;
   constexpr int SF = DAG ? +1 : -1;  // forward projector (1 + SF g_mu)
@@ -114,7 +114,7 @@ LQ_DI void hop_dir(const Geom& g, const SysDesc& sd, const FieldPtrs& f, int pou
       y[MU] = (x[MU] + 1 == g.L[MU]) ? 0 : x[MU] + 1;
     }
     if (ok) {
-      long long cy = eo_index(g, y);
+      const int cy = eo_index(g, y);
       cx<R> psi[12], h[6], w[6];
       Prec<P>::load(psi, in, inn, sd.n, cy - sd.cb0);
       project<MU, SF>(psi, h);
@@ -144,7 +144,7 @@ LQ_DI void hop_dir(const Geom& g, const SysDesc& sd, const FieldPtrs& f, int pou
       y[MU] = (x[MU] == 0) ? g.L[MU] - 1 : x[MU] - 1;
     }
     if (ok) {
-      long long cy = eo_index(g, y);
+      const int cy = eo_index(g, y);
       cx<R> psi[12], h[6], w[6];
       Prec<P>::load(psi, in, inn, sd.n, cy - sd.cb0);
       project<MU, SB>(psi, h);
@@ -160,7 +160,7 @@ LQ_DI void hop_dir(const Geom& g, const SysDesc& sd, const FieldPtrs& f, int pou
 }
 
 template <int P, bool DAG>
-LQ_DI void hop_sum(const Geom& g, const SysDesc& sd, const FieldPtrs& f, int pout, long long cb, const int x[4],
+LQ_DI void hop_sum(const Geom& g, const SysDesc& sd, const FieldPtrs& f, int pout, int cb, const int x[4],
                    const void* in, const float* inn, cx<typename Prec<P>::R> acc[12]) {
 #pragma unroll
   for (int k = 0; k < 12; k++) acc[k] = {0, 0};
@@ -172,14 +172,14 @@ LQ_DI void hop_sum(const Geom& g, const SysDesc& sd, const FieldPtrs& f, int pou
 
 // Clover block apply (A or A^{-1}) on a full spinor.
 template <int P>
-LQ_DI void clover_apply(const FieldPtrs& f, bool inverse, int p, long long Vh, long long cb,
-                        const cx<typename Prec<P>::R> in[12], cx<typename Prec<P>::R> out[12]) {
+LQ_DI void clover_apply(const FieldPtrs& f, bool inverse, int p, int Vh, int cb, const cx<typename Prec<P>::R> in[12],
+                        cx<typename Prec<P>::R> out[12]) {
   if constexpr (P == 64) {
-    const double2* base = inverse ? f.Ai64 : f.A64 + (long long)p * 36 * Vh;
+    const double2* base = inverse ? f.Ai64 : f.A64 + p * 36 * Vh;
     ClovIO<64>::apply(base, Vh, cb, in, out);
     ClovIO<64>::apply(base + 18 * Vh, Vh, cb, in + 6, out + 6);
   } else {
-    const float4* base = inverse ? f.Ai32 : f.A32 + (long long)p * 18 * Vh;
+    const float4* base = inverse ? f.Ai32 : f.A32 + p * 18 * Vh;
     ClovIO<32>::apply(base, Vh, cb, in, out);
     ClovIO<32>::apply(base + 9 * Vh, Vh, cb, in + 6, out + 6);
   }
@@ -204,8 +204,25 @@ struct HopArgs {
   void* out;
   float* outn;
   double alpha, beta, gamma, diag;  // see the kernels
-  double* partial;                  // [nsys][nby][4]
-  int nby;
+  double* partial;                  // [nsys][pstride][4]
+  int pstride;
+};
+
+// Epilogue terms present (compile time): D_hop x, A y, z.
+enum { EPI_X = 1, EPI_Y = 2, EPI_Z = 4 };
+
+// Registers are capped so that HopMinBlocks<P> blocks of 128 threads fit on
+// an SM: the FP32 / FP16 stencil is latency-bound, and occupancy is what
+// hides its loads (4 and 5 blocks measured best on GB300; LQ_HOP_MINB
+// overrides both for experiments).  FP64 is ALU-bound and left uncapped
+// (a cap makes it spill).
+template <int P>
+struct HopMinBlocks {
+#ifdef LQ_HOP_MINB
+  static constexpr int value = P == 64 ? 1 : LQ_HOP_MINB;
+#else
+  static constexpr int value = P == 64 ? 1 : P == 32 ? 4 : 5;
+#endif
 };
 
 template <int NQ>
@@ -244,39 +261,37 @@ LQ_DI const float* nrm_ptr(const float* pool, long long off) { return pool ? poo
 LQ_DI float* nrm_ptr_w(float* pool, long long off) { return pool ? pool + off : nullptr; }
 
 // out = beta * A(y) + alpha * D_hop x + gamma * z   on parity pout
-// (A = diag * 1 without clover; a term is skipped when its coefficient is 0),
-// with an optional fused per-system reduction:
+// (terms present per EPI; A = diag * 1 without clover), with an optional
+// fused per-system reduction over the stored values:
 //   RED_DOT_W: <w, out> (slots 0,1);  RED_TS: <out, y> (0,1) and |out|^2 (2);
 //   RED_NORM: |out|^2 (slot 2).
-template <int P, bool DAG, bool CLOV, int RED>
-__global__ void __launch_bounds__(128) k_hop_lin(HopArgs a) {
+template <int P, bool DAG, bool CLOV, int RED, int EPI>
+__global__ void __launch_bounds__(128, HopMinBlocks<P>::value) k_hop_lin(HopArgs a) {
   typedef typename Prec<P>::R R;
   const int s = blockIdx.x;
   if (a.active && !a.active[s]) return;
   const SysDesc sd = a.sys[s];
-  const long long j = (long long)blockIdx.y * blockDim.x + threadIdx.x;
-  if ((long long)blockIdx.y * blockDim.x >= sd.n) return;  // whole block beyond this system
-  const FieldPtrs f = a.fields[sd.field];
+  if ((int)(blockIdx.y * blockDim.x) >= sd.n) return;  // whole block beyond this system
+  const int j = blockIdx.y * blockDim.x + threadIdx.x;
   double red[3] = {0.0, 0.0, 0.0};
   if (j < sd.n) {
-    const long long cb = sd.cb0 + j;
-    int x[4];
-    eo_coords(a.g, cb, a.pout, x);
-    const void* xin = sys_ptr<P>(a.x, sd.off);
-    const float* xinn = nrm_ptr(a.xn, sd.off);
+    const FieldPtrs f = a.fields[sd.field];
+    const int cb = sd.cb0 + j;
     cx<R> res[12];
-    if (a.alpha != 0.0) {
-      cx<R> acc[12];
-      hop_sum<P, DAG>(a.g, sd, f, a.pout, cb, x, xin, xinn, acc);
+    if (EPI & EPI_X) {
+      int x[4];
+      eo_coords(a.g, cb, a.pout, x);
+      hop_sum<P, DAG>(a.g, sd, f, a.pout, cb, x, sys_ptr<P>(a.x, sd.off), nrm_ptr(a.xn, sd.off), res);
+      const R al = (R)a.alpha;
 #pragma unroll
-      for (int k = 0; k < 12; k++) res[k] = (R)a.alpha * acc[k];
+      for (int k = 0; k < 12; k++) res[k] = al * res[k];
     } else {
 #pragma unroll
       for (int k = 0; k < 12; k++) res[k] = {0, 0};
     }
     cx<R> yv[12];
-    if (a.beta != 0.0 || RED == RED_TS) Prec<P>::load(yv, sys_ptr<P>(a.y, sd.off), nrm_ptr(a.yn, sd.off), sd.n, j);
-    if (a.beta != 0.0) {
+    if ((EPI & EPI_Y) || RED == RED_TS) Prec<P>::load(yv, sys_ptr<P>(a.y, sd.off), nrm_ptr(a.yn, sd.off), sd.n, j);
+    if (EPI & EPI_Y) {
       cx<R> ay[12];
       if (CLOV) {
         clover_apply<P>(f, false, a.pout, a.g.Vh, cb, yv, ay);
@@ -284,76 +299,74 @@ __global__ void __launch_bounds__(128) k_hop_lin(HopArgs a) {
 #pragma unroll
         for (int k = 0; k < 12; k++) ay[k] = (R)a.diag * yv[k];
       }
+      const R be = (R)a.beta;
 #pragma unroll
-      for (int k = 0; k < 12; k++) res[k] = res[k] + (R)a.beta * ay[k];
+      for (int k = 0; k < 12; k++) res[k] = res[k] + be * ay[k];
     }
-    if (a.gamma != 0.0) {
+    if (EPI & EPI_Z) {
       cx<R> zv[12];
       Prec<P>::load(zv, sys_ptr<P>(a.z, sd.off), nrm_ptr(a.zn, sd.off), sd.n, j);
+      const R ga = (R)a.gamma;
 #pragma unroll
-      for (int k = 0; k < 12; k++) res[k] = res[k] + (R)a.gamma * zv[k];
+      for (int k = 0; k < 12; k++) res[k] = res[k] + ga * zv[k];
     }
     Prec<P>::store(sys_ptr_w<P>(a.out, sd.off), nrm_ptr_w(a.outn, sd.off), sd.n, j, res);
     if (RED != RED_NONE) {
-      cx<R> r2[12];  // reduce over the stored (rounded) values
-#pragma unroll
-      for (int k = 0; k < 12; k++) r2[k] = res[k];
-      Prec<P>::quantize(r2);
+      Prec<P>::quantize(res);  // reduce over the stored (rounded) values
       if (RED == RED_DOT_W) {
         cx<R> wv[12];
         Prec<P>::load(wv, sys_ptr<P>(a.w, sd.off), nrm_ptr(a.wn, sd.off), sd.n, j);
 #pragma unroll
         for (int k = 0; k < 12; k++) {
-          red[0] += (double)wv[k].re * r2[k].re + (double)wv[k].im * r2[k].im;
-          red[1] += (double)wv[k].re * r2[k].im - (double)wv[k].im * r2[k].re;
+          red[0] += (double)wv[k].re * res[k].re + (double)wv[k].im * res[k].im;
+          red[1] += (double)wv[k].re * res[k].im - (double)wv[k].im * res[k].re;
         }
       } else if (RED == RED_TS) {
 #pragma unroll
         for (int k = 0; k < 12; k++) {
-          red[0] += (double)r2[k].re * yv[k].re + (double)r2[k].im * yv[k].im;
-          red[1] += (double)r2[k].re * yv[k].im - (double)r2[k].im * yv[k].re;
-          red[2] += (double)r2[k].re * r2[k].re + (double)r2[k].im * r2[k].im;
+          red[0] += (double)res[k].re * yv[k].re + (double)res[k].im * yv[k].im;
+          red[1] += (double)res[k].re * yv[k].im - (double)res[k].im * yv[k].re;
+          red[2] += (double)res[k].re * res[k].re + (double)res[k].im * res[k].im;
         }
       } else {
 #pragma unroll
-        for (int k = 0; k < 12; k++) red[2] += (double)r2[k].re * r2[k].re + (double)r2[k].im * r2[k].im;
+        for (int k = 0; k < 12; k++) red[2] += (double)res[k].re * res[k].re + (double)res[k].im * res[k].im;
       }
     }
   }
-  if (RED != RED_NONE) {
-    block_reduce_store<3>(red, a.partial + ((long long)s * a.nby + blockIdx.y) * 4);
-  }
+  if (RED != RED_NONE) block_reduce_store<3>(red, a.partial + ((long long)s * a.pstride + blockIdx.y) * 4);
 }
 
-// out = A^{-1} (alpha * D_hop x + beta * y) on even sites (pout = 0), with
-// A^{-1} = 1/diag without clover.
-template <int P, bool DAG, bool CLOV>
-__global__ void __launch_bounds__(128) k_hop_clinv(HopArgs a) {
+// out = A^{-1} (alpha * D_hop x + beta * y) on even sites (pout = 0), terms
+// present per EPI (EPI_X, EPI_Y); A^{-1} = 1/diag without clover.
+template <int P, bool DAG, bool CLOV, int EPI>
+__global__ void __launch_bounds__(128, HopMinBlocks<P>::value) k_hop_clinv(HopArgs a) {
   typedef typename Prec<P>::R R;
   const int s = blockIdx.x;
   if (a.active && !a.active[s]) return;
   const SysDesc sd = a.sys[s];
-  const long long j = (long long)blockIdx.y * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.x + threadIdx.x;
   if (j >= sd.n) return;
   const FieldPtrs f = a.fields[sd.field];
-  const long long cb = sd.cb0 + j;
-  int x[4];
-  eo_coords(a.g, cb, a.pout, x);
+  const int cb = sd.cb0 + j;
   cx<R> res[12];
-  if (a.alpha != 0.0) {
-    cx<R> acc[12];
-    hop_sum<P, DAG>(a.g, sd, f, a.pout, cb, x, sys_ptr<P>(a.x, sd.off), nrm_ptr(a.xn, sd.off), acc);
+  if (EPI & EPI_X) {
+    int x[4];
+    eo_coords(a.g, cb, a.pout, x);
+    hop_sum<P, DAG>(a.g, sd, f, a.pout, cb, x, sys_ptr<P>(a.x, sd.off), nrm_ptr(a.xn, sd.off), res);
+    const R al = (R)a.alpha;
 #pragma unroll
-    for (int k = 0; k < 12; k++) res[k] = (R)a.alpha * acc[k];
+    for (int k = 0; k < 12; k++) res[k] = al * res[k];
   } else {
 #pragma unroll
     for (int k = 0; k < 12; k++) res[k] = {0, 0};
   }
-  if (a.beta != 0.0) {
+  if (EPI & EPI_Y) {
     cx<R> yv[12];
     Prec<P>::load(yv, sys_ptr<P>(a.y, sd.off), nrm_ptr(a.yn, sd.off), sd.n, j);
+    const R be = (R)a.beta;
 #pragma unroll
-    for (int k = 0; k < 12; k++) res[k] = res[k] + (R)a.beta * yv[k];
+    for (int k = 0; k < 12; k++) res[k] = res[k] + be * yv[k];
   }
   cx<R> o[12];
   if (CLOV) {

@@ -23,7 +23,8 @@ struct VecP {
 // scalars and the block-partial buffer of the fused reductions.
 struct Batch {
   int nsys = 0;
-  int nby = 0;               // site blocks of the largest system
+  int nby = 0;               // site blocks (one site per thread) of the largest system
+  int pstride = 0;           // partial-buffer blocks per system (>= any kernel's grid.y)
   long long max_n = 0;
   long long total = 0;       // sum of n over systems (sites per parity)
   const lq::SysDesc* sys = nullptr;
@@ -75,7 +76,9 @@ int lq_bicg_p(int P, const Batch& b, VecP p, VecP r, VecP v, cudaStream_t st);
 int lq_inner_init(int P, const Batch& b, const double2* r64, VecP r, VecP r0, VecP p, VecP x, cudaStream_t st);
 int lq_accum64(int P, const Batch& b, double2* x64, VecP x, cudaStream_t st);
 int lq_norm2_64(const Batch& b, const double2* v, cudaStream_t st);
-int lq_finalize(int mode, const Batch& b, double tau2, double floor_rel2, cudaStream_t st);
+int lq_finalize(int mode, const Batch& b, double tau2, double floor_rel2, int wps, cudaStream_t st);
+// 16-byte words per site of the word-parallel vector kernels of precision P (1 for FP16: one site per thread)
+int lq_words_per_site(int P);
 int lq_count_active(const Batch& b, int* d_count, cudaStream_t st);
 int lq_convert(int Pin, int Pout, const Batch& b, VecP in, VecP out, cudaStream_t st);
 

@@ -13,6 +13,11 @@ void lq_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 extern "C" long long lqcd_kernel_launches(void) { return g_launches.load(); }
 
 static inline dim3 grid_of(const Batch& b) { return dim3((unsigned)b.nsys, (unsigned)b.nby, 1); }
+// word-parallel grid: NV 16-byte words per site
+static inline dim3 grid_words(const Batch& b, int P) {
+  const long long nv = P == 64 ? 12 : 6;
+  return dim3((unsigned)b.nsys, (unsigned)((b.max_n * nv + LQ_BLOCK - 1) / LQ_BLOCK), 1);
+}
 
 static inline int launched() {
   lq_count_launch();
@@ -32,30 +37,28 @@ static HopArgs hop_args(const lqcd_lattice* L, const Batch& b, int pout) {
   a.active = b.active;
   a.pout = pout;
   a.partial = b.partial;
-  a.nby = b.nby;
+  a.pstride = b.pstride;
   a.diag = 1.0 / (2.0 * L->kappa);
   return a;
 }
 
+// (reduction, epilogue) pairs the solver uses
 template <int P, bool DAG, bool CLOV>
-static void launch_lin(int red, dim3 gr, const HopArgs& a, cudaStream_t st) {
-  switch (red) {
-    case RED_NONE: k_hop_lin<P, DAG, CLOV, RED_NONE><<<gr, LQ_BLOCK, 0, st>>>(a); break;
-    case RED_DOT_W: k_hop_lin<P, DAG, CLOV, RED_DOT_W><<<gr, LQ_BLOCK, 0, st>>>(a); break;
-    case RED_TS: k_hop_lin<P, DAG, CLOV, RED_TS><<<gr, LQ_BLOCK, 0, st>>>(a); break;
-    default: k_hop_lin<P, DAG, CLOV, RED_NORM><<<gr, LQ_BLOCK, 0, st>>>(a); break;
-  }
+static int launch_lin(int red, int epi, dim3 gr, const HopArgs& a, cudaStream_t st) {
+  constexpr int XY = EPI_X | EPI_Y, XZ = EPI_X | EPI_Z, XYZ = EPI_X | EPI_Y | EPI_Z;
+  if (red == RED_NONE && epi == XY) k_hop_lin<P, DAG, CLOV, RED_NONE, XY><<<gr, LQ_BLOCK, 0, st>>>(a);
+  else if (red == RED_NONE && epi == XZ) k_hop_lin<P, DAG, CLOV, RED_NONE, XZ><<<gr, LQ_BLOCK, 0, st>>>(a);
+  else if (red == RED_DOT_W && epi == XY) k_hop_lin<P, DAG, CLOV, RED_DOT_W, XY><<<gr, LQ_BLOCK, 0, st>>>(a);
+  else if (red == RED_TS && epi == XY) k_hop_lin<P, DAG, CLOV, RED_TS, XY><<<gr, LQ_BLOCK, 0, st>>>(a);
+  else if (red == RED_NORM && epi == XYZ) k_hop_lin<P, DAG, CLOV, RED_NORM, XYZ><<<gr, LQ_BLOCK, 0, st>>>(a);
+  else return -1;
+  return 0;
 }
 
 template <int P>
-static void launch_lin_p(bool dag, bool clov, int red, dim3 gr, const HopArgs& a, cudaStream_t st) {
-  if (dag) {
-    if (clov) launch_lin<P, true, true>(red, gr, a, st);
-    else launch_lin<P, true, false>(red, gr, a, st);
-  } else {
-    if (clov) launch_lin<P, false, true>(red, gr, a, st);
-    else launch_lin<P, false, false>(red, gr, a, st);
-  }
+static int launch_lin_p(bool dag, bool clov, int red, int epi, dim3 gr, const HopArgs& a, cudaStream_t st) {
+  if (dag) return clov ? launch_lin<P, true, true>(red, epi, gr, a, st) : launch_lin<P, true, false>(red, epi, gr, a, st);
+  return clov ? launch_lin<P, false, true>(red, epi, gr, a, st) : launch_lin<P, false, false>(red, epi, gr, a, st);
 }
 
 int lq_hop_lin(int P, bool dag, bool clov, int red, const lqcd_lattice* L, const Batch& b, int pout, VecP x, VecP y,
@@ -67,22 +70,31 @@ int lq_hop_lin(int P, bool dag, bool clov, int red, const lqcd_lattice* L, const
   a.w = w.d; a.wn = w.nrm;
   a.out = out.d; a.outn = out.nrm;
   a.alpha = alpha; a.beta = beta; a.gamma = gamma;
+  const int epi = (alpha != 0.0 ? EPI_X : 0) | (beta != 0.0 ? EPI_Y : 0) | (gamma != 0.0 ? EPI_Z : 0);
   dim3 gr = grid_of(b);
-  if (P == 64) launch_lin_p<64>(dag, clov, red, gr, a, st);
-  else if (P == 32) launch_lin_p<32>(dag, clov, red, gr, a, st);
-  else launch_lin_p<16>(dag, clov, red, gr, a, st);
+  int rc = P == 64 ? launch_lin_p<64>(dag, clov, red, epi, gr, a, st)
+         : P == 32 ? launch_lin_p<32>(dag, clov, red, epi, gr, a, st)
+                   : launch_lin_p<16>(dag, clov, red, epi, gr, a, st);
+  if (rc) {
+    lq_set_error("hop kernel: unsupported (reduction, epilogue) pair");
+    return LQCD_EBADARG;
+  }
   return launched();
 }
 
+template <int P, bool DAG, bool CLOV>
+static int launch_clinv(int epi, dim3 gr, const HopArgs& a, cudaStream_t st) {
+  if (epi == EPI_X) k_hop_clinv<P, DAG, CLOV, EPI_X><<<gr, LQ_BLOCK, 0, st>>>(a);
+  else if (epi == EPI_Y) k_hop_clinv<P, DAG, CLOV, EPI_Y><<<gr, LQ_BLOCK, 0, st>>>(a);
+  else if (epi == (EPI_X | EPI_Y)) k_hop_clinv<P, DAG, CLOV, EPI_X | EPI_Y><<<gr, LQ_BLOCK, 0, st>>>(a);
+  else return -1;
+  return 0;
+}
+
 template <int P>
-static void launch_clinv_p(bool dag, bool clov, dim3 gr, const HopArgs& a, cudaStream_t st) {
-  if (dag) {
-    if (clov) k_hop_clinv<P, true, true><<<gr, LQ_BLOCK, 0, st>>>(a);
-    else k_hop_clinv<P, true, false><<<gr, LQ_BLOCK, 0, st>>>(a);
-  } else {
-    if (clov) k_hop_clinv<P, false, true><<<gr, LQ_BLOCK, 0, st>>>(a);
-    else k_hop_clinv<P, false, false><<<gr, LQ_BLOCK, 0, st>>>(a);
-  }
+static int launch_clinv_p(bool dag, bool clov, int epi, dim3 gr, const HopArgs& a, cudaStream_t st) {
+  if (dag) return clov ? launch_clinv<P, true, true>(epi, gr, a, st) : launch_clinv<P, true, false>(epi, gr, a, st);
+  return clov ? launch_clinv<P, false, true>(epi, gr, a, st) : launch_clinv<P, false, false>(epi, gr, a, st);
 }
 
 int lq_hop_clinv(int P, bool dag, bool clov, const lqcd_lattice* L, const Batch& b, VecP x, VecP y, VecP out,
@@ -92,10 +104,15 @@ int lq_hop_clinv(int P, bool dag, bool clov, const lqcd_lattice* L, const Batch&
   a.y = y.d; a.yn = y.nrm;
   a.out = out.d; a.outn = out.nrm;
   a.alpha = alpha; a.beta = beta;
+  const int epi = (alpha != 0.0 ? EPI_X : 0) | (beta != 0.0 ? EPI_Y : 0);
   dim3 gr = grid_of(b);
-  if (P == 64) launch_clinv_p<64>(dag, clov, gr, a, st);
-  else if (P == 32) launch_clinv_p<32>(dag, clov, gr, a, st);
-  else launch_clinv_p<16>(dag, clov, gr, a, st);
+  int rc = P == 64 ? launch_clinv_p<64>(dag, clov, epi, gr, a, st)
+         : P == 32 ? launch_clinv_p<32>(dag, clov, epi, gr, a, st)
+                   : launch_clinv_p<16>(dag, clov, epi, gr, a, st);
+  if (rc) {
+    lq_set_error("clover-inverse hop kernel: unsupported epilogue");
+    return LQCD_EBADARG;
+  }
   return launched();
 }
 
@@ -105,65 +122,64 @@ static VecArgs vec_args(const Batch& b) {
   v.active = b.active;
   v.sc = b.sc;
   v.partial = b.partial;
-  v.nby = b.nby;
+  v.pstride = b.pstride;
   return v;
 }
 
-#define LQ_DISPATCH_P(P, CALL) \
-  do {                          \
-    if ((P) == 64) {            \
-      constexpr int PP = 64;    \
-      CALL;                     \
-    } else if ((P) == 32) {     \
-      constexpr int PP = 32;    \
-      CALL;                     \
-    } else {                    \
-      constexpr int PP = 16;    \
-      CALL;                     \
-    }                           \
-  } while (0)
+int lq_words_per_site(int P) { return P == 64 ? 12 : P == 32 ? 6 : 1; }
 
 int lq_bicg_s(int P, const Batch& b, VecP r, VecP v, VecP s, cudaStream_t st) {
   VecArgs va = vec_args(b);
-  LQ_DISPATCH_P(P, (k_bicg_s<PP><<<grid_of(b), LQ_BLOCK, 0, st>>>(va, r.d, r.nrm, v.d, v.nrm, s.d, s.nrm)));
+  if (P == 64) k_bicg_s_w<64><<<grid_words(b, 64), LQ_BLOCK, 0, st>>>(va, r.d, v.d, s.d);
+  else if (P == 32) k_bicg_s_w<32><<<grid_words(b, 32), LQ_BLOCK, 0, st>>>(va, r.d, v.d, s.d);
+  else k_bicg_s_h<<<grid_of(b), LQ_BLOCK, 0, st>>>(va, r.d, r.nrm, v.d, v.nrm, s.d, s.nrm);
   return launched();
 }
 
 int lq_bicg_xr(int P, const Batch& b, VecP x, VecP p, VecP s, VecP t, VecP r, VecP r0, cudaStream_t st) {
   VecArgs va = vec_args(b);
-  LQ_DISPATCH_P(P, (k_bicg_xr<PP><<<grid_of(b), LQ_BLOCK, 0, st>>>(va, x.d, x.nrm, p.d, p.nrm, s.d, s.nrm, t.d,
-                                                                    t.nrm, r.d, r.nrm, r0.d, r0.nrm)));
+  if (P == 64) k_bicg_xr_w<64><<<grid_words(b, 64), LQ_BLOCK, 0, st>>>(va, x.d, p.d, s.d, t.d, r.d, r0.d);
+  else if (P == 32) k_bicg_xr_w<32><<<grid_words(b, 32), LQ_BLOCK, 0, st>>>(va, x.d, p.d, s.d, t.d, r.d, r0.d);
+  else
+    k_bicg_xr_h<<<grid_of(b), LQ_BLOCK, 0, st>>>(va, x.d, x.nrm, p.d, p.nrm, s.d, s.nrm, t.d, t.nrm, r.d, r.nrm, r0.d,
+                                                 r0.nrm);
   return launched();
 }
 
 int lq_bicg_p(int P, const Batch& b, VecP p, VecP r, VecP v, cudaStream_t st) {
   VecArgs va = vec_args(b);
-  LQ_DISPATCH_P(P, (k_bicg_p<PP><<<grid_of(b), LQ_BLOCK, 0, st>>>(va, p.d, p.nrm, r.d, r.nrm, v.d, v.nrm)));
+  if (P == 64) k_bicg_p_w<64><<<grid_words(b, 64), LQ_BLOCK, 0, st>>>(va, p.d, r.d, v.d);
+  else if (P == 32) k_bicg_p_w<32><<<grid_words(b, 32), LQ_BLOCK, 0, st>>>(va, p.d, r.d, v.d);
+  else k_bicg_p_h<<<grid_of(b), LQ_BLOCK, 0, st>>>(va, p.d, p.nrm, r.d, r.nrm, v.d, v.nrm);
   return launched();
 }
 
 int lq_inner_init(int P, const Batch& b, const double2* r64, VecP r, VecP r0, VecP p, VecP x, cudaStream_t st) {
   VecArgs va = vec_args(b);
-  LQ_DISPATCH_P(P, (k_inner_init<PP><<<grid_of(b), LQ_BLOCK, 0, st>>>(va, r64, r.d, r.nrm, r0.d, r0.nrm, p.d, p.nrm,
-                                                                       x.d, x.nrm)));
+  if (P == 64) k_inner_init_w<64><<<grid_words(b, 64), LQ_BLOCK, 0, st>>>(va, r64, r.d, r0.d, p.d, x.d);
+  else if (P == 32) k_inner_init_w<32><<<grid_words(b, 32), LQ_BLOCK, 0, st>>>(va, r64, r.d, r0.d, p.d, x.d);
+  else
+    k_inner_init_h<<<grid_of(b), LQ_BLOCK, 0, st>>>(va, r64, r.d, r.nrm, r0.d, r0.nrm, p.d, p.nrm, x.d, x.nrm);
   return launched();
 }
 
 int lq_accum64(int P, const Batch& b, double2* x64, VecP x, cudaStream_t st) {
   VecArgs va = vec_args(b);
-  LQ_DISPATCH_P(P, (k_accum64<PP><<<grid_of(b), LQ_BLOCK, 0, st>>>(va, x64, x.d, x.nrm)));
+  if (P == 64) k_accum64_w<64><<<grid_words(b, 64), LQ_BLOCK, 0, st>>>(va, x64, x.d);
+  else if (P == 32) k_accum64_w<32><<<grid_words(b, 32), LQ_BLOCK, 0, st>>>(va, x64, x.d);
+  else k_accum64_h<<<grid_of(b), LQ_BLOCK, 0, st>>>(va, x64, x.d, x.nrm);
   return launched();
 }
 
 int lq_norm2_64(const Batch& b, const double2* v, cudaStream_t st) {
-  k_norm2_64<<<grid_of(b), LQ_BLOCK, 0, st>>>(vec_args(b), v);
+  k_norm2_64<<<grid_words(b, 64), LQ_BLOCK, 0, st>>>(vec_args(b), v);
   return launched();
 }
 
-int lq_finalize(int mode, const Batch& b, double tau2, double floor_rel2, cudaStream_t st) {
+int lq_finalize(int mode, const Batch& b, double tau2, double floor_rel2, int wps, cudaStream_t st) {
   const int warps = 8;
-  k_finalize<<<(b.nsys + warps - 1) / warps, warps * 32, 0, st>>>(mode, b.nsys, b.sys, b.active, b.sc, b.partial, b.nby,
-                                                                  LQ_BLOCK, tau2, floor_rel2);
+  k_finalize<<<(b.nsys + warps - 1) / warps, warps * 32, 0, st>>>(mode, b.nsys, b.sys, b.active, b.sc, b.partial,
+                                                                  b.pstride, wps, LQ_BLOCK, tau2, floor_rel2);
   return launched();
 }
 

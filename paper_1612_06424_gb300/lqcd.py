@@ -15,7 +15,7 @@ import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "lib", "liblqcd.so")
+LIB_PATH = os.environ.get("LQCD_LIB") or os.path.join(_HERE, "lib", "liblqcd.so")
 
 BC = {"open": 0, "periodic": 1, "antiperiodic": 2}
 
