@@ -186,6 +186,33 @@ int lqcd_dslash_bench(lqcd_lattice *lat, int n_sys, const lqcd_slab *doms, const
                       int reps, double *ms_per_launch, double *bytes_per_launch, double *flops_per_launch,
                       void *stream);
 
+/* Size of the device scratch array of lqcd_dslash_noalloc (16 MiB). */
+#define LQCD_NOALLOC_SCRATCH_BYTES (16 * 1024 * 1024)
+
+/* Allocation-free variant of lqcd_dslash in FP64 (no counterpart in the
+ * paper: an integration aid).  Same operation, arguments and layouts as
+ * lqcd_dslash with precision 64: out = D_L in (dagger = 0) or D_L^dag in
+ * (dagger = 1) on the slab dom (NULL: whole lattice) of field `field`.
+ * For callers that cannot allocate device memory while they run -- an
+ * application whose own allocator owns the GPU's memory, or a latency-
+ * critical path where an allocation's cost or failure is not acceptable --
+ * it calls no cudaMalloc / cudaFree or allocating library routine: its
+ * scratch (even / odd copies of in and out, the system descriptor, a
+ * pointer table) lives in one file-scope device array of
+ * LQCD_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
+ * the process exits.  The caller still owns and passes in / out (device).
+ * Limit: the slab may hold at most (LQCD_NOALLOC_SCRATCH_BYTES - 512) / 384
+ * sites (43 688, e.g. a 16^3 x 10 slab); larger slabs return LQCD_EBADARG.
+ * The first call on a device looks up the array's device address (with that
+ * device current) and caches it; make that first call before any stream
+ * capture.  All calls share the one array and it keeps the last call's
+ * contents (every word a call reads is written by that call first): calls
+ * that overlap on the GPU -- on different streams or host threads without
+ * ordering between them -- race and must not be issued.  Stream-ordered; does
+ * not synchronise.  Errors: LQCD_EBADARG, LQCD_ENOFIELD, LQCD_ECUDA. */
+int lqcd_dslash_noalloc(lqcd_lattice *lat, int field, const lqcd_slab *dom, int dagger, const double *in, double *out,
+                        void *stream);
+
 /* Message of the last failing call on this host thread ("" if none). */
 const char *lqcd_last_error(void);
 
