@@ -91,13 +91,17 @@ typedef struct {
                             and FP16 links in the inner solves, FP64 correction      */
   double inner_tol;      /* relative residual reduction per inner cycle (0: default) */
   int check_every;       /* iterations between host convergence checks (0: default) */
+  int max_wave;          /* systems solved together at most (0: as many as fit in free
+                            device memory; larger batches run in consecutive waves)  */
 } lqcd_solver_params;
 
 typedef struct {
   int iters;             /* inner Krylov iterations summed over cycles                */
   int cycles;            /* FP64 defect-correction cycles (true residual evaluations) */
   int status;            /* LQCD_OK, LQCD_ENOTCONVERGED, LQCD_EBREAKDOWN or LQCD_ENAN */
-  double true_residual;  /* ||eta - D psi||_2 / ||eta||_2 recomputed in FP64 at exit   */
+  double true_residual;  /* ||eta - D psi||_2 / ||eta||_2 recomputed in FP64 from the
+                            final iterate (even-odd: the odd half b^_o - D^ psi_o; the
+                            reconstructed even half is exact up to rounding)          */
   double seconds;        /* wall time of the call that produced this entry           */
 } lqcd_solver_stats;
 
@@ -144,6 +148,17 @@ int lqcd_solve_block(lqcd_lattice *lat, int n_sys, const lqcd_slab *doms, const 
 int lqcd_solve_full(lqcd_lattice *lat, int n_sys, const int *field_ids, const double *src, double *sol,
                     const lqcd_solver_params *params, lqcd_solver_stats *stats, void *stream);
 
+/* Batched point-source propagators: system k solves D_{L_k} psi_k = eta_k on
+ * slab doms[k] of field field_ids[k] with the point source
+ * eta_k(y) = delta(y, x_k) delta(s, s_k) delta(c, c_k), x_k = x_src[4k..4k+3]
+ * (inside the slab), column cols[k] = 3 s_k + c_k.  The sources are built on
+ * the device (no source arrays).  sol: device slab vectors back to back as in
+ * lqcd_solve_block.  Systems beyond free device memory run in consecutive
+ * waves (params->max_wave caps a wave).  stats: host array of n_sys or NULL. */
+int lqcd_point_propagators(lqcd_lattice *lat, int n_sys, const lqcd_slab *doms, const int *field_ids,
+                           const int *x_src, const int *cols, double *sol, const lqcd_solver_params *params,
+                           lqcd_solver_stats *stats, void *stream);
+
 /* The 12-source factorized propagator of Sec. 3 for point sources at x_src
  * (x_src[0] inside Gamma), on field `field`:
  *   y in Gamma:  fact(y,x) = D_Gamma^{-1}(y,x)                        eq. quark_prop_I
@@ -185,6 +200,12 @@ int lqcd_link_force(lqcd_lattice *lat, const lqcd_slab *dom, int field, const do
 int lqcd_dslash_bench(lqcd_lattice *lat, int n_sys, const lqcd_slab *doms, const int *field_ids, int precision,
                       int reps, double *ms_per_launch, double *bytes_per_launch, double *flops_per_launch,
                       void *stream);
+
+/* Measured FMA throughput of the current GPU in TFLOP/s (bits = 64 or 32;
+ * no counterpart in the paper: the ALU roofline of the FP64 kernels).  One
+ * launch of 8 independent FMA chains per thread on 8 blocks per SM, timed
+ * with CUDA events on `stream`; synchronises.  Errors: LQCD_EBADARG. */
+int lqcd_fma_peak(int bits, double *tflops, void *stream);
 
 /* Size of the device scratch array of lqcd_dslash_noalloc (16 MiB). */
 #define LQCD_NOALLOC_SCRATCH_BYTES (16 * 1024 * 1024)

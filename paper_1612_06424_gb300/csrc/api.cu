@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <functional>
 #include <vector>
 
 #include "internal.h"
@@ -280,6 +281,7 @@ int solve_core(lqcd_lattice* L, BatchStore& B, bool dag, const lqcd_solver_param
   for (int k = 0; k < n; k++)
     if (!(bb[k] > 0)) outer[k] = 0;  // zero source: zero solution
   std::vector<double> prev_rr(n, INFINITY);
+  std::vector<double> last_rr(n, 0.0);  // last FP64 residual |bh_o - Dhat x_o|^2 of each system
   std::vector<int> stall(n, 0);
   for (int cycle = 0;; cycle++) {
     // true residual of the preconditioned system: r64 = bh_o - Dhat x_o (FP64);
@@ -301,6 +303,7 @@ int solve_core(lqcd_lattice* L, BatchStore& B, bool dag, const lqcd_solver_param
     for (int k = 0; k < n; k++) {
       if (!outer[k]) continue;
       const double rr = B.h_sc[k].rr;
+      last_rr[k] = rr;
       if (verbose())
         fprintf(stderr, "[lqcd] cycle %d sys %d |r|/|eta| = %.3e iters %d status %d\n", cycle, k, std::sqrt(rr / bb[k]),
                 out.iters[k], B.h_sc[k].status);
@@ -324,11 +327,16 @@ int solve_core(lqcd_lattice* L, BatchStore& B, bool dag, const lqcd_solver_param
       n_act += outer[k];
     }
     if (n_act == 0) break;
+    const double t_in0 = now_s();
     // inner solve of Dhat e = r64 in precision P
     B.h_active = outer;
     RC(B.push_active(st));
     RC(lq_inner_init(P, b, r64, r, r0, p, xs, st));
-    RC(lq_finalize(lq::FIN_INIT, b, inner_tol * inner_tol, 0.25 * tol * tol, lq_words_per_site(P), st));
+    // the first FP32 cycle reduces the residual by inner_tol; later ones start
+    // near the tolerance and aim 10x deeper, so one more FP64 check ends the
+    // solve (FP16 cannot go deeper than inner_tol; FP64 aims at the floor)
+    const double tau = (cycle == 0 || P == 16) ? inner_tol : 0.1 * inner_tol;
+    RC(lq_finalize(lq::FIN_INIT, b, tau * tau, 0.09 * tol * tol, lq_words_per_site(P), st));
     int it = 0;
     int budget = 0;
     for (int k = 0; k < n; k++)
@@ -360,22 +368,16 @@ int solve_core(lqcd_lattice* L, BatchStore& B, bool dag, const lqcd_solver_param
     RC(lq_accum64(P, b, x_o, xs, st));
     for (int k = 0; k < n; k++)
       if (outer[k]) out.iters[k] += B.h_sc[k].iters;
+    if (verbose()) fprintf(stderr, "[lqcd] cycle %d: inner %d its in %.2f ms\n", cycle, it, 1e3 * (now_s() - t_in0));
   }
-  // reconstruct x_e = A_ee^{-1}(b_e + 1/2 H_eo x_o), then the full FP64 residual
+  // reconstruct x_e = A_ee^{-1}(b_e + 1/2 H_eo x_o).  Then the even half of
+  // eta - D x vanishes (up to rounding) and the odd half is bh_o - Dhat x_o, so
+  // the true FP64 residual is the one the last cycle recomputed from x_o.
   std::fill(B.h_active.begin(), B.h_active.end(), 1);
   RC(B.push_active(st));
   RC(lq_hop_clinv(64, dag, clov, L, b, v64(x_o), v64(b_e), v64(x_e), 0.5, 1.0, st));
-  RC(lq_hop_lin(64, dag, clov, lq::RED_NORM, L, b, 0, v64(x_o), v64(x_e), v64(b_e), none, v64(t64), 0.5, -1.0, 1.0, st));
-  RC(lq_finalize(lq::FIN_NORM, b, 0, 0, 1, st));
-  RC(B.pull_sc(st));
-  std::vector<double> rre(n);
-  for (int k = 0; k < n; k++) rre[k] = B.h_sc[k].rr;
-  RC(lq_hop_lin(64, dag, clov, lq::RED_NORM, L, b, 1, v64(x_e), v64(x_o), v64(b_o), none, v64(r64), 0.5, -1.0, 1.0, st));
-  RC(lq_finalize(lq::FIN_NORM, b, 0, 0, 1, st));
-  RC(B.pull_sc(st));
   for (int k = 0; k < n; k++) {
-    const double rr = rre[k] + B.h_sc[k].rr;
-    out.res[k] = bb[k] > 0 ? std::sqrt(rr / bb[k]) : 0.0;
+    out.res[k] = bb[k] > 0 ? std::sqrt(last_rr[k] / bb[k]) : 0.0;
     if (out.status[k] == 0 && !(out.res[k] <= tol)) out.status[k] = std::isfinite(out.res[k]) ? LQCD_ENOTCONVERGED : LQCD_ENAN;
   }
   return 0;
@@ -388,6 +390,7 @@ lqcd_solver_params default_params(const lqcd_solver_params* p) {
   q.precision = 64;
   q.inner_tol = 0;
   q.check_every = 0;
+  q.max_wave = 0;
   if (p) q = *p;
   return q;
 }
@@ -411,6 +414,129 @@ void fill_stats(const SolveOut& o, int k0, int n, double secs, lqcd_solver_stats
     st->true_residual = std::max(st->true_residual, o.res[k]);
     if (o.status[k] != 0 && st->status == 0) st->status = o.status[k];
   }
+}
+
+// ---------------------------------------------------------------- waves
+// One system of a batched call: slab, field and what fills / consumes it.
+struct SysSpec {
+  lqcd_slab dom;
+  int field;
+  int role;   // caller-defined (which source / which output)
+  int col;    // spin-colour column 3*s + c of a point source
+  int4 xsrc;  // point-source position
+};
+
+using FillFn = std::function<int(BatchStore& B, int k0, double2* b_e, double2* b_o)>;
+using SinkFn = std::function<int(BatchStore& B, int k0, const double2* x_e, const double2* x_o)>;
+
+// device bytes per system site (one parity) held during a solve in precision P:
+// 4 caller-side FP64 vectors + 3 solver FP64 vectors + 8 Krylov vectors
+size_t site_bytes(int P) { return (size_t)(7 * 192 + 8 * (P == 64 ? 192 : P == 32 ? 96 : 52)); }
+
+// Free device memory, counting what the stream-ordered pool holds unused.
+size_t free_device_bytes() {
+  size_t fr = 0, tot = 0;
+  cudaMemGetInfo(&fr, &tot);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    unsigned long long res = 0, used = 0;
+    cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &res);
+    cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used);
+    if (res > used) fr += (size_t)(res - used);
+  }
+  cudaGetLastError();
+  return fr;
+}
+
+// Runs of equal role inside [0, n) of a wave starting at k0: f(a, b, role) on [a, b).
+template <typename F>
+int for_role_runs(const std::vector<SysSpec>& sp, int k0, int n, F f) {
+  int a = 0;
+  while (a < n) {
+    int b = a + 1;
+    while (b < n && sp[k0 + b].role == sp[k0 + a].role) b++;
+    RC(f(a, b, sp[k0 + a].role));
+    a = b;
+  }
+  return 0;
+}
+
+// Solve every system of `sp` (D_L x = b, or D_L^dag x = b), in consecutive
+// waves that fit in free device memory (at most prm.max_wave systems each).
+// For each wave: fill its sources, solve, hand the solutions to sink.
+int solve_waves(lqcd_lattice* L, const std::vector<SysSpec>& sp, bool dag, const lqcd_solver_params& prm,
+                const FillFn& fill, const SinkFn& sink, SolveOut& out, cudaStream_t st) {
+  const int N = (int)sp.size();
+  out.iters.assign(N, 0);
+  out.cycles.assign(N, 0);
+  out.status.assign(N, 0);
+  out.res.assign(N, 0.0);
+  const int P = prm.precision == 16 ? 16 : prm.precision == 32 ? 32 : 64;
+  const size_t fb = free_device_bytes();
+  const size_t reserve = (size_t)1 << 30;
+  const size_t budget = fb > 2 * reserve ? (size_t)(0.85 * (double)(fb - reserve)) : fb / 2;
+  int k = 0;
+  while (k < N) {
+    size_t need = 0;
+    int w = 0;
+    while (k + w < N && (prm.max_wave <= 0 || w < prm.max_wave)) {
+      const size_t n = (size_t)(sp[k + w].dom.t1 - sp[k + w].dom.t0 + 1) * (size_t)L->S3h;
+      const size_t add = n * site_bytes(P) + 4096;
+      if (w > 0 && need + add > budget) break;
+      need += add;
+      w++;
+    }
+    std::vector<lqcd_slab> doms(w);
+    std::vector<int> fields(w);
+    for (int q = 0; q < w; q++) {
+      doms[q] = sp[k + q].dom;
+      fields[q] = sp[k + q].field;
+    }
+    BatchStore B;
+    RC(B.build(L, w, doms.data(), fields.data(), st));
+    Pool64 e;
+    RC(e.alloc(B.b, 4, st));
+    RC(fill(B, k, e.v(0), e.v(1)));
+    SolveOut o;
+    RC(solve_core(L, B, dag, prm, e.v(0), e.v(1), e.v(2), e.v(3), o, st));
+    RC(sink(B, k, e.v(2), e.v(3)));
+    for (int q = 0; q < w; q++) {
+      out.iters[k + q] = o.iters[q];
+      out.cycles[k + q] = o.cycles[q];
+      out.status[k + q] = o.status[q];
+      out.res[k + q] = o.res[q];
+    }
+    if (verbose()) fprintf(stderr, "[lqcd] wave of %d systems (%d..%d of %d)\n", w, k, k + w - 1, N);
+    k += w;
+  }
+  return 0;
+}
+
+// Device copies of the per-system point-source columns / positions of [k0, k0+n).
+struct SrcArrays {
+  DBuf cols, xsrc;
+  int upload(const std::vector<SysSpec>& sp, int k0, int n, cudaStream_t st) {
+    std::vector<int> c(n);
+    std::vector<int4> x(n);
+    for (int q = 0; q < n; q++) {
+      c[q] = sp[k0 + q].col;
+      x[q] = sp[k0 + q].xsrc;
+    }
+    RC(cols.alloc(sizeof(int) * n, st));
+    RC(xsrc.alloc(sizeof(int4) * n, st));
+    CK(cudaMemcpyAsync(cols.p, c.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(xsrc.p, x.data(), sizeof(int4) * n, cudaMemcpyHostToDevice, st));
+    return 0;
+  }
+};
+
+// Device array of n pointers.
+int upload_ptrs(DBuf& d, const std::vector<void*>& p, cudaStream_t st) {
+  RC(d.alloc(sizeof(void*) * (p.empty() ? 1 : p.size()), st));
+  if (!p.empty()) CK(cudaMemcpyAsync(d.p, p.data(), sizeof(void*) * p.size(), cudaMemcpyHostToDevice, st));
+  return 0;
 }
 
 }  // namespace
@@ -450,6 +576,15 @@ extern "C" int lqcd_create_lattice(const int dims[4], int bc_t, lqcd_lattice** o
   L->g.S3h = (int)L->S3h;
   L->g.bc_t = bc_t;
   cudaGetDevice(&L->device);
+  // Solver work vectors come from the device's stream-ordered pool; keep its
+  // memory mapped across synchronisations instead of returning it to the
+  // driver (and re-mapping it) at every stream synchronise.
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, L->device) == cudaSuccess) {
+    unsigned long long keep = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  cudaGetLastError();
   *out = L;
   return 0;
 }
@@ -486,7 +621,8 @@ extern "C" int lqcd_set_gauge(lqcd_lattice* L, int n_fields, const double* U, do
   }
   cudaStream_t st = (cudaStream_t)stream;
   CK(cudaStreamSynchronize(st));
-  free_fields(L);
+  const bool reuse = (int)L->fields.size() == n_fields && L->d_fields != nullptr;
+  if (!reuse) free_fields(L);
   L->kappa = kappa;
   L->csw = c_sw;
   const long long V = L->V, Vh = L->Vh;
@@ -498,16 +634,19 @@ extern "C" int lqcd_set_gauge(lqcd_lattice* L, int n_fields, const double* U, do
   RC(fail.alloc(sizeof(int), st));
   std::vector<lq::FieldPtrs> ptrs;
   for (int fi = 0; fi < n_fields; fi++) {
-    FieldData f;
-    CK(cudaMalloc(&f.U64, sizeof(double2) * 2 * 4 * 9 * Vh));
-    L->fields.push_back(f);
-    FieldData& F = L->fields.back();
-    CK(cudaMalloc(&F.U32, sizeof(float4) * 2 * 4 * 3 * Vh));
-    CK(cudaMalloc(&F.U16, sizeof(uint2) * 2 * 4 * 3 * Vh));
-    CK(cudaMalloc(&F.A64, sizeof(double2) * 2 * 36 * Vh));
-    CK(cudaMalloc(&F.Ai64, sizeof(double2) * 36 * Vh));
-    CK(cudaMalloc(&F.A32, sizeof(float4) * 2 * 18 * Vh));
-    CK(cudaMalloc(&F.Ai32, sizeof(float4) * 18 * Vh));
+    if (!reuse) {
+      FieldData f;
+      L->fields.push_back(f);
+      FieldData& F = L->fields.back();
+      CK(cudaMalloc(&F.U64, sizeof(double2) * 2 * 4 * 9 * Vh));
+      CK(cudaMalloc(&F.U32, sizeof(float4) * 2 * 4 * 3 * Vh));
+      CK(cudaMalloc(&F.U16, sizeof(uint2) * 2 * 4 * 3 * Vh));
+      CK(cudaMalloc(&F.A64, sizeof(double2) * 2 * 36 * Vh));
+      CK(cudaMalloc(&F.Ai64, sizeof(double2) * 36 * Vh));
+      CK(cudaMalloc(&F.A32, sizeof(float4) * 2 * 18 * Vh));
+      CK(cudaMalloc(&F.Ai32, sizeof(float4) * 18 * Vh));
+    }
+    FieldData& F = L->fields[fi];
     const double2* src = (const double2*)(U + (size_t)fi * V * 72);
     if (mem == LQCD_MEM_HOST) {
       CK(cudaMemcpyAsync(tmp.p, src, nat_bytes, cudaMemcpyHostToDevice, st));
@@ -544,8 +683,10 @@ extern "C" int lqcd_set_gauge(lqcd_lattice* L, int n_fields, const double* U, do
     fp.Ai32 = F.Ai32;
     ptrs.push_back(fp);
   }
-  CK(cudaMalloc(&L->d_fields, sizeof(lq::FieldPtrs) * n_fields));
-  CK(cudaMemcpy(L->d_fields, ptrs.data(), sizeof(lq::FieldPtrs) * n_fields, cudaMemcpyHostToDevice));
+  if (!reuse) {
+    CK(cudaMalloc(&L->d_fields, sizeof(lq::FieldPtrs) * n_fields));
+    CK(cudaMemcpy(L->d_fields, ptrs.data(), sizeof(lq::FieldPtrs) * n_fields, cudaMemcpyHostToDevice));
+  }
   return 0;
 }
 
@@ -604,26 +745,29 @@ static int solve_api(lqcd_lattice* L, int n, const lqcd_slab* doms, const int* f
   const double t_start = now_s();
   cudaStream_t st = (cudaStream_t)stream;
   lqcd_solver_params prm = default_params(params);
-  BatchStore B;
-  RC(B.build(L, n, doms, field_ids, st));
-  const Batch& b = B.b;
-  std::vector<const double2*> sp(n);
-  std::vector<double2*> dp(n);
+  std::vector<SysSpec> sp(n);
+  std::vector<long long> goff(n + 1, 0);  // natural-order site offset of each system's slab vector
   for (int k = 0; k < n; k++) {
-    sp[k] = (const double2*)src + 2 * B.h_sys[k].off * 12;
-    dp[k] = (double2*)sol + 2 * B.h_sys[k].off * 12;
+    sp[k] = SysSpec{doms[k], field_ids[k], 0, 0, make_int4(0, 0, 0, 0)};
+    const long long len = doms[k].t1 >= doms[k].t0 ? (long long)(doms[k].t1 - doms[k].t0 + 1) * L->S3 : 0;
+    goff[k + 1] = goff[k] + len;
   }
-  DBuf dsp, ddp;
-  RC(dsp.alloc(sizeof(void*) * n, st));
-  RC(ddp.alloc(sizeof(void*) * n, st));
-  CK(cudaMemcpyAsync(dsp.p, sp.data(), sizeof(void*) * n, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(ddp.p, dp.data(), sizeof(void*) * n, cudaMemcpyHostToDevice, st));
-  Pool64 e;
-  RC(e.alloc(b, 4, st));
-  RC(lq_nat_to_eo(L, b, dsp.as<const double2*>(), e.v(0), e.v(1), st));
+  FillFn fill = [&](BatchStore& B, int k0, double2* be, double2* bo) -> int {
+    std::vector<void*> p(B.b.nsys);
+    for (int q = 0; q < B.b.nsys; q++) p[q] = (void*)((const double2*)src + goff[k0 + q] * 12);
+    DBuf d;
+    RC(upload_ptrs(d, p, st));
+    return lq_nat_to_eo(L, B.b, d.as<const double2*>(), be, bo, st);
+  };
+  SinkFn sink = [&](BatchStore& B, int k0, const double2* xe, const double2* xo) -> int {
+    std::vector<void*> p(B.b.nsys);
+    for (int q = 0; q < B.b.nsys; q++) p[q] = (void*)((double2*)sol + goff[k0 + q] * 12);
+    DBuf d;
+    RC(upload_ptrs(d, p, st));
+    return lq_eo_to_nat(L, B.b, xe, xo, d.as<double2* const>(), 1.0, st);
+  };
   SolveOut o;
-  RC(solve_core(L, B, false, prm, e.v(0), e.v(1), e.v(2), e.v(3), o, st));
-  RC(lq_eo_to_nat(L, b, e.v(2), e.v(3), ddp.as<double2* const>(), 1.0, st));
+  RC(solve_waves(L, sp, false, prm, fill, sink, o, st));
   CK(cudaStreamSynchronize(st));
   const double secs = now_s() - t_start;
   if (stats)
@@ -676,74 +820,93 @@ extern "C" int lqcd_factorized_propagator(lqcd_lattice* L, const lqcd_split* spl
       lq_set_error("factorized_propagator: source outside the lattice");
       return LQCD_EBADARG;
     }
+  if (field < 0 || field >= (int)L->fields.size()) {
+    lq_set_error("factorized_propagator: field index not loaded");
+    return LQCD_ENOFIELD;
+  }
   const double t_start = now_s();
   cudaStream_t st = (cudaStream_t)stream;
   lqcd_solver_params prm = default_params(params);
   const lqcd_slab Gb = {0, has_delta ? Dl.t1 : G.t1};
   const bool want_corr = corr != nullptr;
-
-  // stage A: Gammabar and Gamma solves from the point sources (eqs. quark_prop_I, quark_prop_II)
-  std::vector<lqcd_slab> da;
-  std::vector<int> fa, ca;
-  for (int c = 0; c < 12; c++) da.push_back(Gb), fa.push_back(field), ca.push_back(c);
-  if (has_delta)
-    for (int c = 0; c < 12; c++) da.push_back(G), fa.push_back(field), ca.push_back(c);
-  BatchStore A;
-  RC(A.build(L, (int)da.size(), da.data(), fa.data(), st));
-  // stage B: Gamma* solves of the boundary sources, and the full solves
-  std::vector<lqcd_slab> db;
-  std::vector<int> fb, cbv;
-  for (int c = 0; c < 12; c++) db.push_back(Gs), fb.push_back(field), cbv.push_back(c);
-  if (want_corr)
-    for (int c = 0; c < 12; c++) db.push_back(lqcd_slab{0, T - 1}), fb.push_back(field), cbv.push_back(c);
-  BatchStore Bs;
-  RC(Bs.build(L, (int)db.size(), db.data(), fb.data(), st));
-
-  DBuf dcols;
-  RC(dcols.alloc(sizeof(int) * 24, st));
-  CK(cudaMemcpyAsync(dcols.p, ca.data(), sizeof(int) * ca.size(), cudaMemcpyHostToDevice, st));
-  Pool64 ea, eb;
-  RC(ea.alloc(A.b, 4, st));
-  RC(eb.alloc(Bs.b, 4, st));
-  RC(lq_point_source(L, A.b, dcols.as<int>(), x_src, ea.v(0), ea.v(1), st));
-  SolveOut oa, ob;
-  RC(solve_core(L, A, false, prm, ea.v(0), ea.v(1), ea.v(2), ea.v(3), oa, st));
-  // chi = D_dGamma* (D_Gammabar^{-1} eta)|_Gamma  on the first slice of Gamma*
-  RC(lq_boundary_hop(L, Bs.view(0, 12), A.view(0, 12), G.t1, ea.v(2), ea.v(3), eb.v(0), eb.v(1), st));
-  if (want_corr) {
-    Batch fv = Bs.view(12, 12);
-    RC(lq_point_source(L, fv, dcols.as<int>(), x_src, eb.v(0), eb.v(1), st));
-  }
-  RC(solve_core(L, Bs, false, prm, eb.v(0), eb.v(1), eb.v(2), eb.v(3), ob, st));
-
-  // assemble fact: D_Gamma^{-1} eta on Gamma, -zeta on Gamma*
+  const int4 xs = make_int4(x_src[0], x_src[1], x_src[2], x_src[3]);
   const long long V = L->V, S3 = L->S3;
+  enum { R_GBAR = 0, R_GAMMA = 1, R_GSTAR = 2, R_FULL = 3 };
+
   CK(cudaMemsetAsync(fact, 0, sizeof(double2) * 12 * (size_t)V * 12, st));
-  std::vector<double2*> dst(12);
-  DBuf ddst;
-  RC(ddst.alloc(sizeof(void*) * 24, st));
-  {
-    const int k0 = has_delta ? 12 : 0;
-    for (int c = 0; c < 12; c++) dst[c] = (double2*)fact + (size_t)c * V * 12 + (size_t)G.t0 * S3 * 12;
-    CK(cudaMemcpyAsync(ddst.p, dst.data(), sizeof(void*) * 12, cudaMemcpyHostToDevice, st));
-    RC(lq_eo_to_nat(L, A.view(k0, 12), ea.v(2), ea.v(3), ddst.as<double2* const>(), 1.0, st));
-  }
-  {
-    for (int c = 0; c < 12; c++) dst[c] = (double2*)fact + (size_t)c * V * 12 + (size_t)Gs.t0 * S3 * 12;
-    CK(cudaMemcpyAsync(ddst.as<double2*>() + 12, dst.data(), sizeof(void*) * 12, cudaMemcpyHostToDevice, st));
-    RC(lq_eo_to_nat(L, Bs.view(0, 12), eb.v(2), eb.v(3), (double2* const*)(ddst.as<double2*>() + 12), -1.0, st));
-  }
-  if (want_corr) {
-    DBuf dd2;
-    RC(dd2.alloc(sizeof(void*) * 12, st));
-    for (int c = 0; c < 12; c++) dst[c] = (double2*)corr + (size_t)c * V * 12;
-    CK(cudaMemcpyAsync(dd2.p, dst.data(), sizeof(void*) * 12, cudaMemcpyHostToDevice, st));
-    RC(lq_eo_to_nat(L, Bs.view(12, 12), eb.v(2), eb.v(3), dd2.as<double2* const>(), 1.0, st));
-    RC(lq_sub_inplace((double2*)corr, (const double2*)fact, 12 * V * 12, st));
-    CK(cudaStreamSynchronize(st));
-  }
+  // compact boundary source chi[col][slot][slice site][12] (two time slices)
+  DBuf chi;
+  RC(chi.alloc(sizeof(double2) * 12 * 2 * (size_t)S3 * 12, st));
+
+  // stage A: Gammabar (and Gamma) from the 12 point sources (eqs. quark_prop_I, quark_prop_II)
+  std::vector<SysSpec> sa;
+  for (int c = 0; c < 12; c++) sa.push_back(SysSpec{Gb, field, R_GBAR, c, xs});
+  if (has_delta)
+    for (int c = 0; c < 12; c++) sa.push_back(SysSpec{G, field, R_GAMMA, c, xs});
+  FillFn fill_a = [&](BatchStore& B, int k0, double2* be, double2* bo) -> int {
+    SrcArrays s;
+    RC(s.upload(sa, k0, B.b.nsys, st));
+    return lq_point_source(L, B.b, s.cols.as<int>(), s.xsrc.as<int4>(), be, bo, st);
+  };
+  auto write_gamma = [&](BatchStore& B, int k0, int a, int b, const double2* xe, const double2* xo) -> int {
+    std::vector<void*> p;
+    for (int q = a; q < b; q++) p.push_back((double2*)fact + (size_t)sa[k0 + q].col * V * 12 + (size_t)G.t0 * S3 * 12);
+    DBuf d;
+    RC(upload_ptrs(d, p, st));
+    return lq_eo_to_nat(L, B.view(a, b - a), xe, xo, d.as<double2* const>(), 1.0, st);
+  };
+  SinkFn sink_a = [&](BatchStore& B, int k0, const double2* xe, const double2* xo) -> int {
+    return for_role_runs(sa, k0, B.b.nsys, [&](int a, int b, int role) -> int {
+      if (role == R_GAMMA) return write_gamma(B, k0, a, b, xe, xo);
+      // Gammabar: chi = D_dGamma* (D_Gammabar^{-1} eta)|_Gamma, and fact on Gamma when DeltaGamma is empty
+      SrcArrays s;
+      RC(s.upload(sa, k0 + a, b - a, st));
+      RC(lq_boundary_chi(L, B.view(a, b - a), s.cols.as<int>(), G.t1, xe, xo, chi.as<double2>(), st));
+      if (!has_delta) RC(write_gamma(B, k0, a, b, xe, xo));
+      return 0;
+    });
+  };
+  SolveOut oa;
+  const double t_a0 = now_s();
+  RC(solve_waves(L, sa, false, prm, fill_a, sink_a, oa, st));
+  const double t_a1 = now_s();
+
+  // stage B: Gamma* from chi (eq. quark_prop_II), and the full lattice from the point sources
+  std::vector<SysSpec> sb;
+  for (int c = 0; c < 12; c++) sb.push_back(SysSpec{Gs, field, R_GSTAR, c, xs});
+  if (want_corr)
+    for (int c = 0; c < 12; c++) sb.push_back(SysSpec{lqcd_slab{0, T - 1}, field, R_FULL, c, xs});
+  FillFn fill_b = [&](BatchStore& B, int k0, double2* be, double2* bo) -> int {
+    return for_role_runs(sb, k0, B.b.nsys, [&](int a, int b, int role) -> int {
+      SrcArrays s;
+      RC(s.upload(sb, k0 + a, b - a, st));
+      if (role == R_GSTAR) return lq_chi_to_eo(L, B.view(a, b - a), s.cols.as<int>(), G.t1, chi.as<double2>(), be, bo, st);
+      return lq_point_source(L, B.view(a, b - a), s.cols.as<int>(), s.xsrc.as<int4>(), be, bo, st);
+    });
+  };
+  SinkFn sink_b = [&](BatchStore& B, int k0, const double2* xe, const double2* xo) -> int {
+    return for_role_runs(sb, k0, B.b.nsys, [&](int a, int b, int role) -> int {
+      std::vector<void*> p;
+      for (int q = a; q < b; q++) {
+        if (role == R_GSTAR) p.push_back((double2*)fact + (size_t)sb[k0 + q].col * V * 12 + (size_t)Gs.t0 * S3 * 12);
+        else p.push_back((double2*)corr + (size_t)sb[k0 + q].col * V * 12);
+      }
+      DBuf d;
+      RC(upload_ptrs(d, p, st));
+      // fact on Gamma* is -zeta; corr first receives the full propagator
+      return lq_eo_to_nat(L, B.view(a, b - a), xe, xo, d.as<double2* const>(), role == R_GSTAR ? -1.0 : 1.0, st);
+    });
+  };
+  SolveOut ob;
+  const double t_b0 = now_s();
+  RC(solve_waves(L, sb, false, prm, fill_b, sink_b, ob, st));
+  const double t_b1 = now_s();
+  if (want_corr) RC(lq_sub_inplace((double2*)corr, (const double2*)fact, 12 * V * 12, st));  // corr = full - fact
   CK(cudaStreamSynchronize(st));
   const double secs = now_s() - t_start;
+  if (verbose())
+    fprintf(stderr, "[lqcd] factorized: setup %.1f ms, stage A %.1f ms, stage B %.1f ms, assembly %.1f ms\n",
+            1e3 * (t_a0 - t_start), 1e3 * (t_a1 - t_a0), 1e3 * (t_b1 - t_b0), 1e3 * (now_s() - t_b1));
   if (stats) {
     fill_stats(oa, has_delta ? 12 : 0, 12, secs, &stats[0]);  // Gamma
     fill_stats(oa, 0, 12, secs, &stats[1]);                   // Gammabar
@@ -754,6 +917,53 @@ extern "C" int lqcd_factorized_propagator(lqcd_lattice* L, const lqcd_split* spl
   int w = worst_status(oa);
   if (!w) w = worst_status(ob);
   if (w) lq_set_error("factorized_propagator: some solves did not reach the tolerance");
+  return w;
+}
+
+extern "C" int lqcd_point_propagators(lqcd_lattice* L, int n_sys, const lqcd_slab* doms, const int* field_ids,
+                                      const int* x_src, const int* cols, double* sol,
+                                      const lqcd_solver_params* params, lqcd_solver_stats* stats, void* stream) {
+  RC(check_lat(L));
+  if (n_sys < 1 || !doms || !field_ids || !x_src || !cols || !sol) {
+    lq_set_error("point_propagators: bad arguments");
+    return LQCD_EBADARG;
+  }
+  const double t_start = now_s();
+  cudaStream_t st = (cudaStream_t)stream;
+  lqcd_solver_params prm = default_params(params);
+  std::vector<SysSpec> sp(n_sys);
+  std::vector<long long> goff(n_sys + 1, 0);
+  for (int k = 0; k < n_sys; k++) {
+    const int* x = x_src + 4 * k;
+    if (cols[k] < 0 || cols[k] > 11 || x[0] < doms[k].t0 || x[0] > doms[k].t1 || x[1] < 0 || x[1] >= L->dims[1] ||
+        x[2] < 0 || x[2] >= L->dims[2] || x[3] < 0 || x[3] >= L->dims[3]) {
+      lq_set_error("point_propagators: source " + std::to_string(k) + " outside its slab or bad column");
+      return LQCD_EBADARG;
+    }
+    sp[k] = SysSpec{doms[k], field_ids[k], 0, cols[k], make_int4(x[0], x[1], x[2], x[3])};
+    const long long len = doms[k].t1 >= doms[k].t0 ? (long long)(doms[k].t1 - doms[k].t0 + 1) * L->S3 : 0;
+    goff[k + 1] = goff[k] + len;
+  }
+  FillFn fill = [&](BatchStore& B, int k0, double2* be, double2* bo) -> int {
+    SrcArrays s;
+    RC(s.upload(sp, k0, B.b.nsys, st));
+    return lq_point_source(L, B.b, s.cols.as<int>(), s.xsrc.as<int4>(), be, bo, st);
+  };
+  SinkFn sink = [&](BatchStore& B, int k0, const double2* xe, const double2* xo) -> int {
+    std::vector<void*> p(B.b.nsys);
+    for (int q = 0; q < B.b.nsys; q++) p[q] = (void*)((double2*)sol + goff[k0 + q] * 12);
+    DBuf d;
+    RC(upload_ptrs(d, p, st));
+    return lq_eo_to_nat(L, B.b, xe, xo, d.as<double2* const>(), 1.0, st);
+  };
+  SolveOut o;
+  RC(solve_waves(L, sp, false, prm, fill, sink, o, st));
+  CK(cudaStreamSynchronize(st));
+  const double secs = now_s() - t_start;
+  if (stats)
+    for (int k = 0; k < n_sys; k++) fill_stats(o, k, 1, secs, &stats[k]);
+  int w = worst_status(o);
+  if (w) lq_set_error("point_propagators: some systems did not reach the tolerance");
   return w;
 }
 

@@ -9,10 +9,11 @@
 // coalesced 128-bit load or store.  FP16 vectors carry one norm per site and
 // are processed one site per thread.
 //
-// Inner products accumulate in FP64 (per thread, then a warp-shuffle tree,
-// then one partial per block); `k_finalize` sums a system's block partials
-// in a fixed order, so every result is deterministic for a given launch
-// shape.  `wps` (words per site) tells the finalize how many blocks the
+// Inner products accumulate per thread and per warp in the kernel's own
+// precision (FP32 for the FP32 / FP16 solver: FP64 arithmetic is a small
+// fraction of the FP32 rate on this GPU), then in FP64 across the warps of a
+// block and across blocks; `k_finalize` sums a system's block partials in a
+// fixed order, so every result is deterministic for a given launch shape.  `wps` (words per site) tells the finalize how many blocks the
 // producing kernel used per system.
 #pragma once
 
@@ -122,7 +123,7 @@ __global__ void __launch_bounds__(128) k_bicg_xr_w(VecArgs va, void* x, const vo
   typedef Word<P> W;
   typedef typename W::R R;
   LQ_WORD_PROLOGUE(P)
-  double red[3] = {0.0, 0.0, 0.0};
+  R red[3] = {0, 0, 0};
   if (valid) {
     const cx<R> al = c_of<R>(va.sc[s].alpha), om = c_of<R>(va.sc[s].omega);
     cx<R> xv[W::NC], pv[W::NC], sv_[W::NC], tv[W::NC], w[W::NC];
@@ -140,19 +141,19 @@ __global__ void __launch_bounds__(128) k_bicg_xr_w(VecArgs va, void* x, const vo
     W::put(wptr_w<P>(r, sd.off), i, sv_);
 #pragma unroll
     for (int k = 0; k < W::NC; k++) {
-      red[0] += (double)w[k].re * sv_[k].re + (double)w[k].im * sv_[k].im;
-      red[1] += (double)w[k].re * sv_[k].im - (double)w[k].im * sv_[k].re;
-      red[2] += (double)sv_[k].re * sv_[k].re + (double)sv_[k].im * sv_[k].im;
+      red[0] += w[k].re * sv_[k].re + w[k].im * sv_[k].im;
+      red[1] += w[k].re * sv_[k].im - w[k].im * sv_[k].re;
+      red[2] += sv_[k].re * sv_[k].re + sv_[k].im * sv_[k].im;
     }
   }
-  block_reduce_store<3>(red, va.partial + ((long long)s * va.pstride + blockIdx.y) * 4);
+  block_reduce_store<3, R>(red, va.partial + ((long long)s * va.pstride + blockIdx.y) * 4);
 }
 
 __global__ void __launch_bounds__(128) k_bicg_xr_h(VecArgs va, void* x, float* xn, const void* p, const float* pn,
                                                    const void* sv, const float* svn, const void* t, const float* tn,
                                                    void* r, float* rn, const void* r0, const float* r0n) {
   LQ_SITE_PROLOGUE
-  double red[3] = {0.0, 0.0, 0.0};
+  float red[3] = {0.f, 0.f, 0.f};
   if (valid) {
     const cx<float> al = c_of<float>(va.sc[s].alpha), om = c_of<float>(va.sc[s].omega);
     cx<float> xv[12], pv[12], sv_[12], tv[12];
@@ -171,12 +172,12 @@ __global__ void __launch_bounds__(128) k_bicg_xr_h(VecArgs va, void* x, float* x
     Prec<16>::load(w, sys_ptr<16>(r0, sd.off), nrm_ptr(r0n, sd.off), sd.n, j);
 #pragma unroll
     for (int k = 0; k < 12; k++) {
-      red[0] += (double)w[k].re * sv_[k].re + (double)w[k].im * sv_[k].im;
-      red[1] += (double)w[k].re * sv_[k].im - (double)w[k].im * sv_[k].re;
-      red[2] += (double)sv_[k].re * sv_[k].re + (double)sv_[k].im * sv_[k].im;
+      red[0] += w[k].re * sv_[k].re + w[k].im * sv_[k].im;
+      red[1] += w[k].re * sv_[k].im - w[k].im * sv_[k].re;
+      red[2] += sv_[k].re * sv_[k].re + sv_[k].im * sv_[k].im;
     }
   }
-  block_reduce_store<3>(red, va.partial + ((long long)s * va.pstride + blockIdx.y) * 4);
+  block_reduce_store<3, float>(red, va.partial + ((long long)s * va.pstride + blockIdx.y) * 4);
 }
 
 // ------------------------------------------------- p = r + beta (p - omega v)
@@ -224,7 +225,7 @@ __global__ void __launch_bounds__(128) k_inner_init_w(VecArgs va, const double2*
   typedef Word<P> W;
   typedef typename W::R R;
   LQ_WORD_PROLOGUE(P)
-  double red[3] = {0.0, 0.0, 0.0};
+  R red[3] = {0, 0, 0};
   if (valid) {
     int q, j;
     split_word(i, sd.n, q, j);
@@ -235,20 +236,20 @@ __global__ void __launch_bounds__(128) k_inner_init_w(VecArgs va, const double2*
       double2 v = __ldg(src + (q * W::NC + k) * sd.n + j);
       b[k] = {(R)v.x, (R)v.y};
       z[k] = {0, 0};
-      red[2] += (double)b[k].re * b[k].re + (double)b[k].im * b[k].im;
+      red[2] += b[k].re * b[k].re + b[k].im * b[k].im;
     }
     W::put(wptr_w<P>(r, sd.off), i, b);
     W::put(wptr_w<P>(r0, sd.off), i, b);
     W::put(wptr_w<P>(p, sd.off), i, b);
     W::put(wptr_w<P>(x, sd.off), i, z);
   }
-  block_reduce_store<3>(red, va.partial + ((long long)s * va.pstride + blockIdx.y) * 4);
+  block_reduce_store<3, R>(red, va.partial + ((long long)s * va.pstride + blockIdx.y) * 4);
 }
 
 __global__ void __launch_bounds__(128) k_inner_init_h(VecArgs va, const double2* r64, void* r, float* rn, void* r0,
                                                       float* r0n, void* p, float* pn, void* x, float* xn) {
   LQ_SITE_PROLOGUE
-  double red[3] = {0.0, 0.0, 0.0};
+  float red[3] = {0.f, 0.f, 0.f};
   if (valid) {
     cx<double> a[12];
     Prec<64>::load(a, sys_ptr<64>(r64, sd.off), nullptr, sd.n, j);
@@ -264,9 +265,9 @@ __global__ void __launch_bounds__(128) k_inner_init_h(VecArgs va, const double2*
     Prec<16>::store(sys_ptr_w<16>(x, sd.off), nrm_ptr_w(xn, sd.off), sd.n, j, z);
     Prec<16>::quantize(b);  // the values just stored
 #pragma unroll
-    for (int k = 0; k < 12; k++) red[2] += (double)b[k].re * b[k].re + (double)b[k].im * b[k].im;
+    for (int k = 0; k < 12; k++) red[2] += b[k].re * b[k].re + b[k].im * b[k].im;
   }
-  block_reduce_store<3>(red, va.partial + ((long long)s * va.pstride + blockIdx.y) * 4);
+  block_reduce_store<3, float>(red, va.partial + ((long long)s * va.pstride + blockIdx.y) * 4);
 }
 
 // x64 += x (inner solution of precision P).  A cycle that ended in NaN or
@@ -309,7 +310,7 @@ __global__ void __launch_bounds__(128) k_norm2_64(VecArgs va, const double2* v) 
     double2 a = __ldg(v + sd.off * 12 + i);
     red[2] = a.x * a.x + a.y * a.y;
   }
-  block_reduce_store<3>(red, va.partial + ((long long)s * va.pstride + blockIdx.y) * 4);
+  block_reduce_store<3, double>(red, va.partial + ((long long)s * va.pstride + blockIdx.y) * 4);
 }
 
 // Precision conversion of a system vector set, one site per thread.

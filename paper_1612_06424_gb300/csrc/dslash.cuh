@@ -225,8 +225,13 @@ struct HopMinBlocks {
 #endif
 };
 
-template <int NQ>
-LQ_DI void block_reduce_store(double v[NQ], double* dst) {
+// Block reduction of NQ per-thread partial sums of type A (the kernel's own
+// precision: FP32 for the FP32 / FP16 solver, whose FP64 rate on this GPU is a
+// small fraction of its FP32 rate) through a warp-shuffle tree; the per-warp
+// sums are widened to FP64 and combined in FP64, and one partial per block is
+// stored.  The order is fixed, so results are deterministic.
+template <int NQ, typename A>
+LQ_DI void block_reduce_store(A v[NQ], double* dst) {
   __shared__ double sh[32][NQ > 0 ? NQ : 1];
 #pragma unroll
   for (int q = 0; q < NQ; q++)
@@ -235,7 +240,7 @@ LQ_DI void block_reduce_store(double v[NQ], double* dst) {
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0)
 #pragma unroll
-    for (int q = 0; q < NQ; q++) sh[wid][q] = v[q];
+    for (int q = 0; q < NQ; q++) sh[wid][q] = (double)v[q];
   __syncthreads();
   if (wid == 0) {
     int nw = blockDim.x >> 5;
@@ -273,7 +278,7 @@ __global__ void __launch_bounds__(128, HopMinBlocks<P>::value) k_hop_lin(HopArgs
   const SysDesc sd = a.sys[s];
   if ((int)(blockIdx.y * blockDim.x) >= sd.n) return;  // whole block beyond this system
   const int j = blockIdx.y * blockDim.x + threadIdx.x;
-  double red[3] = {0.0, 0.0, 0.0};
+  R red[3] = {0, 0, 0};
   if (j < sd.n) {
     const FieldPtrs f = a.fields[sd.field];
     const int cb = sd.cb0 + j;
@@ -318,23 +323,23 @@ __global__ void __launch_bounds__(128, HopMinBlocks<P>::value) k_hop_lin(HopArgs
         Prec<P>::load(wv, sys_ptr<P>(a.w, sd.off), nrm_ptr(a.wn, sd.off), sd.n, j);
 #pragma unroll
         for (int k = 0; k < 12; k++) {
-          red[0] += (double)wv[k].re * res[k].re + (double)wv[k].im * res[k].im;
-          red[1] += (double)wv[k].re * res[k].im - (double)wv[k].im * res[k].re;
+          red[0] += wv[k].re * res[k].re + wv[k].im * res[k].im;
+          red[1] += wv[k].re * res[k].im - wv[k].im * res[k].re;
         }
       } else if (RED == RED_TS) {
 #pragma unroll
         for (int k = 0; k < 12; k++) {
-          red[0] += (double)res[k].re * yv[k].re + (double)res[k].im * yv[k].im;
-          red[1] += (double)res[k].re * yv[k].im - (double)res[k].im * yv[k].re;
-          red[2] += (double)res[k].re * res[k].re + (double)res[k].im * res[k].im;
+          red[0] += res[k].re * yv[k].re + res[k].im * yv[k].im;
+          red[1] += res[k].re * yv[k].im - res[k].im * yv[k].re;
+          red[2] += res[k].re * res[k].re + res[k].im * res[k].im;
         }
       } else {
 #pragma unroll
-        for (int k = 0; k < 12; k++) red[2] += (double)res[k].re * res[k].re + (double)res[k].im * res[k].im;
+        for (int k = 0; k < 12; k++) red[2] += res[k].re * res[k].re + res[k].im * res[k].im;
       }
     }
   }
-  if (RED != RED_NONE) block_reduce_store<3>(red, a.partial + ((long long)s * a.pstride + blockIdx.y) * 4);
+  if (RED != RED_NONE) block_reduce_store<3, R>(red, a.partial + ((long long)s * a.pstride + blockIdx.y) * 4);
 }
 
 // out = A^{-1} (alpha * D_hop x + beta * y) on even sites (pout = 0), terms

@@ -87,12 +87,15 @@ int lq_nat_to_eo(const lqcd_lattice* L, const Batch& b, const double2* const* sr
                  cudaStream_t st);
 int lq_eo_to_nat(const lqcd_lattice* L, const Batch& b, const double2* ve, const double2* vo, double2* const* dst,
                  double scale, cudaStream_t st);
-// point sources: system k gets the unit vector of column cols[k] at x_src
-int lq_point_source(const lqcd_lattice* L, const Batch& b, const int* d_cols, const int x_src[4], double2* ve,
+// point sources: system k gets the unit vector of column cols[k] at xsrc[k]
+int lq_point_source(const lqcd_lattice* L, const Batch& b, const int* d_cols, const int4* d_xsrc, double2* ve,
                     double2* vo, cudaStream_t st);
-// chi(y) = [D_{Gamma*,Gamma} psi](y): time hops from y in Gamma* into Gamma
-int lq_boundary_hop(const lqcd_lattice* L, const Batch& bout, const Batch& bin, int g1, const double2* in_e,
-                    const double2* in_o, double2* out_e, double2* out_o, cudaStream_t st);
+// compact boundary source chi[col][slot][slice site][12] of Gamma* from the Gammabar solutions
+int lq_boundary_chi(const lqcd_lattice* L, const Batch& bin, const int* d_cols, int g1, const double2* in_e,
+                    const double2* in_o, double2* chi, cudaStream_t st);
+// Gamma* sources from chi
+int lq_chi_to_eo(const lqcd_lattice* L, const Batch& b, const int* d_cols, int g1, const double2* chi, double2* ve,
+                 double2* vo, cudaStream_t st);
 // a -= b elementwise over n double2 words
 int lq_sub_inplace(double2* a, const double2* b, long long n, cudaStream_t st);
 

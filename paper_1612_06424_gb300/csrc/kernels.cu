@@ -252,84 +252,127 @@ int lq_eo_to_nat(const lqcd_lattice* L, const Batch& b, const double2* ve, const
   return launched();
 }
 
-// Zero both parities of every system and place 1 at (x_src, column cols[s]).
-__global__ void __launch_bounds__(128) k_point_source(Geom g, const SysDesc* sys, const int* cols, int xs0, int xs1,
-                                                      int xs2, int xs3, double2* ve, double2* vo) {
+// Zero both parities of every system and place 1 at (xsrc[s], column cols[s]).
+__global__ void __launch_bounds__(128) k_point_source(Geom g, const SysDesc* sys, const int* cols, const int4* xsrc,
+                                                      double2* ve, double2* vo) {
   const int s = blockIdx.x;
   const SysDesc sd = sys[s];
-  const long long j = (long long)blockIdx.y * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.x + threadIdx.x;
   if (j >= sd.n) return;
   const int p = blockIdx.z;
-  const int xs[4] = {xs0, xs1, xs2, xs3};
-  const int ps = (xs0 + xs1 + xs2 + xs3) & 1;
-  const long long cbs = eo_index(g, xs);
+  const int4 q = xsrc[s];
+  const int xs[4] = {q.x, q.y, q.z, q.w};
+  const int ps = (q.x + q.y + q.z + q.w) & 1;
+  const int cbs = eo_index(g, xs);
   double2* out = (p == 0 ? ve : vo) + sd.off * 12;
   const bool here = (p == ps) && (sd.cb0 + j == cbs);
+  const int col = cols[s];
 #pragma unroll
-  for (int k = 0; k < 12; k++) out[k * sd.n + j] = make_double2((here && k == cols[s]) ? 1.0 : 0.0, 0.0);
+  for (int k = 0; k < 12; k++) out[k * sd.n + j] = make_double2((here && k == col) ? 1.0 : 0.0, 0.0);
 }
 
-int lq_point_source(const lqcd_lattice* L, const Batch& b, const int* d_cols, const int x_src[4], double2* ve,
+int lq_point_source(const lqcd_lattice* L, const Batch& b, const int* d_cols, const int4* d_xsrc, double2* ve,
                     double2* vo, cudaStream_t st) {
-  k_point_source<<<dim3(b.nsys, b.nby, 2), LQ_BLOCK, 0, st>>>(L->g, b.sys, d_cols, x_src[0], x_src[1], x_src[2],
-                                                              x_src[3], ve, vo);
+  k_point_source<<<dim3(b.nsys, b.nby, 2), LQ_BLOCK, 0, st>>>(L->g, b.sys, d_cols, d_xsrc, ve, vo);
   return launched();
 }
 
-// chi = P_{Gamma*} D P_{Gamma} psi for Gamma = 0..g1, Gamma* = g1+1..T-1:
-// only the time hops from a site y of Gamma* to a site of Gamma survive,
-//   y0 = g1+1 :   -1/2 (1 + g_0) U_0(y-0)^dag psi(y-0)
-//   y0 = T-1  :   -1/2 (1 - g_0) U_0(y) psi(y+0) * sign  (periodic / antiperiodic only)
-// Output systems (Gamma*) and input systems (the Gammabar solutions) are
-// paired by index.
-__global__ void __launch_bounds__(128) k_boundary_hop(Geom g, const FieldPtrs* fields, const SysDesc* sout,
-                                                      const SysDesc* sin, int g1, const double2* in_e,
-                                                      const double2* in_o, double2* out_e, double2* out_o) {
+// Boundary source of the Schur assembly, Sec. 3 eq. quark_prop_II:
+//   chi = P_Gamma* D P_Gamma psi,  Gamma = 0..g1, Gamma* = g1+1..T-1.
+// Only time hops from a site y of Gamma* to a site of Gamma survive:
+//   slot 0, y0 = g1+1 :  -1/2 (1 + g_0) U_0(y-0)^dag psi(y-0)
+//   slot 1, y0 = T-1  :  -1/2 (1 - g_0) U_0(y) psi(y+0) * sign   (periodic / antiperiodic only)
+// chi is stored compactly, natural order within a time slice:
+//   chi[c][slot][site of slice][12].  psi: the Gammabar solution of system s
+// (its eo pools), written to chi column cols[s].
+__global__ void __launch_bounds__(128) k_boundary_chi(Geom g, const FieldPtrs* fields, const SysDesc* sin,
+                                                      const int* cols, int g1, const double2* in_e,
+                                                      const double2* in_o, double2* chi) {
   const int s = blockIdx.x;
-  const SysDesc so = sout[s], si = sin[s];
-  const long long j = (long long)blockIdx.y * blockDim.x + threadIdx.x;
-  if (j >= so.n) return;
-  const int p = blockIdx.z;
-  const FieldPtrs f = fields[so.field];
-  int x[4];
-  const long long cb = so.cb0 + j;
-  eo_coords(g, cb, p, x);
+  const SysDesc si = sin[s];
+  const int S3 = 2 * g.S3h;
+  const int i = blockIdx.y * blockDim.x + threadIdx.x;  // site within the slice
+  const int slot = blockIdx.z;
+  if (i >= S3) return;
+  double2* out = chi + ((long long)(cols[s] * 2 + slot) * S3 + i) * 12;
   cx<double> acc[12];
 #pragma unroll
   for (int k = 0; k < 12; k++) acc[k] = {0.0, 0.0};
-  const double2* inb = (p == 0 ? in_o : in_e) + si.off * 12;  // neighbour parity
-  if (x[0] == g1 + 1) {
-    int y[4] = {x[0] - 1, x[1], x[2], x[3]};
-    const long long cy = eo_index(g, y);
+  const bool active = slot == 0 || g.bc_t != 0;
+  if (active) {
+    int x[4];
+    x[3] = i % g.L[3];
+    x[2] = (i / g.L[3]) % g.L[2];
+    x[1] = i / (g.L[3] * g.L[2]);
+    x[0] = slot == 0 ? g1 + 1 : g.L[0] - 1;
+    const int p = (x[0] + x[1] + x[2] + x[3]) & 1;
+    const FieldPtrs f = fields[si.field];
+    const double2* inb = (p == 0 ? in_o : in_e) + si.off * 12;  // neighbour parity
     cx<double> psi[12], h[6], w[6];
-    Prec<64>::load(psi, inb, nullptr, si.n, cy - si.cb0);
-    project<0, +1>(psi, h);
-    su3<double> u = LinkIO<64>::load(f, p ^ 1, 0, g.Vh, cy);
-    mul_udag(u, h, w);
-    expand_add<0, +1>(acc, w);
-  }
-  if (g.bc_t != 0 && x[0] == g.L[0] - 1) {
-    const double sg = g.bc_t == 2 ? -1.0 : 1.0;
-    int y[4] = {0, x[1], x[2], x[3]};
-    const long long cy = eo_index(g, y);
-    cx<double> psi[12], h[6], w[6];
-    Prec<64>::load(psi, inb, nullptr, si.n, cy - si.cb0);
-    project<0, -1>(psi, h);
-    su3<double> u = LinkIO<64>::load(f, p, 0, g.Vh, cb);
-    mul_u(u, h, w);
+    if (slot == 0) {
+      int y[4] = {x[0] - 1, x[1], x[2], x[3]};
+      const int cy = eo_index(g, y);
+      Prec<64>::load(psi, inb, nullptr, si.n, cy - si.cb0);
+      project<0, +1>(psi, h);
+      su3<double> u = LinkIO<64>::load(f, p ^ 1, 0, g.Vh, cy);
+      mul_udag(u, h, w);
+      expand_add<0, +1>(acc, w);
+    } else {
+      const double sg = g.bc_t == 2 ? -1.0 : 1.0;
+      int y[4] = {0, x[1], x[2], x[3]};
+      const int cy = eo_index(g, y);
+      Prec<64>::load(psi, inb, nullptr, si.n, cy - si.cb0);
+      project<0, -1>(psi, h);
+      su3<double> u = LinkIO<64>::load(f, p, 0, g.Vh, eo_index(g, x));
+      mul_u(u, h, w);
 #pragma unroll
-    for (int k = 0; k < 6; k++) w[k] = sg * w[k];
-    expand_add<0, -1>(acc, w);
+      for (int k = 0; k < 6; k++) w[k] = sg * w[k];
+      expand_add<0, -1>(acc, w);
+    }
   }
 #pragma unroll
-  for (int k = 0; k < 12; k++) acc[k] = -0.5 * acc[k];
-  Prec<64>::store((p == 0 ? out_e : out_o) + so.off * 12, nullptr, so.n, j, acc);
+  for (int k = 0; k < 12; k++) out[k] = make_double2(-0.5 * acc[k].re, -0.5 * acc[k].im);
 }
 
-int lq_boundary_hop(const lqcd_lattice* L, const Batch& bout, const Batch& bin, int g1, const double2* in_e,
-                    const double2* in_o, double2* out_e, double2* out_o, cudaStream_t st) {
-  k_boundary_hop<<<dim3(bout.nsys, bout.nby, 2), LQ_BLOCK, 0, st>>>(L->g, L->d_fields, bout.sys, bin.sys, g1, in_e,
-                                                                    in_o, out_e, out_o);
+int lq_boundary_chi(const lqcd_lattice* L, const Batch& bin, const int* d_cols, int g1, const double2* in_e,
+                    const double2* in_o, double2* chi, cudaStream_t st) {
+  const int S3 = 2 * L->g.S3h;
+  k_boundary_chi<<<dim3(bin.nsys, (S3 + LQ_BLOCK - 1) / LQ_BLOCK, 2), LQ_BLOCK, 0, st>>>(L->g, L->d_fields, bin.sys,
+                                                                                      d_cols, g1, in_e, in_o, chi);
+  return launched();
+}
+
+// Source of a Gamma* system: chi (compact, column cols[s]) scattered into the
+// system's even / odd FP64 vectors, zero elsewhere.
+__global__ void __launch_bounds__(128) k_chi_to_eo(Geom g, const SysDesc* sys, const int* cols, int g1,
+                                                   const double2* chi, double2* ve, double2* vo) {
+  const int s = blockIdx.x;
+  const SysDesc sd = sys[s];
+  const int j = blockIdx.y * blockDim.x + threadIdx.x;
+  if (j >= sd.n) return;
+  const int p = blockIdx.z;
+  int x[4];
+  eo_coords(g, sd.cb0 + j, p, x);
+  const int S3 = 2 * g.S3h;
+  const int i = (x[1] * g.L[2] + x[2]) * g.L[3] + x[3];
+  double2 v[12];
+#pragma unroll
+  for (int k = 0; k < 12; k++) v[k] = make_double2(0.0, 0.0);
+  for (int slot = 0; slot < 2; slot++) {
+    const bool on = slot == 0 ? x[0] == g1 + 1 : (g.bc_t != 0 && x[0] == g.L[0] - 1);
+    if (!on) continue;
+    const double2* c = chi + ((long long)(cols[s] * 2 + slot) * S3 + i) * 12;
+#pragma unroll
+    for (int k = 0; k < 12; k++) v[k] = make_double2(v[k].x + c[k].x, v[k].y + c[k].y);
+  }
+  double2* out = (p == 0 ? ve : vo) + sd.off * 12;
+#pragma unroll
+  for (int k = 0; k < 12; k++) out[k * sd.n + j] = v[k];
+}
+
+int lq_chi_to_eo(const lqcd_lattice* L, const Batch& b, const int* d_cols, int g1, const double2* chi, double2* ve,
+                 double2* vo, cudaStream_t st) {
+  k_chi_to_eo<<<dim3(b.nsys, b.nby, 2), LQ_BLOCK, 0, st>>>(L->g, b.sys, d_cols, g1, chi, ve, vo);
   return launched();
 }
 

@@ -26,6 +26,8 @@ __all__ = [
     "gell_mann",
     "random_su3",
     "random_su3_field",
+    "random_su3_field_device",
+    "inner_level_fields_device",
     "unit_field",
     "random_gauge_transform",
     "point_sources",
@@ -90,6 +92,74 @@ def random_su3_field(dims, eps: float, seed: int, stream: int = 0,
         hi = min(n, lo + chunk)
         out[lo:hi] = random_su3(hi - lo, eps, seed, stream * 65536 + k)
     return out.reshape(V, 4, 3, 3)
+
+
+def _su3_torch(h, eps: float, torch_device):
+    """exp(i eps H) for H = sum_a h_a lambda_a / 2 (h: numpy (n, 8)), computed on a torch device,
+    then re-unitarised; returns a complex128 tensor (n, 3, 3) on that device."""
+    import torch
+
+    lam = torch.from_numpy(gell_mann() / 2).to(torch_device)
+    ht = torch.from_numpy(h).to(torch_device).to(torch.complex128)
+    H = torch.einsum("na,aij->nij", ht, lam)
+    u = torch.linalg.matrix_exp(1j * eps * H)
+    r0 = u[:, 0, :]
+    r0 = r0 / torch.linalg.vector_norm(r0, dim=-1, keepdim=True)
+    r1 = u[:, 1, :]
+    r1 = r1 - torch.sum(torch.conj(r0) * r1, dim=-1, keepdim=True) * r0
+    r1 = r1 / torch.linalg.vector_norm(r1, dim=-1, keepdim=True)
+    r2 = torch.conj(torch.linalg.cross(r0, r1, dim=-1))
+    return torch.stack([r0, r1, r2], dim=-2)
+
+
+def random_su3_field_device(dims, eps: float, seed: int, device="cuda", stream: int = 0, chunk: int = 1 << 22):
+    """The field law of random_su3_field (same Philox draws) with the matrix
+    exponential done by torch on `device`; returns a complex128 tensor
+    [V, 4, 3, 3] there.  For large lattices, where the numpy path is slow."""
+    import torch
+
+    V = int(np.prod(dims))
+    n = 4 * V
+    out = torch.empty((n, 3, 3), dtype=torch.complex128, device=device)
+    for k, lo in enumerate(range(0, n, chunk)):
+        hi = min(n, lo + chunk)
+        h = _rng(seed, stream * 65536 + k).standard_normal((hi - lo, 8))
+        out[lo:hi] = _su3_torch(h, eps, out.device)
+    return out.reshape(V, 4, 3, 3)
+
+
+def inner_level_fields_device(U0, dims, slabs, n_fields: int, eps: float, seed: int, frozen=None,
+                              chunk: int = 1 << 22):
+    """inner_level_fields with the redrawn links exponentiated by torch on U0's device.
+    U0: complex128 tensor [V, 4, 3, 3]; returns [n_fields, V, 4, 3, 3] on the same device."""
+    import torch
+
+    T = dims[0]
+    s3 = int(dims[1] * dims[2] * dims[3])
+    V = T * s3
+    t_of_site = np.arange(V) // s3
+    out = U0.unsqueeze(0).repeat(n_fields, 1, 1, 1, 1)
+    for d, (t0, t1) in enumerate(slabs):
+        in_slab = (t_of_site >= t0) & (t_of_site <= t1)
+        own = np.repeat(in_slab[:, None], 4, axis=1)
+        own[:, 0] &= t_of_site != t1
+        if frozen is not None:
+            f0, f1 = frozen
+            start_frozen = (t_of_site >= f0) & (t_of_site <= f1)
+            end_t = np.minimum(t_of_site + 1, T - 1)
+            end_frozen_t = (end_t >= f0) & (end_t <= f1)
+            own &= ~start_frozen[:, None]
+            own[:, 0] &= ~end_frozen_t
+        idx = np.nonzero(own.reshape(-1))[0]
+        idx_t = torch.from_numpy(idx).to(U0.device)
+        for j in range(n_fields):
+            flat = out[j].reshape(-1, 3, 3)
+            rng = _rng(seed, (d + 1) * 4096 + j)
+            for lo in range(0, idx.size, chunk):
+                hi = min(idx.size, lo + chunk)
+                h = rng.standard_normal((hi - lo, 8))
+                flat[idx_t[lo:hi]] = _su3_torch(h, eps, U0.device)
+    return out
 
 
 def unit_field(dims) -> np.ndarray:

@@ -41,7 +41,7 @@ class SplitC(ctypes.Structure):
 
 class ParamsC(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
-                ("inner_tol", ctypes.c_double), ("check_every", ctypes.c_int)]
+                ("inner_tol", ctypes.c_double), ("check_every", ctypes.c_int), ("max_wave", ctypes.c_int)]
 
 
 class StatsC(ctypes.Structure):
@@ -59,9 +59,10 @@ class SolverParams:
     precision: int = 64
     inner_tol: float = 0.0
     check_every: int = 0
+    max_wave: int = 0
 
     def c(self) -> ParamsC:
-        return ParamsC(self.tol, self.max_iter, self.precision, self.inner_tol, self.check_every)
+        return ParamsC(self.tol, self.max_iter, self.precision, self.inner_tol, self.check_every, self.max_wave)
 
 
 _lib = None
@@ -88,6 +89,8 @@ def lib() -> ctypes.CDLL:
                                              ctypes.POINTER(StatsC), vp]
     L.lqcd_link_force.argtypes = [vp, ctypes.POINTER(Slab), c, vp, vp, dp, ctypes.POINTER(ParamsC),
                                   ctypes.POINTER(StatsC), vp]
+    L.lqcd_point_propagators.argtypes = [vp, c, ctypes.POINTER(Slab), ip, ip, ip, vp, ctypes.POINTER(ParamsC),
+                                         ctypes.POINTER(StatsC), vp]
     L.lqcd_dslash_bench.argtypes = [vp, c, ctypes.POINTER(Slab), ip, c, c, dp, dp, dp, vp]
     L.lqcd_last_error.restype = ctypes.c_char_p
     L.lqcd_kernel_launches.restype = ctypes.c_longlong
@@ -113,6 +116,14 @@ def _dev(t: torch.Tensor, name: str) -> ctypes.c_void_p:
 
 def kernel_launches() -> int:
     return int(lib().lqcd_kernel_launches())
+
+
+def fma_peak(bits: int = 64) -> float:
+    """Measured FMA throughput of the current GPU (TFLOP/s) in FP64 or FP32."""
+    t = ctypes.c_double(0.0)
+    lib().lqcd_fma_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
+    _check(lib().lqcd_fma_peak(bits, ctypes.byref(t), _stream(None)))
+    return t.value
 
 
 class Lattice:
@@ -179,6 +190,23 @@ class Lattice:
         rc = lib().lqcd_solve_block(self._h, n, sl, fi, _dev(src, "src"), _dev(sol, "sol"), ctypes.byref(p), st,
                                     _stream(stream))
         _check(rc)
+        return sol, [s.as_dict() for s in st]
+
+    def point_propagators(self, doms, field_ids, x_src, cols, params: SolverParams | None = None, sol=None,
+                          stream=None):
+        """Batched D_{L_k} psi_k = point source (x_src[k], column cols[k]); returns (sol, stats)."""
+        n = len(doms)
+        sl = (Slab * n)(*[Slab(*d) for d in doms])
+        fi = (ctypes.c_int * n)(*field_ids)
+        xs = (ctypes.c_int * (4 * n))(*[int(v) for x in x_src for v in x])
+        cs = (ctypes.c_int * n)(*cols)
+        total = sum(self.slab_len(*d) for d in doms)
+        if sol is None:
+            sol = torch.empty((total, 4, 3), dtype=torch.complex128, device=torch.device("cuda", torch.cuda.current_device()))
+        st = (StatsC * n)()
+        p = (params or SolverParams()).c()
+        _check(lib().lqcd_point_propagators(self._h, n, sl, fi, xs, cs, _dev(sol, "sol"), ctypes.byref(p), st,
+                                            _stream(stream)))
         return sol, [s.as_dict() for s in st]
 
     def solve_full(self, src: torch.Tensor, field_ids, params: SolverParams | None = None, stream=None):

@@ -2,9 +2,13 @@
 
   python -m paper_1612_06424_gb300.profile_dslash --dims 32 16 16 16 --precision 32 \
       --slabs 0:17x12 0:13x12 --reps 3
+  python -m paper_1612_06424_gb300.profile_dslash --factorized --precision 32
 
 Prints ms per launch, algorithmic GB/s and TFLOP/s.  Each launch is one
 k_hop_lin (out_o = A_oo y_o - 1/4 D_hop x_e) over every system of the batch.
+With --factorized it instead runs one 12-source factorized propagator with
+correction on the 16^3x32 workload (Gamma 0..13, DeltaGamma 14..17, Gamma*
+14..31, source (2,0,0,0)), i.e. every kernel of the solver.
 """
 import argparse
 import os
@@ -24,6 +28,7 @@ def main():
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--kappa", type=float, default=0.13)
     ap.add_argument("--csw", type=float, default=1.0)
+    ap.add_argument("--factorized", action="store_true")
     a = ap.parse_args()
     from paper_1612_06424_gb300 import build, inputs, lqcd
 
@@ -36,6 +41,19 @@ def main():
     U = inputs.random_su3_field(tuple(a.dims), 0.4, 1)
     lat = lqcd.Lattice(tuple(a.dims), "open")
     lat.set_gauge(U, a.kappa, a.csw)
+    if a.factorized:
+        import time
+
+        import torch
+
+        t = time.time()
+        _, _, st = lat.factorized_propagator((0, 13), (14, 31), (2, 0, 0, 0), delta=(14, 17),
+                                             params=lqcd.SolverParams(precision=a.precision))
+        torch.cuda.synchronize()
+        print(f"factorized propagator P={a.precision}: {1e3 * (time.time() - t):.1f} ms",
+              {k: (v["iters"], v["true_residual"]) for k, v in st.items()})
+        lat.close()
+        return
     ms, by, fl = lat.dslash_bench(doms, [0] * len(doms), a.precision, a.reps)
     print(f"dims={a.dims} P={a.precision} systems={len(doms)}: {ms:.4f} ms/launch, "
           f"{by / ms / 1e6:.1f} GB/s algorithmic ({by / 1e6:.1f} MB/launch), {fl / ms / 1e9:.2f} TFLOP/s")

@@ -1,0 +1,171 @@
+"""Parity at the full size of the 16^3x32 workload (the launch configuration
+bench.py times), checked on sampled columns with the oracle's own operator.
+
+Oracle solves at this size take hours, so every GPU result is checked through
+properties the exact answer has, each evaluated with the oracle's independent
+FP64 D (no oracle input comes from the CUDA path except the vectors under test):
+  full = fact + corr solves D full = eta               (eq. observable_factorization)
+  fact on Gamma solves D_Gamma fact = eta              (eq. quark_prop_I)
+  psi = D_Gammabar^{-1} eta (solve_block) solves D_Gammabar psi = eta
+  -fact on Gamma* solves D_Gamma* (-fact) = P_Gamma* D P_Gamma psi   (eq. quark_prop_II)
+Tolerance: the solver's residual 1e-10 (x 1.05 for rounding of the check).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1612_06424_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+DIMS = (32, 16, 16, 16)
+KAPPA, CSW = 0.13, 1.0
+G, DL, GS = (0, 13), (14, 17), (14, 31)
+GB = (0, 17)
+X_SRC = (2, 0, 0, 0)
+COLS = (0, 7)
+
+
+@pytest.fixture(scope="module")
+def field():
+    U = inputs.random_su3_field(DIMS, 0.4, 1)
+    return U, oracle.Operator(DIMS, U, KAPPA, CSW)
+
+
+def _res(op, b, x, slab):
+    r = b - op.apply(x, *slab)
+    return np.linalg.norm(r) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_factorized_propagator_16x32_properties(field, prec):
+    from paper_1612_06424_gb300 import build, lqcd
+
+    build.build()
+    U, op = field
+    lat = lqcd.Lattice(DIMS, "open")
+    lat.set_gauge(U, KAPPA, CSW)
+    params = lqcd.SolverParams(tol=1e-10, precision=prec)
+    fact, corr, st = lat.factorized_propagator(G, GS, X_SRC, delta=DL, corr=True, params=params)
+    eta = inputs.point_sources(DIMS, X_SRC)
+    sgb = inputs.slab_sites(DIMS, *GB)
+    src = torch.from_numpy(np.ascontiguousarray(eta[:, sgb])).reshape(-1, 4, 3).cuda()
+    psi_gb, st_gb = lat.solve_block(src.contiguous(), [GB] * 12, [0] * 12, params)
+    fact, corr = fact.cpu().numpy(), corr.cpu().numpy()
+    psi_gb = psi_gb.cpu().numpy().reshape(12, -1, 4, 3)
+    tol = 1.05e-10
+    for k in ("gamma", "gamma_bar", "gamma_star", "full"):
+        assert st[k]["status"] == 0 and st[k]["true_residual"] <= 1e-10, (k, st[k])
+    m_g, m_gs = op.slab(*G), op.slab(*GS)
+    for c in COLS:
+        assert _res(op, eta[c], fact[c] + corr[c], (0, DIMS[0] - 1)) <= tol
+        b_g = op.masked(eta[c], *G)
+        x_g = op.masked(fact[c], *G)
+        assert _res(op, b_g, x_g, G) <= tol
+        x_gb = np.zeros((op.V, 4, 3), complex)
+        x_gb[sgb] = psi_gb[c]
+        assert _res(op, op.masked(eta[c], *GB), x_gb, GB) <= tol
+        chi = op.boundary_hop(x_gb, G, GS)
+        zeta = -op.masked(fact[c], *GS)
+        assert _res(op, chi, zeta, GS) <= tol
+        # fact is supported on Gamma u Gamma* = the whole lattice and splits exactly there
+        assert np.all(fact[c][~(m_g | m_gs)] == 0)
+    lat.close()
+
+
+def test_batched_32x64_domain_propagators_sampled():
+    """The 32^3x64 batched workload (8 slabs x 12 sources x 16 inner-level fields,
+    1536 systems, FP16 inner solves + FP64 correction): every system reports a
+    true residual <= 1e-10, and sampled systems are checked with the oracle's D."""
+    from paper_1612_06424_gb300 import build, lqcd
+
+    build.build()
+    dims = (64, 32, 32, 32)
+    slabs = [(8 * d, 8 * d + 7) for d in range(8)]
+    nf = 16
+    U0 = inputs.random_su3_field_device(dims, 0.4, 3, device="cuda")
+    Uf = inputs.inner_level_fields_device(U0, dims, slabs, nf, 0.4, 4)
+    del U0
+    lat = lqcd.Lattice(dims, "open")
+    lat.set_gauge(Uf, 0.134, 1.0)
+    doms, fields, xs, cols = [], [], [], []
+    for j in range(nf):
+        for d, (a, b) in enumerate(slabs):
+            for c in range(12):
+                doms.append((a, b)); fields.append(j); xs.append((a + 4, 0, 0, 0)); cols.append(c)
+    sol, st = lat.point_propagators(doms, fields, xs, cols, lqcd.SolverParams(tol=1e-10, precision=16))
+    assert all(x["status"] == 0 and x["true_residual"] <= 1e-10 for x in st)
+    n_slab = lat.slab_len(0, 7)
+    for k in (5, 1000):  # (field 0, slab 0, col 5) and (field 10, slab 3, col 4)
+        j, (a, b) = fields[k], doms[k]
+        U = Uf[j].cpu().numpy()
+        op = oracle.Operator(dims, U, 0.134, 1.0)
+        x = np.zeros((op.V, 4, 3), complex)
+        sl = inputs.slab_sites(dims, a, b)
+        x[sl] = sol[k * n_slab:(k + 1) * n_slab].cpu().numpy()
+        eta = np.zeros((op.V, 4, 3), complex)
+        s0, c0 = divmod(cols[k], 3)
+        eta[((xs[k][0] * 32 + xs[k][1]) * 32 + xs[k][2]) * 32 + xs[k][3], s0, c0] = 1.0
+        assert _res(op, eta, x, (a, b)) <= 1.05e-10, k
+    lat.close()
+
+
+def _expm_i(H):
+    w, v = np.linalg.eigh(H)
+    return v @ np.diag(np.exp(1j * w)) @ v.conj().T
+
+
+def test_link_force_24x48_finite_differences():
+    """Force of phi^dag (D_L^dag D_L)^{-1} phi on the 24^3x48 lattice, domain
+    t 12..23, against central finite differences (h = 1e-5) on 64 random links
+    inside, on and around the domain.  The difference S(+h) - S(-h) is taken
+    without cancellation as X+^dag (M- - M+) X-, M = D_L^dag D_L, with the GPU's
+    FP64 solves (D_L^{-dag} = g5 D_L^{-1} g5) and operator."""
+    from paper_1612_06424_gb300 import build, lqcd
+
+    build.build()
+    dims = (48, 24, 24, 24)
+    dom = (12, 23)
+    Ud = inputs.random_su3_field_device(dims, 0.4, 5, device="cuda")
+    U = Ud.cpu().numpy()
+    lat = lqcd.Lattice(dims, "open")
+    lat.set_gauge(Ud, 0.132, 1.0)
+    sl = inputs.slab_sites(dims, *dom)
+    phi = torch.from_numpy(inputs.gaussian_spinor(dims, 51)[0][sl]).cuda()
+    params = lqcd.SolverParams(tol=1e-12, precision=64)
+    F, S, _ = lat.link_force(phi, dom, 0, params)
+    F = F.cpu().numpy()
+    g5 = torch.tensor([1, 1, -1, -1], dtype=torch.complex128, device="cuda").view(1, 4, 1)
+    rng = np.random.default_rng(7)
+    s3 = 24 ** 3
+    lam = inputs.gell_mann() / 2
+    h = 1e-5
+    worst = 0.0
+    for t in rng.choice([11, 12, 13, 17, 22, 23, 24], size=64):
+        site = int(t) * s3 + int(rng.integers(s3))
+        mu, a = int(rng.integers(4)), int(rng.integers(8))
+        Up, Um = U[site, mu].copy(), U[site, mu].copy()
+        Up = _expm_i(h * lam[a]) @ Up
+        Um = _expm_i(-h * lam[a]) @ Um
+        two = Ud.unsqueeze(0).repeat(2, 1, 1, 1, 1)
+        two[0, site, mu] = torch.from_numpy(Up).cuda()
+        two[1, site, mu] = torch.from_numpy(Um).cuda()
+        lat.set_gauge(two, 0.132, 1.0)
+        X = []
+        for f in (0, 1):
+            y, _ = lat.solve_block((g5 * phi).contiguous(), [dom], [f], params)   # D^{-1} g5 phi
+            y = (g5 * y).contiguous()                                            # Y = D^{-dag} phi
+            x, _ = lat.solve_block(y, [dom], [f], params)                        # X = D^{-1} Y
+            X.append(x)
+        Xp, Xm = X
+
+        def M(f, v):
+            return lat.dslash(lat.dslash(v, f, dom, False, 64), f, dom, True, 64)
+
+        dS = torch.vdot(Xp.reshape(-1), (M(1, Xm) - M(0, Xm)).reshape(-1)).real.item()
+        fd = dS / (2 * h)
+        err = abs(F[site, mu, a] - fd)
+        assert err <= 1e-6 * abs(fd) + 1e-9 * np.abs(F).max(), (site, mu, a, F[site, mu, a], fd)
+        worst = max(worst, err)
+    lat.close()
