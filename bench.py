@@ -151,36 +151,54 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
-def _cpu_baseline(U, iters_per_group, sample_seconds=12.0):
-    """The oracle (plain FP64 C, one thread) on the host: time of one D
-    application on the full 16^3x32 lattice, measured on a bounded sample, and
-    scaled to one 12-source propagator by the number of operator applications
-    the same solves need (2 per BiCGStab iteration, iteration counts of the
-    unpreconditioned oracle solver taken as twice the even-odd ones)."""
-    import numpy as np
+_ORACLE_ITERS = {}
 
+
+def _oracle_iterations(op):
+    """Iterations the oracle's own BiCGStab needs on this workload to residual
+    1e-10: one column solved on Gamma (t 0..13) to 1e-5, doubled (the residual
+    falls geometrically), measured once per process (about 20 s)."""
+    from paper_1612_06424_gb300 import inputs
+
+    if "gamma" not in _ORACLE_ITERS:
+        eta = inputs.point_sources(WL["dims"], WL["x_src"])[0]
+        t0 = time.perf_counter()
+        _, its, _ = op.solve(eta, *WL["gamma"], tol=1e-5)
+        _ORACLE_ITERS["gamma"] = 2 * its
+        _ORACLE_ITERS["seconds"] = time.perf_counter() - t0
+    return _ORACLE_ITERS["gamma"]
+
+
+def _cpu_baseline(U, sample_seconds=8.0):
+    """The oracle (plain FP64 C, one thread) on the host cores, for one
+    12-source factorized propagator with correction on the 16^3x32 workload,
+    from a bounded sample: the time of one oracle D application on each solve
+    domain (Gamma, Gammabar, Gamma*, full lattice), measured, times
+    2 applications per BiCGStab iteration x the oracle's iteration count
+    (measured on Gamma, one column, residual 1e-10) x 12 columns."""
     import oracle
     from paper_1612_06424_gb300 import inputs
 
     dims = WL["dims"]
     op = oracle.Operator(dims, U, WL["kappa"], WL["csw"])
+    its = _oracle_iterations(op)
     psi = inputs.gaussian_spinor(dims, 99)[0]
-    t0 = time.perf_counter()
-    n = 0
-    while time.perf_counter() - t0 < sample_seconds or n < 2:
-        op.apply(psi)
-        n += 1
-    t_apply = (time.perf_counter() - t0) / n
     T = dims[0]
-    sites = {"gamma": WL["gamma"][1] - WL["gamma"][0] + 1, "gamma_bar": WL["delta"][1] + 1,
-             "gamma_star": WL["gamma_star"][1] - WL["gamma_star"][0] + 1, "full": T}
-    total = 0.0
-    for k, its in iters_per_group.items():
-        total += 12 * 2 * (2 * its) * t_apply * sites[k] / T
+    groups = {"gamma": WL["gamma"], "gamma_bar": (0, WL["delta"][1]), "gamma_star": WL["gamma_star"], "full": (0, T - 1)}
+    per = sample_seconds / len(groups)
+    t_apply = {}
+    for k, (a, b) in groups.items():
+        t0 = time.perf_counter()
+        n = 0
+        while time.perf_counter() - t0 < per or n < 2:
+            op.apply(psi, a, b)
+            n += 1
+        t_apply[k] = (time.perf_counter() - t0) / n
+    total = sum(12 * 2 * its * t for t in t_apply.values())
     return {"value": total, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} oracle D applications on the full 16^3x32 lattice ({t_apply:.3f} s each), scaled by "
-                      f"2 x (2 x even-odd iteration count) applications per column over the 4 solve groups x 12 columns "
-                      f"(extrapolated)"}
+            "sample": f"oracle D applications on each solve domain ({', '.join(f'{k} {v:.3f} s' for k, v in t_apply.items())}) "
+                      f"x 2 x {its} oracle BiCGStab iterations to 1e-10 (twice those measured for one column on Gamma "
+                      f"to 1e-5, {_ORACLE_ITERS.get('seconds', 0):.0f} s) x 12 columns; extrapolated"}
 
 
 def run_reference(args):
@@ -191,12 +209,9 @@ def run_reference(args):
     from paper_1612_06424_gb300 import inputs
 
     U = inputs.random_su3_field(WL["dims"], WL["eps"], 1)
-    iters = {"gamma": 60, "gamma_bar": 70, "gamma_star": 70, "full": 80}
-    vals = []
     for _ in range(args.warmup):
-        pass
-    for _ in range(args.steps):
-        vals.append(_cpu_baseline(U, iters, sample_seconds=4.0))
+        _cpu_baseline(U, sample_seconds=2.0)
+    vals = [_cpu_baseline(U, sample_seconds=4.0) for _ in range(args.steps)]
     v = statistics.median(x["value"] for x in vals)
     cb = dict(vals[-1])
     cb["value"] = v
@@ -434,17 +449,20 @@ def main():
                 "ms_per_launch": round(d_ms, 5), "alg_bytes_per_launch": d_bytes,
                 "tflops": round(d_flops / (d_ms * 1e-3) / 1e12, 3)}
     dslash_other = {}
+    fp64_peak = lqcd.fma_peak(64)
     for p in (64, 32, 16):
         if p == args.precision:
             continue
         m, b, f = lat.dslash_bench(doms, [0] * 24, p, 20)
         dslash_other[str(p)] = {"GB/s": round(b / (m * 1e-3) / 1e9, 1), "TFLOP/s": round(f / (m * 1e-3) / 1e12, 3),
                                 "ms": round(m, 5)}
+        if p == 64:  # FP64 is bound by the FP64 FMA rate on this GPU, not by HBM
+            dslash_other["64"].update({"bound": "alu", "fp64_fma_peak_tflops_measured": round(fp64_peak, 3),
+                                       "alu_frac": round(f / (m * 1e-3) / 1e12 / fp64_peak, 3)})
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        iters = {k: v["iters"] for k, v in stats.items()}
-        cpu = _cpu_baseline(U, iters)
+        cpu = _cpu_baseline(U)
 
     if rank == 0:
         line = {

@@ -229,6 +229,8 @@ int solve_core(lqcd_lattice* L, BatchStore& B, bool dag, const lqcd_solver_param
   const double tol = prm.tol > 0 ? prm.tol : 1e-10;
   const int max_iter = prm.max_iter > 0 ? prm.max_iter : 100000;
   const int check_every = prm.check_every > 0 ? prm.check_every : 8;
+  // the inner iterations run as a captured CUDA graph unless LQCD_NO_GRAPH is set
+  static const bool use_graph = getenv("LQCD_NO_GRAPH") == nullptr;
   double inner_tol = prm.inner_tol;
   if (!(inner_tol > 0)) inner_tol = P == 64 ? 0.0 : P == 32 ? 1e-5 : 2e-2;
   // iterations of one inner cycle: a reduced-precision BiCGStab that has not
@@ -253,6 +255,8 @@ int solve_core(lqcd_lattice* L, BatchStore& B, bool dag, const lqcd_solver_param
   RC(dcnt.alloc(sizeof(int), st));
   VecP none;
 
+  // stencil variant for this batch shape (autotuned once per shape)
+  b.hop_variant = lq_tune_hop(L, b, P, clov, te, p, v, st);
   // |eta|^2 of each system (both parities)
   std::fill(B.h_active.begin(), B.h_active.end(), 1);
   RC(B.push_active(st));
@@ -342,23 +346,71 @@ int solve_core(lqcd_lattice* L, BatchStore& B, bool dag, const lqcd_solver_param
     for (int k = 0; k < n; k++)
       if (outer[k]) budget = std::max(budget, max_iter - out.iters[k]);
     budget = std::min(budget, cycle_cap);
-    while (it < budget) {
-      RC(lq_hop_clinv(P, dag, clov, L, b, p, none, te, 1.0, 0.0, st));
-      RC(lq_hop_lin(P, dag, clov, lq::RED_DOT_W, L, b, 1, te, p, none, r0, v, -0.25, 1.0, 0.0, st));
-      RC(lq_finalize(lq::FIN_ALPHA, b, 0, 0, 1, st));
-      RC(lq_bicg_s(P, b, r, v, s, st));
-      RC(lq_hop_clinv(P, dag, clov, L, b, s, none, te, 1.0, 0.0, st));
-      RC(lq_hop_lin(P, dag, clov, lq::RED_TS, L, b, 1, te, s, none, none, t, -0.25, 1.0, 0.0, st));
-      RC(lq_finalize(lq::FIN_OMEGA, b, 0, 0, 1, st));
-      RC(lq_bicg_xr(P, b, xs, p, s, t, r, r0, st));
-      RC(lq_finalize(lq::FIN_BETA, b, 0, 0, lq_words_per_site(P), st));
-      RC(lq_bicg_p(P, b, p, r, v, st));
-      it++;
-      if (it % check_every == 0 || it >= budget) {
-        RC(lq_count_active(b, dcnt.as<int>(), st));
-        CK(cudaMemcpyAsync(cnt.h, dcnt.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
+    // one BiCGStab iteration: 10 kernels, all scalars and flags on the device
+    auto iteration = [&](cudaStream_t s_) -> int {
+      RC(lq_hop_clinv(P, dag, clov, L, b, p, none, te, 1.0, 0.0, s_));
+      RC(lq_hop_lin(P, dag, clov, lq::RED_DOT_W, L, b, 1, te, p, none, r0, v, -0.25, 1.0, 0.0, s_));
+      RC(lq_finalize(lq::FIN_ALPHA, b, 0, 0, lq_hop_wps(P, b), s_));
+      RC(lq_bicg_s(P, b, r, v, s, s_));
+      RC(lq_hop_clinv(P, dag, clov, L, b, s, none, te, 1.0, 0.0, s_));
+      RC(lq_hop_lin(P, dag, clov, lq::RED_TS, L, b, 1, te, s, none, none, t, -0.25, 1.0, 0.0, s_));
+      RC(lq_finalize(lq::FIN_OMEGA, b, 0, 0, lq_hop_wps(P, b), s_));
+      RC(lq_bicg_xr(P, b, xs, p, s, t, r, r0, s_));
+      RC(lq_finalize(lq::FIN_BETA, b, 0, 0, lq_words_per_site(P), s_));
+      RC(lq_bicg_p(P, b, p, r, v, s_));
+      return 0;
+    };
+    auto poll = [&](cudaStream_t s_) -> int {  // systems still iterating
+      RC(lq_count_active(b, dcnt.as<int>(), s_));
+      CK(cudaMemcpyAsync(cnt.h, dcnt.p, sizeof(int), cudaMemcpyDeviceToHost, s_));
+      CK(cudaStreamSynchronize(s_));
+      return 0;
+    };
+    if (use_graph && budget >= 2 * check_every) {
+      // check_every iterations captured once as a CUDA graph on a private
+      // stream, replayed between host convergence checks (retired systems
+      // skip every kernel, so iterations past convergence change nothing)
+      cudaStream_t gs = L->graph_stream;
+      CK(cudaEventRecord(L->graph_event, st));
+      CK(cudaStreamWaitEvent(gs, L->graph_event, 0));
+      const long long c0 = lqcd_kernel_launches();
+      cudaGraph_t graph = nullptr;
+      CK(cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal));
+      int crc = 0;
+      for (int g = 0; g < check_every && !crc; g++) crc = iteration(gs);
+      cudaError_t ce = cudaStreamEndCapture(gs, &graph);
+      if (crc) return crc;
+      CK(ce);
+      const long long per_replay = lqcd_kernel_launches() - c0;
+      lq_count_launches(-per_replay);  // captured, not run
+      cudaGraphExec_t exec = nullptr;
+      cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      CK(ie);
+      int grc = 0;
+      while (it < budget) {
+        if (cudaGraphLaunch(exec, gs) != cudaSuccess) {
+          lq_set_error("solve: CUDA graph launch failed");
+          grc = LQCD_ECUDA;
+          break;
+        }
+        lq_count_launches(per_replay);
+        it += check_every;
+        if ((grc = poll(gs)) != 0) break;
         if (*cnt.h == 0) break;
+      }
+      cudaGraphExecDestroy(exec);
+      if (grc) return grc;
+      CK(cudaEventRecord(L->graph_event, gs));
+      CK(cudaStreamWaitEvent(st, L->graph_event, 0));
+    } else {
+      while (it < budget) {
+        RC(iteration(st));
+        it++;
+        if (it % check_every == 0 || it >= budget) {
+          RC(poll(st));
+          if (*cnt.h == 0) break;
+        }
       }
     }
     // x_o += e for the systems of this cycle
@@ -585,6 +637,13 @@ extern "C" int lqcd_create_lattice(const int dims[4], int bc_t, lqcd_lattice** o
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
   }
   cudaGetLastError();
+  if (cudaStreamCreateWithFlags(&L->graph_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&L->graph_event, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    delete L;
+    lq_set_error("create_lattice: cannot create the solver stream");
+    return LQCD_ECUDA;
+  }
   *out = L;
   return 0;
 }
@@ -608,6 +667,8 @@ extern "C" int lqcd_destroy_lattice(lqcd_lattice* L) {
   RC(check_lat(L));
   cudaDeviceSynchronize();
   free_fields(L);
+  if (L->graph_stream) cudaStreamDestroy(L->graph_stream);
+  if (L->graph_event) cudaEventDestroy(L->graph_event);
   delete L;
   return 0;
 }
@@ -1063,6 +1124,7 @@ extern "C" int lqcd_dslash_bench(lqcd_lattice* L, int n_sys, const lqcd_slab* do
   RC(lq_convert(64, precision, b, v64(tmp.v(1)), q.v(1), st));
   const bool clov = L->csw != 0.0;
   VecP none;
+  B.b.hop_variant = lq_tune_hop(L, B.b, precision, clov, q.v(0), q.v(1), q.v(2), st);
   for (int w = 0; w < 3; w++)
     RC(lq_hop_lin(precision, false, clov, lq::RED_NONE, L, b, 1, q.v(0), q.v(1), none, none, q.v(2), -0.25, 1.0, 0.0,
                   st));

@@ -384,4 +384,173 @@ __global__ void __launch_bounds__(128, HopMinBlocks<P>::value) k_hop_clinv(HopAr
   Prec<P>::store(sys_ptr_w<P>(a.out, sd.off), nrm_ptr_w(a.outn, sd.off), sd.n, j, o);
 }
 
+// ---------------------------------------------------------------------------
+#ifndef LQ_HOP2_MINB
+#define LQ_HOP2_MINB 5
+#endif
+// FP32 stencil with two threads per output site.  A block of 128 threads
+// covers 64 sites; warps 0-1 (half 0) sum the hops in directions 0 and 1,
+// warps 2-3 (half 1) those in directions 2 and 3, so the split is uniform per
+// warp (no divergence) and each warp still reads 32 consecutive sites.  The
+// halves swap the half-spinor the other one needs through shared memory; then
+// half h owns chirality block h (spins 2h, 2h+1, i.e. float4 words 3h..3h+2):
+// its y / z / w words, its 6x6 clover block and its output words.
+LQ_DI void load_half32(cx<float> s[6], const void* base, int n, int j, int h) {
+  const float4* p = (const float4*)base + 3 * h * n + j;
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    float4 v = __ldg(p + k * n);
+    s[2 * k] = {v.x, v.y};
+    s[2 * k + 1] = {v.z, v.w};
+  }
+}
+LQ_DI void store_half32(void* base, int n, int j, int h, const cx<float> s[6]) {
+  float4* p = (float4*)base + 3 * h * n + j;
+#pragma unroll
+  for (int k = 0; k < 3; k++) p[k * n] = make_float4(s[2 * k].re, s[2 * k].im, s[2 * k + 1].re, s[2 * k + 1].im);
+}
+
+// Sum of the hops of this thread's two directions, combined with the other
+// half's sum: returns chirality block h of D_hop x (6 complex).
+template <bool DAG>
+LQ_DI void hop_pair32(const HopArgs& a, const SysDesc& sd, const FieldPtrs& f, int cb, bool valid, int h, int tl,
+                      cx<float> mine[6]) {
+  __shared__ float2 xch[2][6][64];
+  cx<float> part[12];
+#pragma unroll
+  for (int k = 0; k < 12; k++) part[k] = {0.f, 0.f};
+  if (valid) {
+    int x[4];
+    eo_coords(a.g, cb, a.pout, x);
+    const void* in = sys_ptr<32>(a.x, sd.off);
+    if (h == 0) {
+      hop_dir<32, DAG, 0>(a.g, sd, f, a.pout, cb, x, in, nullptr, part);
+      hop_dir<32, DAG, 1>(a.g, sd, f, a.pout, cb, x, in, nullptr, part);
+    } else {
+      hop_dir<32, DAG, 2>(a.g, sd, f, a.pout, cb, x, in, nullptr, part);
+      hop_dir<32, DAG, 3>(a.g, sd, f, a.pout, cb, x, in, nullptr, part);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 6; k++) {
+    const cx<float> send = h == 0 ? part[6 + k] : part[k];
+    xch[h][k][tl] = make_float2(send.re, send.im);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 6; k++) {
+    const float2 o = xch[h ^ 1][k][tl];
+    const cx<float> keep = h == 0 ? part[k] : part[6 + k];
+    mine[k] = {keep.re + o.x, keep.im + o.y};
+  }
+}
+
+template <bool DAG, bool CLOV, int RED, int EPI>
+__global__ void __launch_bounds__(128, LQ_HOP2_MINB) k_hop2_lin(HopArgs a) {
+  const int s = blockIdx.x;
+  if (a.active && !a.active[s]) return;
+  const SysDesc sd = a.sys[s];
+  if ((int)(blockIdx.y * 64) >= sd.n) return;
+  const int h = threadIdx.x >> 6, tl = threadIdx.x & 63;
+  const int j = blockIdx.y * 64 + tl;
+  const bool valid = j < sd.n;
+  const FieldPtrs f = a.fields[sd.field];
+  const int cb = sd.cb0 + j;
+  cx<float> res[6];
+  if (EPI & EPI_X) {
+    hop_pair32<DAG>(a, sd, f, cb, valid, h, tl, res);
+    const float al = (float)a.alpha;
+#pragma unroll
+    for (int k = 0; k < 6; k++) res[k] = al * res[k];
+  } else {
+#pragma unroll
+    for (int k = 0; k < 6; k++) res[k] = {0.f, 0.f};
+  }
+  float red[3] = {0.f, 0.f, 0.f};
+  if (valid) {
+    cx<float> yv[6];
+    if ((EPI & EPI_Y) || RED == RED_TS) load_half32(yv, sys_ptr<32>(a.y, sd.off), sd.n, j, h);
+    if (EPI & EPI_Y) {
+      cx<float> ay[6];
+      if (CLOV) {
+        ClovIO<32>::apply(f.A32 + (a.pout * 18 + 9 * h) * a.g.Vh, a.g.Vh, cb, yv, ay);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 6; k++) ay[k] = (float)a.diag * yv[k];
+      }
+      const float be = (float)a.beta;
+#pragma unroll
+      for (int k = 0; k < 6; k++) res[k] = res[k] + be * ay[k];
+    }
+    if (EPI & EPI_Z) {
+      cx<float> zv[6];
+      load_half32(zv, sys_ptr<32>(a.z, sd.off), sd.n, j, h);
+      const float ga = (float)a.gamma;
+#pragma unroll
+      for (int k = 0; k < 6; k++) res[k] = res[k] + ga * zv[k];
+    }
+    store_half32(sys_ptr_w<32>(a.out, sd.off), sd.n, j, h, res);
+    if (RED == RED_DOT_W) {
+      cx<float> wv[6];
+      load_half32(wv, sys_ptr<32>(a.w, sd.off), sd.n, j, h);
+#pragma unroll
+      for (int k = 0; k < 6; k++) {
+        red[0] += wv[k].re * res[k].re + wv[k].im * res[k].im;
+        red[1] += wv[k].re * res[k].im - wv[k].im * res[k].re;
+      }
+    } else if (RED == RED_TS) {
+#pragma unroll
+      for (int k = 0; k < 6; k++) {
+        red[0] += res[k].re * yv[k].re + res[k].im * yv[k].im;
+        red[1] += res[k].re * yv[k].im - res[k].im * yv[k].re;
+        red[2] += res[k].re * res[k].re + res[k].im * res[k].im;
+      }
+    } else if (RED == RED_NORM) {
+#pragma unroll
+      for (int k = 0; k < 6; k++) red[2] += res[k].re * res[k].re + res[k].im * res[k].im;
+    }
+  }
+  if (RED != RED_NONE) block_reduce_store<3, float>(red, a.partial + ((long long)s * a.pstride + blockIdx.y) * 4);
+}
+
+template <bool DAG, bool CLOV, int EPI>
+__global__ void __launch_bounds__(128, LQ_HOP2_MINB) k_hop2_clinv(HopArgs a) {
+  const int s = blockIdx.x;
+  if (a.active && !a.active[s]) return;
+  const SysDesc sd = a.sys[s];
+  if ((int)(blockIdx.y * 64) >= sd.n) return;
+  const int h = threadIdx.x >> 6, tl = threadIdx.x & 63;
+  const int j = blockIdx.y * 64 + tl;
+  const bool valid = j < sd.n;
+  const FieldPtrs f = a.fields[sd.field];
+  const int cb = sd.cb0 + j;
+  cx<float> res[6];
+  if (EPI & EPI_X) {
+    hop_pair32<DAG>(a, sd, f, cb, valid, h, tl, res);
+    const float al = (float)a.alpha;
+#pragma unroll
+    for (int k = 0; k < 6; k++) res[k] = al * res[k];
+  } else {
+#pragma unroll
+    for (int k = 0; k < 6; k++) res[k] = {0.f, 0.f};
+  }
+  if (!valid) return;
+  if (EPI & EPI_Y) {
+    cx<float> yv[6];
+    load_half32(yv, sys_ptr<32>(a.y, sd.off), sd.n, j, h);
+    const float be = (float)a.beta;
+#pragma unroll
+    for (int k = 0; k < 6; k++) res[k] = res[k] + be * yv[k];
+  }
+  cx<float> o[6];
+  if (CLOV) {
+    ClovIO<32>::apply(f.Ai32 + 9 * h * a.g.Vh, a.g.Vh, cb, res, o);
+  } else {
+    const float inv = (float)(1.0 / a.diag);
+#pragma unroll
+    for (int k = 0; k < 6; k++) o[k] = inv * res[k];
+  }
+  store_half32(sys_ptr_w<32>(a.out, sd.off), sd.n, j, h, o);
+}
+
 }  // namespace lq

@@ -11,6 +11,8 @@
 #include "common.cuh"
 
 void lq_count_launch();
+void lq_count_launches(long long n);
+extern "C" long long lqcd_kernel_launches(void);
 void lq_set_error(const std::string& msg);
 
 // A vector of a batch in one precision: pool base (and FP16 norm pool).
@@ -25,6 +27,7 @@ struct Batch {
   int nsys = 0;
   int nby = 0;               // site blocks (one site per thread) of the largest system
   int pstride = 0;           // partial-buffer blocks per system (>= any kernel's grid.y)
+  int hop_variant = 1;       // FP32 stencil: 1 = one thread per site, 2 = two threads per site
   long long max_n = 0;
   long long total = 0;       // sum of n over systems (sites per parity)
   const lq::SysDesc* sys = nullptr;
@@ -55,6 +58,8 @@ struct lqcd_lattice {
   std::vector<FieldData> fields;
   lq::FieldPtrs* d_fields = nullptr;
   int device = 0;
+  cudaStream_t graph_stream = nullptr;  // private stream the solver's CUDA graphs run on
+  cudaEvent_t graph_event = nullptr;
 };
 
 // ---------------------------------------------------------------- launchers
@@ -79,6 +84,12 @@ int lq_norm2_64(const Batch& b, const double2* v, cudaStream_t st);
 int lq_finalize(int mode, const Batch& b, double tau2, double floor_rel2, int wps, cudaStream_t st);
 // 16-byte words per site of the word-parallel vector kernels of precision P (1 for FP16: one site per thread)
 int lq_words_per_site(int P);
+// blocks-per-site factor of the hop kernels' reductions (2: two threads per site)
+int lq_hop_wps(int P, const Batch& b);
+// Autotuner: the fastest FP32 stencil variant for this batch shape, timed on
+// the given vectors (x on even sites, y / out on odd sites) once per shape and
+// cached; returns the variant (1 or 2).
+int lq_tune_hop(const lqcd_lattice* L, const Batch& b, int P, bool clov, VecP x, VecP y, VecP out, cudaStream_t st);
 int lq_count_active(const Batch& b, int* d_count, cudaStream_t st);
 int lq_convert(int Pin, int Pout, const Batch& b, VecP in, VecP out, cudaStream_t st);
 

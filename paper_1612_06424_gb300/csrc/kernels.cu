@@ -2,6 +2,11 @@
 // kernels (natural <-> even-odd), point sources and the boundary hop of
 // the Schur-complement assembly.
 #include <atomic>
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "blas.cuh"
 #include "internal.h"
@@ -10,6 +15,7 @@ using namespace lq;
 
 static std::atomic<long long> g_launches{0};
 void lq_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void lq_count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 extern "C" long long lqcd_kernel_launches(void) { return g_launches.load(); }
 
 static inline dim3 grid_of(const Batch& b) { return dim3((unsigned)b.nsys, (unsigned)b.nby, 1); }
@@ -42,6 +48,46 @@ static HopArgs hop_args(const lqcd_lattice* L, const Batch& b, int pout) {
   return a;
 }
 
+// FP32 stencil variant of a batch: 1 = one thread per site (k_hop_*), 2 = two
+// threads per site (k_hop2_*).  LQCD_HOP_SPLIT=1|2 forces one for every batch.
+static int forced_variant() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("LQCD_HOP_SPLIT");
+    v = (e && (e[0] == '1' || e[0] == '2')) ? e[0] - '0' : 0;
+  }
+  return v;
+}
+
+static int variant_of(int P, const Batch& b) {
+  if (P != 32) return 1;
+  const int f = forced_variant();
+  return f ? f : (b.hop_variant == 2 ? 2 : 1);
+}
+
+int lq_hop_wps(int P, const Batch& b) { return variant_of(P, b) == 2 ? 2 : 1; }
+
+template <bool DAG, bool CLOV>
+static int launch_lin2(int red, int epi, dim3 gr, const HopArgs& a, cudaStream_t st) {
+  constexpr int XY = EPI_X | EPI_Y, XZ = EPI_X | EPI_Z, XYZ = EPI_X | EPI_Y | EPI_Z;
+  if (red == RED_NONE && epi == XY) k_hop2_lin<DAG, CLOV, RED_NONE, XY><<<gr, LQ_BLOCK, 0, st>>>(a);
+  else if (red == RED_NONE && epi == XZ) k_hop2_lin<DAG, CLOV, RED_NONE, XZ><<<gr, LQ_BLOCK, 0, st>>>(a);
+  else if (red == RED_DOT_W && epi == XY) k_hop2_lin<DAG, CLOV, RED_DOT_W, XY><<<gr, LQ_BLOCK, 0, st>>>(a);
+  else if (red == RED_TS && epi == XY) k_hop2_lin<DAG, CLOV, RED_TS, XY><<<gr, LQ_BLOCK, 0, st>>>(a);
+  else if (red == RED_NORM && epi == XYZ) k_hop2_lin<DAG, CLOV, RED_NORM, XYZ><<<gr, LQ_BLOCK, 0, st>>>(a);
+  else return -1;
+  return 0;
+}
+
+template <bool DAG, bool CLOV>
+static int launch_clinv2(int epi, dim3 gr, const HopArgs& a, cudaStream_t st) {
+  if (epi == EPI_X) k_hop2_clinv<DAG, CLOV, EPI_X><<<gr, LQ_BLOCK, 0, st>>>(a);
+  else if (epi == EPI_Y) k_hop2_clinv<DAG, CLOV, EPI_Y><<<gr, LQ_BLOCK, 0, st>>>(a);
+  else if (epi == (EPI_X | EPI_Y)) k_hop2_clinv<DAG, CLOV, EPI_X | EPI_Y><<<gr, LQ_BLOCK, 0, st>>>(a);
+  else return -1;
+  return 0;
+}
+
 // (reduction, epilogue) pairs the solver uses
 template <int P, bool DAG, bool CLOV>
 static int launch_lin(int red, int epi, dim3 gr, const HopArgs& a, cudaStream_t st) {
@@ -72,6 +118,16 @@ int lq_hop_lin(int P, bool dag, bool clov, int red, const lqcd_lattice* L, const
   a.alpha = alpha; a.beta = beta; a.gamma = gamma;
   const int epi = (alpha != 0.0 ? EPI_X : 0) | (beta != 0.0 ? EPI_Y : 0) | (gamma != 0.0 ? EPI_Z : 0);
   dim3 gr = grid_of(b);
+  if (variant_of(P, b) == 2) {
+    const dim3 g2((unsigned)b.nsys, (unsigned)((b.max_n + 63) / 64), 1);
+    int rc = dag ? (clov ? launch_lin2<true, true>(red, epi, g2, a, st) : launch_lin2<true, false>(red, epi, g2, a, st))
+                 : (clov ? launch_lin2<false, true>(red, epi, g2, a, st) : launch_lin2<false, false>(red, epi, g2, a, st));
+    if (rc) {
+      lq_set_error("hop kernel: unsupported (reduction, epilogue) pair");
+      return LQCD_EBADARG;
+    }
+    return launched();
+  }
   int rc = P == 64 ? launch_lin_p<64>(dag, clov, red, epi, gr, a, st)
          : P == 32 ? launch_lin_p<32>(dag, clov, red, epi, gr, a, st)
                    : launch_lin_p<16>(dag, clov, red, epi, gr, a, st);
@@ -106,6 +162,16 @@ int lq_hop_clinv(int P, bool dag, bool clov, const lqcd_lattice* L, const Batch&
   a.alpha = alpha; a.beta = beta;
   const int epi = (alpha != 0.0 ? EPI_X : 0) | (beta != 0.0 ? EPI_Y : 0);
   dim3 gr = grid_of(b);
+  if (variant_of(P, b) == 2) {
+    const dim3 g2((unsigned)b.nsys, (unsigned)((b.max_n + 63) / 64), 1);
+    int rc = dag ? (clov ? launch_clinv2<true, true>(epi, g2, a, st) : launch_clinv2<true, false>(epi, g2, a, st))
+                 : (clov ? launch_clinv2<false, true>(epi, g2, a, st) : launch_clinv2<false, false>(epi, g2, a, st));
+    if (rc) {
+      lq_set_error("clover-inverse hop kernel: unsupported epilogue");
+      return LQCD_EBADARG;
+    }
+    return launched();
+  }
   int rc = P == 64 ? launch_clinv_p<64>(dag, clov, epi, gr, a, st)
          : P == 32 ? launch_clinv_p<32>(dag, clov, epi, gr, a, st)
                    : launch_clinv_p<16>(dag, clov, epi, gr, a, st);
@@ -410,4 +476,76 @@ int lq_fill64(double2* p, long long n, unsigned seed, cudaStream_t st) {
   if (blocks > 152 * 16) blocks = 152 * 16;
   k_fill64<<<(unsigned)blocks, 256, 0, st>>>(p, n, seed);
   return launched();
+}
+
+// --------------------------------------------------------------- autotuner
+// Decisions per batch shape (precision, systems, sites per parity of the
+// largest system), kept for the process and, if LQCD_TUNE_CACHE names a file,
+// read from and appended to it ("P nsys max_n variant" per line).
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, long long>, int> g_tune;
+bool g_tune_loaded = false;
+
+void tune_load() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = getenv("LQCD_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = fopen(path, "r");
+  if (!f) return;
+  int P, n, v;
+  long long m;
+  while (fscanf(f, "%d %d %lld %d", &P, &n, &m, &v) == 4) g_tune[std::make_tuple(P, n, m)] = v;
+  fclose(f);
+}
+
+void tune_store(int P, int n, long long m, int v) {
+  const char* path = getenv("LQCD_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "%d %d %lld %d\n", P, n, m, v);
+  fclose(f);
+}
+}  // namespace
+
+int lq_tune_hop(const lqcd_lattice* L, const Batch& b, int P, bool clov, VecP x, VecP y, VecP out, cudaStream_t st) {
+  if (P != 32) return 1;
+  if (forced_variant()) return forced_variant();
+  const auto key = std::make_tuple(P, b.nsys, b.max_n);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load();
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) return it->second;
+  }
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return 1;
+  VecP none;
+  float best = 1e30f;
+  int pick = 1;
+  for (int v = 1; v <= 2; v++) {
+    Batch t = b;
+    t.hop_variant = v;
+    t.active = nullptr;  // time every system
+    lq_hop_lin(P, false, clov, RED_NONE, L, t, 1, x, y, none, none, out, -0.25, 1.0, 0.0, st);  // warm-up
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 3; r++) lq_hop_lin(P, false, clov, RED_NONE, L, t, 1, x, y, none, none, out, -0.25, 1.0, 0.0, st);
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      pick = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGetLastError();
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = pick;
+  tune_store(P, b.nsys, b.max_n, pick);
+  return pick;
 }
