@@ -19,6 +19,7 @@ Gamma*, and corr = D^{-1} - fact.
   python bench.py --impl reference     # the CPU oracle on the host cores
   python bench.py --workload batched_32x64   # 8 slabs x 12 sources x 16 inner-level fields
   python bench.py --workload force_24x48     # domain pseudofermion link force, 4 domains
+  python bench.py --workload factorized_48x96  # 8 inner-level fields x 12 sources, 48^3x96
 
 Multi-GPU (torchrun): every rank computes its own propagators (its own
 gauge field, independent problems); there is no collective on the data path.
@@ -65,7 +66,8 @@ def _args():
     ap.add_argument("--no-fp64-form", action="store_true", help="skip timing the plain FP64 form")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="factorized_16x32",
-                    choices=["factorized_16x32", "batched_32x64", "force_24x48"])
+                    choices=["factorized_16x32", "batched_32x64", "force_24x48", "factorized_48x96"])
+    ap.add_argument("--fields", type=int, default=8, help="inner-level fields of factorized_48x96")
     return ap.parse_args()
 
 
@@ -224,6 +226,23 @@ def run_reference(args):
         "gpu_launches": 0}))
 
 
+def _max_over_ranks(value, dist, device="cuda"):
+    """The largest of the ranks' values (the job's time); the only collective of
+    the multi-GPU path besides the barriers around the timed region."""
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def _rank_seed(rank):
+    """Gauge-field seed of a rank: every rank solves its own, independent problem."""
+    return 1 + rank
+
+
 def run_batched(args):
     """32^3x64, kappa 0.1340, c_sw 1.0: 8 time-slab domains of 8 slices x 12 point
     sources (slab centre, spatial origin) x 16 inner-level fields (every slab's own
@@ -331,6 +350,56 @@ def run_force(args):
     lat.close()
 
 
+def run_factorized_48(args):
+    """48^3x96, kappa 0.1350, c_sw 1.0: Gamma = t 0..43, frozen DeltaGamma = 44..51,
+    Gamma* = 44..95; 12 point sources at (2,0,0,0) on each of `--fields` inner-level
+    fields (the level-0 field with the links of Gamma and of t 52..95 redrawn; links
+    starting or ending in the frozen slab kept), factorized propagator plus the
+    full-lattice correction per field.  The fields run one after another (each
+    packed field is 23 GB; fact + corr are 49 GB)."""
+    import torch
+
+    from paper_1612_06424_gb300 import build, inputs, lqcd
+
+    build.build()
+    dims = (96, 48, 48, 48)
+    G, DL, GS = (0, 43), (44, 51), (44, 95)
+    lat = lqcd.Lattice(dims, "open")
+    V = lat.V
+    fact = torch.empty((12, V, 4, 3), dtype=torch.complex128, device="cuda")
+    corr = torch.empty_like(fact)
+    params = lqcd.SolverParams(tol=1e-10, precision=args.precision)
+    t_fields, t_solve, stats = 0.0, 0.0, []
+    U0 = inputs.random_su3_field_device(dims, 0.4, 7, device="cuda")
+    with Clocks() as clk:
+        for j in range(args.fields):
+            t0 = time.time()
+            Uj = inputs.inner_level_fields_device(U0, dims, [G, (52, 95)], args.fields, 0.4, 8, frozen=DL,
+                                                  field_ids=[j])
+            lat.set_gauge(Uj, 0.135, 1.0)
+            del Uj
+            torch.cuda.synchronize()
+            t1 = time.time()
+            _, _, st = lat.factorized_propagator(G, GS, (2, 0, 0, 0), delta=DL, corr=True, params=params,
+                                                 out=(fact, corr))
+            torch.cuda.synchronize()
+            t_fields += t1 - t0
+            t_solve += time.time() - t1
+            stats.append(st)
+    print(json.dumps({
+        "metric": "s per 12-source factorized propagator + correction @ res 1e-10 (48^3x96)",
+        "value": t_solve / args.fields, "unit": "s/propagator", "n_gpus": 1, "steps": args.fields, "warmup": 0,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": {64: "f64", 32: "f32+f64", 16: "f16+f32+f64"}[args.precision], "data": "synthetic",
+        "config": {"workload": "48^3x96 factorized propagator, inner-level fields", "dims": list(dims), "kappa": 0.135,
+                   "c_sw": 1.0, "gamma": list(G), "delta": list(DL), "gamma_star": list(GS), "fields": args.fields},
+        "field_setup_s_per_field": t_fields / args.fields,
+        "iters": [{k: v["iters"] for k, v in st.items()} for st in stats],
+        "true_residual_max": max(v["true_residual"] for st in stats for v in st.values()),
+        "clocks": clk.summary()}))
+    lat.close()
+
+
 def main():
     args = _args()
     if args.impl == "reference":
@@ -339,6 +408,8 @@ def main():
         return run_batched(args)
     if args.workload == "force_24x48":
         return run_force(args)
+    if args.workload == "factorized_48x96":
+        return run_factorized_48(args)
     import numpy as np
     import torch
 
@@ -360,7 +431,7 @@ def main():
 
     build.build()
     dims = WL["dims"]
-    U = inputs.random_su3_field(dims, WL["eps"], 1 + rank)
+    U = inputs.random_su3_field(dims, WL["eps"], _rank_seed(rank))
     U_dev = torch.from_numpy(U).cuda()
     lat = lqcd.Lattice(dims, "open")
     V = lat.V
@@ -388,12 +459,8 @@ def main():
         e1.record()
         torch.cuda.synchronize()
         barrier()
-        ms = e0.elapsed_time(e1)
+        ms = _max_over_ranks(e0.elapsed_time(e1), dist)
         launches = lqcd.kernel_launches() - l0
-        if dist is not None:
-            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = t.item()
         return ms, launches, stats
 
     # headline: the requested precision
@@ -427,11 +494,7 @@ def main():
     e1.record()
     torch.cuda.synchronize()
     barrier()
-    e2e_ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = t.item()
+    e2e_ms = _max_over_ranks(e0.elapsed_time(e1), dist)
     e2e = {"value": e2e_ms / 1e3 / (Ke * world), "unit": UNIT, "h2d_bytes_per_step": int(U.nbytes),
            "d2h_bytes_per_step": int(fact.numel() * 16 * 2)}
 

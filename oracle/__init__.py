@@ -64,6 +64,7 @@ def lib():
         _lib.ora_solve.argtypes = [ip, c, dp, dp, c, c, c, dp, dp, d, c, ip, dp]
         _lib.ora_solve.restype = c
         _lib.ora_force.argtypes = [ip, c, dp, d, c, c, dp, dp, dp]
+        _lib.ora_dirac_sites.argtypes = [ip, c, dp, d, d, c, c, ctypes.POINTER(ctypes.c_long), c, dp, dp]
     return _lib
 
 
@@ -74,6 +75,18 @@ def _dp(a: np.ndarray):
 
 def _dims(dims):
     return (ctypes.c_int * 4)(*[int(v) for v in dims])
+
+
+def dirac_at_sites(dims, U, kappa: float, csw: float, bc: int, slab, sites, psi) -> np.ndarray:
+    """(D_L psi)(x) at the natural site indices `sites` only, shape (len(sites), 4, 3).
+    Builds no full-lattice clover array, so it serves very large lattices."""
+    Uc = np.ascontiguousarray(U, dtype=np.complex128)
+    ps = np.ascontiguousarray(psi, dtype=np.complex128)
+    st = np.ascontiguousarray(np.asarray(sites, dtype=np.int64))
+    out = np.zeros((st.size, 4, 3), dtype=np.complex128)
+    lib().ora_dirac_sites(_dims(dims), int(bc), _dp(Uc), float(kappa), float(csw), int(slab[0]), int(slab[1]),
+                          st.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), int(st.size), _dp(ps), _dp(out))
+    return out
 
 
 def gamma(mu: int) -> np.ndarray:

@@ -265,29 +265,34 @@ static su3 fhat(const geo *g, const cplx *U, long z, int mu, int nu) {
 /* A[V][12][12]: the site-diagonal part of D,
  *   A(x) = 1/(2 kappa) + c_sw (i/4) sum_{mu != nu} sigma_mu_nu Fhat_mu_nu(x),
  * with row/column index 3*s + c. */
+/* The 12x12 site-diagonal block of D at site z. */
+static void clover_site(const geo *g, const cplx *U, long z, double kappa, double csw, cplx *M) {
+  static cplx sg[4][4][4][4];
+  static int sg_ready = 0;
+  if (!sg_ready) {
+    for (int mu = 0; mu < 4; mu++)
+      for (int nu = 0; nu < 4; nu++) sigma(mu, nu, sg[mu][nu]);
+    sg_ready = 1;
+  }
+  memset(M, 0, 144 * sizeof(cplx));
+  for (int r = 0; r < 12; r++) M[r * 12 + r] = 1.0 / (2.0 * kappa);
+  if (csw == 0.0) return;
+  for (int mu = 0; mu < 4; mu++)
+    for (int nu = 0; nu < 4; nu++) {
+      if (mu == nu) continue;
+      su3 F = fhat(g, U, z, mu, nu);
+      for (int s = 0; s < 4; s++)
+        for (int t = 0; t < 4; t++)
+          for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++) M[(3 * s + a) * 12 + 3 * t + b] += csw * 0.25 * I * sg[mu][nu][s][t] * F.m[a][b];
+    }
+}
+
 void ora_clover(const int dims[4], int bc, const double *Ud, double kappa, double csw, double *Ad) {
   geo g = make_geo(dims, bc);
   const cplx *U = (const cplx *)Ud;
   cplx *A = (cplx *)Ad;
-  cplx sg[4][4][4][4];
-  for (int mu = 0; mu < 4; mu++)
-    for (int nu = 0; nu < 4; nu++) sigma(mu, nu, sg[mu][nu]);
-  for (long z = 0; z < g.V; z++) {
-    cplx *M = A + z * 144;
-    memset(M, 0, 144 * sizeof(cplx));
-    for (int r = 0; r < 12; r++) M[r * 12 + r] = 1.0 / (2.0 * kappa);
-    if (csw == 0.0) continue;
-    for (int mu = 0; mu < 4; mu++)
-      for (int nu = 0; nu < 4; nu++) {
-        if (mu == nu) continue;
-        su3 F = fhat(&g, U, z, mu, nu);
-        for (int s = 0; s < 4; s++)
-          for (int t = 0; t < 4; t++)
-            for (int a = 0; a < 3; a++)
-              for (int b = 0; b < 3; b++)
-                M[(3 * s + a) * 12 + 3 * t + b] += csw * 0.25 * I * sg[mu][nu][s][t] * F.m[a][b];
-      }
-  }
+  for (long z = 0; z < g.V; z++) clover_site(&g, U, z, kappa, csw, A + z * 144);
 }
 
 /* ------------------------------------------------------- Dirac operator */
@@ -635,6 +640,42 @@ void ora_force(const int dims[4], int bc, const double *Ud, double csw, int t0, 
               force_add(F, fk.site, fk.dir, a, -2.0 * creal(csw * 0.25 * I * tr));
             }
           }
+      }
+  }
+}
+
+/* (D_L in)(x) at the listed sites x only (natural indices, inside the slab
+ * t0..t1): out[k][12] for sites[k].  Same terms as ora_dirac (dagger = 0),
+ * with the site-diagonal block built from the links at each listed site, so
+ * no full-lattice clover array is needed on very large lattices. */
+void ora_dirac_sites(const int dims[4], int bc, const double *Ud, double kappa, double csw, int t0, int t1,
+                     const long *sites, int nsites, const double *ind, double *outd) {
+  geo g = make_geo(dims, bc);
+  const cplx *U = (const cplx *)Ud, *in = (const cplx *)ind;
+  cplx *out = (cplx *)outd;
+  cplx B[12][12], M[144];
+  for (int k = 0; k < nsites; k++) {
+    const long x = sites[k];
+    cplx *o = out + (long)k * 12;
+    memset(o, 0, 12 * sizeof(cplx));
+    if (!in_slab(&g, x, t0, t1)) continue;
+    int xc[4];
+    coords(&g, x, xc);
+    clover_site(&g, U, x, kappa, csw, M);
+    for (int r = 0; r < 12; r++)
+      for (int c = 0; c < 12; c++) B[r][c] = M[r * 12 + c];
+    blk_apply(B, in + x * 12, o, 0);
+    for (int mu = 0; mu < 4; mu++)
+      for (int fwd = 1; fwd >= 0; fwd--) {
+        int crossed;
+        long y = neighbour(&g, xc, mu, fwd ? 1 : -1, &crossed);
+        int yc[4];
+        coords(&g, y, yc);
+        double f = hop_factor(&g, mu, crossed, yc[0], t0, t1);
+        if (f == 0.0) continue;
+        su3 W = fwd ? link_of(U, x, mu) : dag(link_of(U, y, mu));
+        hop_block(&W, mu, fwd, f, B);
+        blk_apply(B, in + y * 12, o, 0);
       }
   }
 }

@@ -264,6 +264,35 @@ struct Prec<16> {
   }
 };
 
+// ------------------------------------------------------- read-once loads
+// Links and clover blocks are read once per stencil launch: loading them
+// without L1 allocation keeps L1 for the input spinors, each of which is read
+// by 8 neighbouring sites (L2 still serves the links to the other systems of
+// the batch that share the gauge field).  LQ_LINK_NA=0 restores plain loads.
+#ifndef LQ_LINK_NA
+#define LQ_LINK_NA 1
+#endif
+LQ_DI float4 ld_once(const float4* p) {
+#if LQ_LINK_NA
+  float4 v;
+  asm("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+      : "l"(p));
+  return v;
+#else
+  return __ldg(p);
+#endif
+}
+LQ_DI uint2 ld_once(const uint2* p) {
+#if LQ_LINK_NA
+  uint2 v;
+  asm("ld.global.nc.L1::no_allocate.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+  return v;
+#else
+  return __ldg(p);
+#endif
+}
+
 // ------------------------------------------------------------------- links
 template <typename R>
 struct su3 {
@@ -299,7 +328,7 @@ struct LinkIO<32> {
   LQ_DI static su3<float> load(const FieldPtrs& f, int p, int mu, int Vh, int cb) {
     const float4* b = f.U32 + (p * 4 + mu) * 3 * Vh + cb;
     su3<float> u;
-    float4 a = __ldg(b), c = __ldg(b + Vh), d = __ldg(b + 2 * Vh);
+    float4 a = ld_once(b), c = ld_once(b + Vh), d = ld_once(b + 2 * Vh);
     u.m[0][0] = {a.x, a.y};
     u.m[0][1] = {a.z, a.w};
     u.m[0][2] = {c.x, c.y};
@@ -318,7 +347,7 @@ struct LinkIO<16> {
     su3<float> u;
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-      uint2 v = __ldg(b + k * Vh);
+      uint2 v = ld_once(b + k * Vh);
       float2 x = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
       float2 y = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
       u.m[(2 * k) / 3][(2 * k) % 3] = {x.x, x.y};
@@ -338,7 +367,7 @@ struct ClovIO {
     float a[36];
 #pragma unroll
     for (int k = 0; k < 9; k++) {
-      float4 v = __ldg(base + k * Vh + cb);
+      float4 v = ld_once(base + k * Vh + cb);
       a[4 * k] = v.x;
       a[4 * k + 1] = v.y;
       a[4 * k + 2] = v.z;

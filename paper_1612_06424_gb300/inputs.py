@@ -129,16 +129,18 @@ def random_su3_field_device(dims, eps: float, seed: int, device="cuda", stream: 
 
 
 def inner_level_fields_device(U0, dims, slabs, n_fields: int, eps: float, seed: int, frozen=None,
-                              chunk: int = 1 << 22):
+                              chunk: int = 1 << 22, field_ids=None):
     """inner_level_fields with the redrawn links exponentiated by torch on U0's device.
-    U0: complex128 tensor [V, 4, 3, 3]; returns [n_fields, V, 4, 3, 3] on the same device."""
+    U0: complex128 tensor [V, 4, 3, 3]; returns [n, V, 4, 3, 3] on the same device for the
+    fields field_ids (default: all n_fields)."""
     import torch
 
     T = dims[0]
     s3 = int(dims[1] * dims[2] * dims[3])
     V = T * s3
     t_of_site = np.arange(V) // s3
-    out = U0.unsqueeze(0).repeat(n_fields, 1, 1, 1, 1)
+    ids = list(range(n_fields)) if field_ids is None else list(field_ids)
+    out = U0.unsqueeze(0).repeat(len(ids), 1, 1, 1, 1)
     for d, (t0, t1) in enumerate(slabs):
         in_slab = (t_of_site >= t0) & (t_of_site <= t1)
         own = np.repeat(in_slab[:, None], 4, axis=1)
@@ -152,8 +154,8 @@ def inner_level_fields_device(U0, dims, slabs, n_fields: int, eps: float, seed: 
             own[:, 0] &= ~end_frozen_t
         idx = np.nonzero(own.reshape(-1))[0]
         idx_t = torch.from_numpy(idx).to(U0.device)
-        for j in range(n_fields):
-            flat = out[j].reshape(-1, 3, 3)
+        for q, j in enumerate(ids):
+            flat = out[q].reshape(-1, 3, 3)
             rng = _rng(seed, (d + 1) * 4096 + j)
             for lo in range(0, idx.size, chunk):
                 hi = min(idx.size, lo + chunk)

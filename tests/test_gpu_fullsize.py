@@ -169,3 +169,45 @@ def test_link_force_24x48_finite_differences():
         assert err <= 1e-6 * abs(fd) + 1e-9 * np.abs(F).max(), (site, mu, a, F[site, mu, a], fd)
         worst = max(worst, err)
     lat.close()
+
+
+def test_factorized_48x96_sampled_sites():
+    """48^3x96, kappa 0.135, c_sw 1: Gamma 0..43, frozen 44..51, Gamma* 44..95, one
+    inner-level field, FP32 inner + FP64 correction.  Sampled sites (all time
+    slices near the cuts, and random ones) of the residuals
+      eta - D (fact + corr),  eta - D_Gamma fact|_Gamma
+    are evaluated by the oracle one site at a time (no oracle clover array over
+    10.6 M sites); each must stay below the solver tolerance times |eta|."""
+    from paper_1612_06424_gb300 import build, lqcd
+
+    build.build()
+    dims = (96, 48, 48, 48)
+    G, DL, GS = (0, 43), (44, 51), (44, 95)
+    U0 = inputs.random_su3_field_device(dims, 0.4, 7, device="cuda")
+    Uj = inputs.inner_level_fields_device(U0, dims, [G, (52, 95)], 8, 0.4, 8, frozen=DL, field_ids=[3])
+    del U0
+    lat = lqcd.Lattice(dims, "open")
+    lat.set_gauge(Uj, 0.135, 1.0)
+    fact, corr, st = lat.factorized_propagator(G, GS, (2, 0, 0, 0), delta=DL, corr=True,
+                                               params=lqcd.SolverParams(tol=1e-10, precision=32))
+    for k in ("gamma", "gamma_bar", "gamma_star", "full"):
+        assert st[k]["status"] == 0 and st[k]["true_residual"] <= 1e-10, (k, st[k])
+    U = Uj[0].cpu().numpy()
+    del Uj
+    s3 = 48 ** 3
+    rng = np.random.default_rng(11)
+    ts = [0, 1, 2, 3, 42, 43, 44, 45, 50, 51, 52, 94, 95] + list(rng.integers(0, 96, 8))
+    sites = np.array([t * s3 + int(rng.integers(s3)) for t in ts] + [2 * s3])  # + the source site
+    for c in (0, 11):
+        full = (fact[c] + corr[c]).cpu().numpy()
+        eta = np.zeros_like(full)
+        s0, c0 = divmod(c, 3)
+        eta[2 * s3, s0, c0] = 1.0
+        r = eta[sites] - oracle.dirac_at_sites(dims, U, 0.135, 1.0, oracle.BC_OPEN, (0, 95), sites, full)
+        assert np.abs(r).max() <= 1e-10
+        fg = fact[c].cpu().numpy()
+        fg[(G[1] + 1) * s3:] = 0  # fact restricted to Gamma
+        in_g = sites[sites < (G[1] + 1) * s3]
+        r = eta[in_g] - oracle.dirac_at_sites(dims, U, 0.135, 1.0, oracle.BC_OPEN, G, in_g, fg)
+        assert np.abs(r).max() <= 1e-10
+    lat.close()

@@ -144,3 +144,17 @@ def test_neumann_series_small_kappa():
     series = 2 * kappa * acc
     sol, _, _ = op.solve(b, tol=1e-14)
     assert np.abs(sol - series).max() < 1e-13 * np.abs(sol).max()
+
+
+@pytest.mark.parametrize("csw,slab,bc", [(1.0, (0, 7), oracle.BC_OPEN), (1.0, (2, 5), oracle.BC_OPEN),
+                                         (0.0, (0, 7), oracle.BC_ANTIPERIODIC)])
+def test_dirac_at_sites_matches_full_operator(csw, slab, bc):
+    dims = (8, 4, 4, 6)
+    U = inputs.random_su3_field(dims, 0.4, 91)
+    op = oracle.Operator(dims, U, 0.13, csw, bc)
+    psi = op.masked(inputs.gaussian_spinor(dims, 92)[0], *slab)
+    full = op.apply(psi, *slab)
+    rng = np.random.default_rng(93)
+    sites = rng.choice(op.V, 40, replace=False)
+    got = oracle.dirac_at_sites(dims, U, 0.13, csw, bc, slab, sites, psi)
+    assert np.abs(got - full[sites]).max() < 1e-14 * np.abs(full).max()
