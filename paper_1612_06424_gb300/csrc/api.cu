@@ -127,8 +127,8 @@ struct BatchStore {
     b.total = off;
     b.nby = (int)((maxn + LQ_BLOCK - 1) / LQ_BLOCK);
     b.pstride = (int)((12 * maxn + LQ_BLOCK - 1) / LQ_BLOCK);
-    if (b.pstride > 65535) {
-      lq_set_error("slab too large for one batch");
+    if ((long long)n * b.pstride >= (1LL << 31)) {
+      lq_set_error("batch too large for one grid (systems x blocks per system >= 2^31)");
       return LQCD_EBADARG;
     }
     RC(sys.alloc(sizeof(lq::SysDesc) * n, st));

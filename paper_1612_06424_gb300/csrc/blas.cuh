@@ -27,6 +27,7 @@ struct VecArgs {
   SolverScal* sc;
   double* partial;
   int pstride;
+  int nsys;
 };
 
 template <typename R>
@@ -71,20 +72,22 @@ LQ_DI typename Word<P>::T* wptr_w(void* pool, long long off) {
 }
 
 #define LQ_WORD_PROLOGUE(P)                                   \
-  const int s = blockIdx.x;                                   \
+  int s, by;                                                  \
+  grid_pos(va.nsys, s, by);                                   \
   if (va.active && !va.active[s]) return;                     \
   const SysDesc sd = va.sys[s];                               \
   const int nw = sd.n * Prec<P>::NV;                          \
-  if ((int)(blockIdx.y * blockDim.x) >= nw) return;           \
-  const int i = blockIdx.y * blockDim.x + threadIdx.x;        \
+  if (by * (int)blockDim.x >= nw) return;                     \
+  const int i = by * blockDim.x + threadIdx.x;                \
   const bool valid = i < nw;
 
 #define LQ_SITE_PROLOGUE                                      \
-  const int s = blockIdx.x;                                   \
+  int s, by;                                                  \
+  grid_pos(va.nsys, s, by);                                   \
   if (va.active && !va.active[s]) return;                     \
   const SysDesc sd = va.sys[s];                               \
-  if ((int)(blockIdx.y * blockDim.x) >= sd.n) return;         \
-  const int j = blockIdx.y * blockDim.x + threadIdx.x;        \
+  if (by * (int)blockDim.x >= sd.n) return;                   \
+  const int j = by * blockDim.x + threadIdx.x;                \
   const bool valid = j < sd.n;
 
 // ------------------------------------------------------------ s = r - alpha v
@@ -146,7 +149,7 @@ __global__ void __launch_bounds__(128) k_bicg_xr_w(VecArgs va, void* x, const vo
       red[2] += sv_[k].re * sv_[k].re + sv_[k].im * sv_[k].im;
     }
   }
-  block_reduce_store<3, R>(red, va.partial + ((long long)s * va.pstride + blockIdx.y) * 4);
+  block_reduce_store<3, R>(red, va.partial + ((long long)s * va.pstride + by) * 4);
 }
 
 __global__ void __launch_bounds__(128) k_bicg_xr_h(VecArgs va, void* x, float* xn, const void* p, const float* pn,
@@ -177,7 +180,7 @@ __global__ void __launch_bounds__(128) k_bicg_xr_h(VecArgs va, void* x, float* x
       red[2] += sv_[k].re * sv_[k].re + sv_[k].im * sv_[k].im;
     }
   }
-  block_reduce_store<3, float>(red, va.partial + ((long long)s * va.pstride + blockIdx.y) * 4);
+  block_reduce_store<3, float>(red, va.partial + ((long long)s * va.pstride + by) * 4);
 }
 
 // ------------------------------------------------- p = r + beta (p - omega v)
@@ -243,7 +246,7 @@ __global__ void __launch_bounds__(128) k_inner_init_w(VecArgs va, const double2*
     W::put(wptr_w<P>(p, sd.off), i, b);
     W::put(wptr_w<P>(x, sd.off), i, z);
   }
-  block_reduce_store<3, R>(red, va.partial + ((long long)s * va.pstride + blockIdx.y) * 4);
+  block_reduce_store<3, R>(red, va.partial + ((long long)s * va.pstride + by) * 4);
 }
 
 __global__ void __launch_bounds__(128) k_inner_init_h(VecArgs va, const double2* r64, void* r, float* rn, void* r0,
@@ -267,7 +270,7 @@ __global__ void __launch_bounds__(128) k_inner_init_h(VecArgs va, const double2*
 #pragma unroll
     for (int k = 0; k < 12; k++) red[2] += b[k].re * b[k].re + b[k].im * b[k].im;
   }
-  block_reduce_store<3, float>(red, va.partial + ((long long)s * va.pstride + blockIdx.y) * 4);
+  block_reduce_store<3, float>(red, va.partial + ((long long)s * va.pstride + by) * 4);
 }
 
 // x64 += x (inner solution of precision P).  A cycle that ended in NaN or
@@ -310,7 +313,7 @@ __global__ void __launch_bounds__(128) k_norm2_64(VecArgs va, const double2* v) 
     double2 a = __ldg(v + sd.off * 12 + i);
     red[2] = a.x * a.x + a.y * a.y;
   }
-  block_reduce_store<3, double>(red, va.partial + ((long long)s * va.pstride + blockIdx.y) * 4);
+  block_reduce_store<3, double>(red, va.partial + ((long long)s * va.pstride + by) * 4);
 }
 
 // Precision conversion of a system vector set, one site per thread.

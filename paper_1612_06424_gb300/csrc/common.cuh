@@ -264,33 +264,17 @@ struct Prec<16> {
   }
 };
 
-// ------------------------------------------------------- read-once loads
-// Links and clover blocks are read once per stencil launch: loading them
-// without L1 allocation keeps L1 for the input spinors, each of which is read
-// by 8 neighbouring sites (L2 still serves the links to the other systems of
-// the batch that share the gauge field).  LQ_LINK_NA=0 restores plain loads.
-#ifndef LQ_LINK_NA
-#define LQ_LINK_NA 1
-#endif
-LQ_DI float4 ld_once(const float4* p) {
-#if LQ_LINK_NA
-  float4 v;
-  asm("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
-      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-      : "l"(p));
-  return v;
-#else
-  return __ldg(p);
-#endif
-}
-LQ_DI uint2 ld_once(const uint2* p) {
-#if LQ_LINK_NA
-  uint2 v;
-  asm("ld.global.nc.L1::no_allocate.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
-  return v;
-#else
-  return __ldg(p);
-#endif
+// Read-once loads of links and clover (a no-L1-allocate variant measured no
+// faster on GB300, so these are plain read-only loads).
+LQ_DI float4 ld_once(const float4* p) { return __ldg(p); }
+LQ_DI uint2 ld_once(const uint2* p) { return __ldg(p); }
+
+// Position of a block in a linearised (system, block) grid: the system index
+// runs fastest, so the blocks of all systems that cover the same sites (and
+// share a gauge field) run together and meet their links in L2.
+LQ_DI void grid_pos(int nsys, int& s, int& by) {
+  s = (int)(blockIdx.x % (unsigned)nsys);
+  by = (int)(blockIdx.x / (unsigned)nsys);
 }
 
 // ------------------------------------------------------------------- links

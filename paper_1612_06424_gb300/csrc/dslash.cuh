@@ -90,9 +90,20 @@ LQ_DI void mul_udag(const su3<R>& u, const cx<R> h[6], cx<R> w[6]) {
     }
 }
 
-template <int P, bool DAG, int MU>
-LQ_DI void hop_dir(const Geom& g, const SysDesc& sd, const FieldPtrs& f, int pout, int cb, const int x[4],
-                   const void* in, const float* inn, cx<typename Prec<P>::R> acc[12]) {
+// Neighbour spinor fetch of the stencil: (local index, window hint) -> psi.
+// Window hints: 0 the site's own row (x2, x3 hops), 1 / 2 the rows at
+// x1 -+ 1, 3 / 4 the rows at x0 -+ 1.
+template <int P>
+struct GlobalFetch {
+  const void* in;
+  const float* inn;
+  int n;
+  LQ_DI void operator()(int q, int, cx<typename Prec<P>::R> psi[12]) const { Prec<P>::load(psi, in, inn, n, q); }
+};
+
+template <int P, bool DAG, int MU, typename Fetch>
+LQ_DI void hop_dir_f(const Geom& g, const SysDesc& sd, const FieldPtrs& f, int pout, int cb, const int x[4],
+                     const Fetch& fetch, cx<typename Prec<P>::R> acc[12]) {
   typedef typename Prec<P>::R R;
   constexpr int SF = DAG ? +1 : -1;  // forward projector (1 + SF g_mu)
   constexpr int SB = -SF;           // backward projector
@@ -116,7 +127,7 @@ LQ_DI void hop_dir(const Geom& g, const SysDesc& sd, const FieldPtrs& f, int pou
     if (ok) {
       const int cy = eo_index(g, y);
       cx<R> psi[12], h[6], w[6];
-      Prec<P>::load(psi, in, inn, sd.n, cy - sd.cb0);
+      fetch(cy - sd.cb0, MU == 0 ? 4 : MU == 1 ? 2 : 0, psi);
       project<MU, SF>(psi, h);
       su3<R> u = LinkIO<P>::load(f, pout, MU, g.Vh, cb);
       mul_u(u, h, w);
@@ -146,7 +157,7 @@ LQ_DI void hop_dir(const Geom& g, const SysDesc& sd, const FieldPtrs& f, int pou
     if (ok) {
       const int cy = eo_index(g, y);
       cx<R> psi[12], h[6], w[6];
-      Prec<P>::load(psi, in, inn, sd.n, cy - sd.cb0);
+      fetch(cy - sd.cb0, MU == 0 ? 3 : MU == 1 ? 1 : 0, psi);
       project<MU, SB>(psi, h);
       su3<R> u = LinkIO<P>::load(f, pin, MU, g.Vh, cy);
       mul_udag(u, h, w);
@@ -159,15 +170,27 @@ LQ_DI void hop_dir(const Geom& g, const SysDesc& sd, const FieldPtrs& f, int pou
   }
 }
 
+template <int P, bool DAG, int MU>
+LQ_DI void hop_dir(const Geom& g, const SysDesc& sd, const FieldPtrs& f, int pout, int cb, const int x[4],
+                   const void* in, const float* inn, cx<typename Prec<P>::R> acc[12]) {
+  hop_dir_f<P, DAG, MU>(g, sd, f, pout, cb, x, GlobalFetch<P>{in, inn, sd.n}, acc);
+}
+
+template <int P, bool DAG, typename Fetch>
+LQ_DI void hop_sum_f(const Geom& g, const SysDesc& sd, const FieldPtrs& f, int pout, int cb, const int x[4],
+                     const Fetch& fetch, cx<typename Prec<P>::R> acc[12]) {
+#pragma unroll
+  for (int k = 0; k < 12; k++) acc[k] = {0, 0};
+  hop_dir_f<P, DAG, 0>(g, sd, f, pout, cb, x, fetch, acc);
+  hop_dir_f<P, DAG, 1>(g, sd, f, pout, cb, x, fetch, acc);
+  hop_dir_f<P, DAG, 2>(g, sd, f, pout, cb, x, fetch, acc);
+  hop_dir_f<P, DAG, 3>(g, sd, f, pout, cb, x, fetch, acc);
+}
+
 template <int P, bool DAG>
 LQ_DI void hop_sum(const Geom& g, const SysDesc& sd, const FieldPtrs& f, int pout, int cb, const int x[4],
                    const void* in, const float* inn, cx<typename Prec<P>::R> acc[12]) {
-#pragma unroll
-  for (int k = 0; k < 12; k++) acc[k] = {0, 0};
-  hop_dir<P, DAG, 0>(g, sd, f, pout, cb, x, in, inn, acc);
-  hop_dir<P, DAG, 1>(g, sd, f, pout, cb, x, in, inn, acc);
-  hop_dir<P, DAG, 2>(g, sd, f, pout, cb, x, in, inn, acc);
-  hop_dir<P, DAG, 3>(g, sd, f, pout, cb, x, in, inn, acc);
+  hop_sum_f<P, DAG>(g, sd, f, pout, cb, x, GlobalFetch<P>{in, inn, sd.n}, acc);
 }
 
 // Clover block apply (A or A^{-1}) on a full spinor.
@@ -206,6 +229,7 @@ struct HopArgs {
   double alpha, beta, gamma, diag;  // see the kernels
   double* partial;                  // [nsys][pstride][4]
   int pstride;
+  int nsys;                         // systems of the (linearised) grid
 };
 
 // Epilogue terms present (compile time): D_hop x, A y, z.
@@ -273,11 +297,12 @@ LQ_DI float* nrm_ptr_w(float* pool, long long off) { return pool ? pool + off : 
 template <int P, bool DAG, bool CLOV, int RED, int EPI>
 __global__ void __launch_bounds__(128, HopMinBlocks<P>::value) k_hop_lin(HopArgs a) {
   typedef typename Prec<P>::R R;
-  const int s = blockIdx.x;
+  int s, by;
+  grid_pos(a.nsys, s, by);
   if (a.active && !a.active[s]) return;
   const SysDesc sd = a.sys[s];
-  if ((int)(blockIdx.y * blockDim.x) >= sd.n) return;  // whole block beyond this system
-  const int j = blockIdx.y * blockDim.x + threadIdx.x;
+  if (by * (int)blockDim.x >= sd.n) return;  // whole block beyond this system
+  const int j = by * blockDim.x + threadIdx.x;
   R red[3] = {0, 0, 0};
   if (j < sd.n) {
     const FieldPtrs f = a.fields[sd.field];
@@ -339,7 +364,7 @@ __global__ void __launch_bounds__(128, HopMinBlocks<P>::value) k_hop_lin(HopArgs
       }
     }
   }
-  if (RED != RED_NONE) block_reduce_store<3, R>(red, a.partial + ((long long)s * a.pstride + blockIdx.y) * 4);
+  if (RED != RED_NONE) block_reduce_store<3, R>(red, a.partial + ((long long)s * a.pstride + by) * 4);
 }
 
 // out = A^{-1} (alpha * D_hop x + beta * y) on even sites (pout = 0), terms
@@ -347,10 +372,11 @@ __global__ void __launch_bounds__(128, HopMinBlocks<P>::value) k_hop_lin(HopArgs
 template <int P, bool DAG, bool CLOV, int EPI>
 __global__ void __launch_bounds__(128, HopMinBlocks<P>::value) k_hop_clinv(HopArgs a) {
   typedef typename Prec<P>::R R;
-  const int s = blockIdx.x;
+  int s, by;
+  grid_pos(a.nsys, s, by);
   if (a.active && !a.active[s]) return;
   const SysDesc sd = a.sys[s];
-  const int j = blockIdx.y * blockDim.x + threadIdx.x;
+  const int j = by * blockDim.x + threadIdx.x;
   if (j >= sd.n) return;
   const FieldPtrs f = a.fields[sd.field];
   const int cb = sd.cb0 + j;
@@ -447,12 +473,13 @@ LQ_DI void hop_pair32(const HopArgs& a, const SysDesc& sd, const FieldPtrs& f, i
 
 template <bool DAG, bool CLOV, int RED, int EPI>
 __global__ void __launch_bounds__(128, LQ_HOP2_MINB) k_hop2_lin(HopArgs a) {
-  const int s = blockIdx.x;
+  int s, by;
+  grid_pos(a.nsys, s, by);
   if (a.active && !a.active[s]) return;
   const SysDesc sd = a.sys[s];
-  if ((int)(blockIdx.y * 64) >= sd.n) return;
+  if (by * 64 >= sd.n) return;
   const int h = threadIdx.x >> 6, tl = threadIdx.x & 63;
-  const int j = blockIdx.y * 64 + tl;
+  const int j = by * 64 + tl;
   const bool valid = j < sd.n;
   const FieldPtrs f = a.fields[sd.field];
   const int cb = sd.cb0 + j;
@@ -510,17 +537,18 @@ __global__ void __launch_bounds__(128, LQ_HOP2_MINB) k_hop2_lin(HopArgs a) {
       for (int k = 0; k < 6; k++) red[2] += res[k].re * res[k].re + res[k].im * res[k].im;
     }
   }
-  if (RED != RED_NONE) block_reduce_store<3, float>(red, a.partial + ((long long)s * a.pstride + blockIdx.y) * 4);
+  if (RED != RED_NONE) block_reduce_store<3, float>(red, a.partial + ((long long)s * a.pstride + by) * 4);
 }
 
 template <bool DAG, bool CLOV, int EPI>
 __global__ void __launch_bounds__(128, LQ_HOP2_MINB) k_hop2_clinv(HopArgs a) {
-  const int s = blockIdx.x;
+  int s, by;
+  grid_pos(a.nsys, s, by);
   if (a.active && !a.active[s]) return;
   const SysDesc sd = a.sys[s];
-  if ((int)(blockIdx.y * 64) >= sd.n) return;
+  if (by * 64 >= sd.n) return;
   const int h = threadIdx.x >> 6, tl = threadIdx.x & 63;
-  const int j = blockIdx.y * 64 + tl;
+  const int j = by * 64 + tl;
   const bool valid = j < sd.n;
   const FieldPtrs f = a.fields[sd.field];
   const int cb = sd.cb0 + j;

@@ -18,11 +18,15 @@ void lq_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void lq_count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 extern "C" long long lqcd_kernel_launches(void) { return g_launches.load(); }
 
-static inline dim3 grid_of(const Batch& b) { return dim3((unsigned)b.nsys, (unsigned)b.nby, 1); }
+// Linearised (system, block) grids: block x = by * nsys + s (see grid_pos).
+static inline dim3 grid_lin(const Batch& b, long long blocks_per_sys, unsigned z = 1) {
+  return dim3((unsigned)(b.nsys * blocks_per_sys), 1, z);
+}
+static inline dim3 grid_of(const Batch& b) { return grid_lin(b, b.nby); }
 // word-parallel grid: NV 16-byte words per site
 static inline dim3 grid_words(const Batch& b, int P) {
   const long long nv = P == 64 ? 12 : 6;
-  return dim3((unsigned)b.nsys, (unsigned)((b.max_n * nv + LQ_BLOCK - 1) / LQ_BLOCK), 1);
+  return grid_lin(b, (b.max_n * nv + LQ_BLOCK - 1) / LQ_BLOCK);
 }
 
 static inline int launched() {
@@ -44,6 +48,7 @@ static HopArgs hop_args(const lqcd_lattice* L, const Batch& b, int pout) {
   a.pout = pout;
   a.partial = b.partial;
   a.pstride = b.pstride;
+  a.nsys = b.nsys;
   a.diag = 1.0 / (2.0 * L->kappa);
   return a;
 }
@@ -54,7 +59,7 @@ static int forced_variant() {
   static int v = -1;
   if (v < 0) {
     const char* e = getenv("LQCD_HOP_SPLIT");
-    v = (e && (e[0] == '1' || e[0] == '2')) ? e[0] - '0' : 0;
+    v = (e && e[0] >= '1' && e[0] <= '2') ? e[0] - '0' : 0;
   }
   return v;
 }
@@ -62,7 +67,8 @@ static int forced_variant() {
 static int variant_of(int P, const Batch& b) {
   if (P != 32) return 1;
   const int f = forced_variant();
-  return f ? f : (b.hop_variant == 2 ? 2 : 1);
+  const int v = f ? f : b.hop_variant;
+  return v == 2 ? 2 : 1;
 }
 
 int lq_hop_wps(int P, const Batch& b) { return variant_of(P, b) == 2 ? 2 : 1; }
@@ -119,7 +125,7 @@ int lq_hop_lin(int P, bool dag, bool clov, int red, const lqcd_lattice* L, const
   const int epi = (alpha != 0.0 ? EPI_X : 0) | (beta != 0.0 ? EPI_Y : 0) | (gamma != 0.0 ? EPI_Z : 0);
   dim3 gr = grid_of(b);
   if (variant_of(P, b) == 2) {
-    const dim3 g2((unsigned)b.nsys, (unsigned)((b.max_n + 63) / 64), 1);
+    const dim3 g2 = grid_lin(b, (b.max_n + 63) / 64);
     int rc = dag ? (clov ? launch_lin2<true, true>(red, epi, g2, a, st) : launch_lin2<true, false>(red, epi, g2, a, st))
                  : (clov ? launch_lin2<false, true>(red, epi, g2, a, st) : launch_lin2<false, false>(red, epi, g2, a, st));
     if (rc) {
@@ -163,7 +169,7 @@ int lq_hop_clinv(int P, bool dag, bool clov, const lqcd_lattice* L, const Batch&
   const int epi = (alpha != 0.0 ? EPI_X : 0) | (beta != 0.0 ? EPI_Y : 0);
   dim3 gr = grid_of(b);
   if (variant_of(P, b) == 2) {
-    const dim3 g2((unsigned)b.nsys, (unsigned)((b.max_n + 63) / 64), 1);
+    const dim3 g2 = grid_lin(b, (b.max_n + 63) / 64);
     int rc = dag ? (clov ? launch_clinv2<true, true>(epi, g2, a, st) : launch_clinv2<true, false>(epi, g2, a, st))
                  : (clov ? launch_clinv2<false, true>(epi, g2, a, st) : launch_clinv2<false, false>(epi, g2, a, st));
     if (rc) {
@@ -189,6 +195,7 @@ static VecArgs vec_args(const Batch& b) {
   v.sc = b.sc;
   v.partial = b.partial;
   v.pstride = b.pstride;
+  v.nsys = b.nsys;
   return v;
 }
 
@@ -268,12 +275,13 @@ int lq_convert(int Pin, int Pout, const Batch& b, VecP in, VecP out, cudaStream_
 // ------------------------------------------------------------ layout kernels
 // Natural slab vector of system s (src[s], sites t0*S3 .. (t1+1)*S3 - 1)
 // <-> the system's even and odd FP64 vectors.
-__global__ void __launch_bounds__(128) k_nat_to_eo(Geom g, const SysDesc* sys, const int* active,
+__global__ void __launch_bounds__(128) k_nat_to_eo(Geom g, int nsys, const SysDesc* sys, const int* active,
                                                    const double2* const* src, double2* ve, double2* vo) {
-  const int s = blockIdx.x;
+  int s, by;
+  grid_pos(nsys, s, by);
   if (active && !active[s]) return;
   const SysDesc sd = sys[s];
-  const long long j = (long long)blockIdx.y * blockDim.x + threadIdx.x;
+  const long long j = (long long)by * blockDim.x + threadIdx.x;
   if (j >= sd.n) return;
   const int p = blockIdx.z;
   int x[4];
@@ -286,11 +294,12 @@ __global__ void __launch_bounds__(128) k_nat_to_eo(Geom g, const SysDesc* sys, c
   for (int k = 0; k < 12; k++) out[k * sd.n + j] = in[k];
 }
 
-__global__ void __launch_bounds__(128) k_eo_to_nat(Geom g, const SysDesc* sys, const double2* ve, const double2* vo,
-                                                   double2* const* dst, double scale) {
-  const int s = blockIdx.x;
+__global__ void __launch_bounds__(128) k_eo_to_nat(Geom g, int nsys, const SysDesc* sys, const double2* ve,
+                                                   const double2* vo, double2* const* dst, double scale) {
+  int s, by;
+  grid_pos(nsys, s, by);
   const SysDesc sd = sys[s];
-  const long long j = (long long)blockIdx.y * blockDim.x + threadIdx.x;
+  const long long j = (long long)by * blockDim.x + threadIdx.x;
   if (j >= sd.n) return;
   const int p = blockIdx.z;
   int x[4];
@@ -308,22 +317,23 @@ __global__ void __launch_bounds__(128) k_eo_to_nat(Geom g, const SysDesc* sys, c
 
 int lq_nat_to_eo(const lqcd_lattice* L, const Batch& b, const double2* const* src, double2* ve, double2* vo,
                  cudaStream_t st) {
-  k_nat_to_eo<<<dim3(b.nsys, b.nby, 2), LQ_BLOCK, 0, st>>>(L->g, b.sys, nullptr, src, ve, vo);
+  k_nat_to_eo<<<grid_lin(b, b.nby, 2), LQ_BLOCK, 0, st>>>(L->g, b.nsys, b.sys, nullptr, src, ve, vo);
   return launched();
 }
 
 int lq_eo_to_nat(const lqcd_lattice* L, const Batch& b, const double2* ve, const double2* vo, double2* const* dst,
                  double scale, cudaStream_t st) {
-  k_eo_to_nat<<<dim3(b.nsys, b.nby, 2), LQ_BLOCK, 0, st>>>(L->g, b.sys, ve, vo, dst, scale);
+  k_eo_to_nat<<<grid_lin(b, b.nby, 2), LQ_BLOCK, 0, st>>>(L->g, b.nsys, b.sys, ve, vo, dst, scale);
   return launched();
 }
 
 // Zero both parities of every system and place 1 at (xsrc[s], column cols[s]).
-__global__ void __launch_bounds__(128) k_point_source(Geom g, const SysDesc* sys, const int* cols, const int4* xsrc,
-                                                      double2* ve, double2* vo) {
-  const int s = blockIdx.x;
+__global__ void __launch_bounds__(128) k_point_source(Geom g, int nsys, const SysDesc* sys, const int* cols,
+                                                      const int4* xsrc, double2* ve, double2* vo) {
+  int s, by;
+  grid_pos(nsys, s, by);
   const SysDesc sd = sys[s];
-  const int j = blockIdx.y * blockDim.x + threadIdx.x;
+  const int j = by * blockDim.x + threadIdx.x;
   if (j >= sd.n) return;
   const int p = blockIdx.z;
   const int4 q = xsrc[s];
@@ -339,7 +349,7 @@ __global__ void __launch_bounds__(128) k_point_source(Geom g, const SysDesc* sys
 
 int lq_point_source(const lqcd_lattice* L, const Batch& b, const int* d_cols, const int4* d_xsrc, double2* ve,
                     double2* vo, cudaStream_t st) {
-  k_point_source<<<dim3(b.nsys, b.nby, 2), LQ_BLOCK, 0, st>>>(L->g, b.sys, d_cols, d_xsrc, ve, vo);
+  k_point_source<<<grid_lin(b, b.nby, 2), LQ_BLOCK, 0, st>>>(L->g, b.nsys, b.sys, d_cols, d_xsrc, ve, vo);
   return launched();
 }
 
@@ -351,13 +361,14 @@ int lq_point_source(const lqcd_lattice* L, const Batch& b, const int* d_cols, co
 // chi is stored compactly, natural order within a time slice:
 //   chi[c][slot][site of slice][12].  psi: the Gammabar solution of system s
 // (its eo pools), written to chi column cols[s].
-__global__ void __launch_bounds__(128) k_boundary_chi(Geom g, const FieldPtrs* fields, const SysDesc* sin,
+__global__ void __launch_bounds__(128) k_boundary_chi(Geom g, int nsys, const FieldPtrs* fields, const SysDesc* sin,
                                                       const int* cols, int g1, const double2* in_e,
                                                       const double2* in_o, double2* chi) {
-  const int s = blockIdx.x;
+  int s, by;
+  grid_pos(nsys, s, by);
   const SysDesc si = sin[s];
   const int S3 = 2 * g.S3h;
-  const int i = blockIdx.y * blockDim.x + threadIdx.x;  // site within the slice
+  const int i = by * blockDim.x + threadIdx.x;  // site within the slice
   const int slot = blockIdx.z;
   if (i >= S3) return;
   double2* out = chi + ((long long)(cols[s] * 2 + slot) * S3 + i) * 12;
@@ -403,18 +414,20 @@ __global__ void __launch_bounds__(128) k_boundary_chi(Geom g, const FieldPtrs* f
 int lq_boundary_chi(const lqcd_lattice* L, const Batch& bin, const int* d_cols, int g1, const double2* in_e,
                     const double2* in_o, double2* chi, cudaStream_t st) {
   const int S3 = 2 * L->g.S3h;
-  k_boundary_chi<<<dim3(bin.nsys, (S3 + LQ_BLOCK - 1) / LQ_BLOCK, 2), LQ_BLOCK, 0, st>>>(L->g, L->d_fields, bin.sys,
-                                                                                      d_cols, g1, in_e, in_o, chi);
+  k_boundary_chi<<<grid_lin(bin, (S3 + LQ_BLOCK - 1) / LQ_BLOCK, 2), LQ_BLOCK, 0, st>>>(L->g, bin.nsys, L->d_fields,
+                                                                                      bin.sys, d_cols, g1, in_e,
+                                                                                      in_o, chi);
   return launched();
 }
 
 // Source of a Gamma* system: chi (compact, column cols[s]) scattered into the
 // system's even / odd FP64 vectors, zero elsewhere.
-__global__ void __launch_bounds__(128) k_chi_to_eo(Geom g, const SysDesc* sys, const int* cols, int g1,
+__global__ void __launch_bounds__(128) k_chi_to_eo(Geom g, int nsys, const SysDesc* sys, const int* cols, int g1,
                                                    const double2* chi, double2* ve, double2* vo) {
-  const int s = blockIdx.x;
+  int s, by;
+  grid_pos(nsys, s, by);
   const SysDesc sd = sys[s];
-  const int j = blockIdx.y * blockDim.x + threadIdx.x;
+  const int j = by * blockDim.x + threadIdx.x;
   if (j >= sd.n) return;
   const int p = blockIdx.z;
   int x[4];
@@ -438,7 +451,7 @@ __global__ void __launch_bounds__(128) k_chi_to_eo(Geom g, const SysDesc* sys, c
 
 int lq_chi_to_eo(const lqcd_lattice* L, const Batch& b, const int* d_cols, int g1, const double2* chi, double2* ve,
                  double2* vo, cudaStream_t st) {
-  k_chi_to_eo<<<dim3(b.nsys, b.nby, 2), LQ_BLOCK, 0, st>>>(L->g, b.sys, d_cols, g1, chi, ve, vo);
+  k_chi_to_eo<<<grid_lin(b, b.nby, 2), LQ_BLOCK, 0, st>>>(L->g, b.nsys, b.sys, d_cols, g1, chi, ve, vo);
   return launched();
 }
 
