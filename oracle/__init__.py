@@ -235,3 +235,26 @@ def link_force(op: Operator, phi: np.ndarray, t0: int, t1: int, tol: float = 1e-
     X, _, _ = op.solve(Y, t0, t1, dagger=False, tol=tol)
     S = float(np.real(np.vdot(phi_m, X)))
     return op.force(X, Y, t0, t1), S, X, Y
+
+
+def disconnected_trace(op: Operator, etas: np.ndarray, t0: int, t1: int, tol: float = 1e-13,
+                       hops: int = 8) -> np.ndarray:
+    """Stochastic estimate of sum_x tr{gamma_5 D_L^{-1}(x,x)} per time slice x0 of the
+    slab L = t0..t1 (Sec. 4.1, eq. stochastic_estimator), plain Wilson operator:
+        t(x0) = (1/n_src) sum_i sum_{x in slice x0} eta_i^dag(x) [(kappa D_hop)^8 D_L^{-1} gamma_5 eta_i](x),
+    with 2 kappa D = 1 - kappa D_hop, i.e. kappa D_hop psi = psi - 2 kappa D_L psi on the slab.
+    etas: (n_src, V, 4, 3) sources (only their slab part is used).  Returns complex (T,) with
+    zeros outside the slab.  `hops` exists only so that a test can plant a wrong power."""
+    if op.csw != 0.0:
+        raise ValueError("the (kappa D_hop)^8 subtraction of eq. stochastic_estimator is for the Wilson operator")
+    g5 = gamma(4)
+    s3 = op.V // op.T
+    out = np.zeros(op.T, dtype=np.complex128)
+    for eta in etas:
+        e = op.masked(eta, t0, t1)
+        psi, _, _ = op.solve(np.einsum("st,xtc->xsc", g5, e), t0, t1, tol=tol)
+        for _ in range(hops):
+            psi = psi - 2 * op.kappa * op.apply(psi, t0, t1)
+        prod = np.sum(np.conj(e) * psi, axis=(1, 2))
+        out += prod.reshape(op.T, s3).sum(axis=1)
+    return out / len(etas)
