@@ -237,24 +237,127 @@ def link_force(op: Operator, phi: np.ndarray, t0: int, t1: int, tol: float = 1e-
     return op.force(X, Y, t0, t1), S, X, Y
 
 
+def disconnected_contract(op: Operator, etas: np.ndarray, psis: np.ndarray, t0: int, t1: int,
+                          hops: int = 8) -> np.ndarray:
+    """The contraction half of eq. stochastic_estimator (Sec. 4.1), given the solutions
+    psi_i = D_L^{-1} gamma_5 eta_i on the slab L = t0..t1 (plain Wilson operator):
+        t(x0) = (1/n_src) sum_i sum_{x in slice x0} eta_i^dag(x) [(kappa D_hop)^hops psi_i](x),
+    kappa D_hop psi = psi - 2 kappa D_L psi (since 2 kappa D = 1 - kappa D_hop).
+    etas, psis: (n_src, V, 4, 3).  Returns complex (T,), zero outside the slab.
+    `hops` exists only so that a test can plant a wrong power."""
+    if op.csw != 0.0:
+        raise ValueError("the (kappa D_hop)^8 subtraction of eq. stochastic_estimator is for the Wilson operator")
+    s3 = op.V // op.T
+    out = np.zeros(op.T, dtype=np.complex128)
+    for eta, psi in zip(etas, psis):
+        e = op.masked(eta, t0, t1)
+        y = op.masked(psi, t0, t1)
+        for _ in range(hops):
+            y = y - 2 * op.kappa * op.apply(y, t0, t1)
+        prod = np.sum(np.conj(e) * y, axis=(1, 2))
+        out += prod.reshape(op.T, s3).sum(axis=1)
+    return out / len(etas)
+
+
 def disconnected_trace(op: Operator, etas: np.ndarray, t0: int, t1: int, tol: float = 1e-13,
                        hops: int = 8) -> np.ndarray:
     """Stochastic estimate of sum_x tr{gamma_5 D_L^{-1}(x,x)} per time slice x0 of the
     slab L = t0..t1 (Sec. 4.1, eq. stochastic_estimator), plain Wilson operator:
-        t(x0) = (1/n_src) sum_i sum_{x in slice x0} eta_i^dag(x) [(kappa D_hop)^8 D_L^{-1} gamma_5 eta_i](x),
-    with 2 kappa D = 1 - kappa D_hop, i.e. kappa D_hop psi = psi - 2 kappa D_L psi on the slab.
+        t(x0) = (1/n_src) sum_i sum_{x in slice x0} eta_i^dag(x) [(kappa D_hop)^8 D_L^{-1} gamma_5 eta_i](x).
     etas: (n_src, V, 4, 3) sources (only their slab part is used).  Returns complex (T,) with
-    zeros outside the slab.  `hops` exists only so that a test can plant a wrong power."""
+    zeros outside the slab."""
     if op.csw != 0.0:
         raise ValueError("the (kappa D_hop)^8 subtraction of eq. stochastic_estimator is for the Wilson operator")
     g5 = gamma(4)
-    s3 = op.V // op.T
-    out = np.zeros(op.T, dtype=np.complex128)
+    psis = []
     for eta in etas:
         e = op.masked(eta, t0, t1)
         psi, _, _ = op.solve(np.einsum("st,xtc->xsc", g5, e), t0, t1, tol=tol)
-        for _ in range(hops):
-            psi = psi - 2 * op.kappa * op.apply(psi, t0, t1)
-        prod = np.sum(np.conj(e) * psi, axis=(1, 2))
-        out += prod.reshape(op.T, s3).sum(axis=1)
-    return out / len(etas)
+        psis.append(psi)
+    return disconnected_contract(op, etas, np.asarray(psis), t0, t1, hops=hops)
+
+
+# --------------------------------------------------------------------------
+# Quark-line projection (Sec. 3.3 eqs. projection, quark_prop_II_proj; Sec. 5)
+
+def orthonormalize(W: np.ndarray) -> np.ndarray:
+    """The orthonormal factor Q of W = Q R (columns of W (n, N) linearly independent), with R
+    upper triangular and real positive on its diagonal, which makes Q unique: numpy's
+    Householder QR, its column phases fixed."""
+    Q, R = np.linalg.qr(W)
+    d = np.diag(R)
+    return Q * (d / np.abs(d))[None, :]
+
+
+def spin_project_plus(v: np.ndarray) -> np.ndarray:
+    """P_+ v = (1 + gamma_0)/2 v on the spin index (axis -2 of (..., 4, 3)): the half of a
+    spinor on the last slice of Gamma that the boundary block D_dGamma* reads (its backward
+    time hop carries (1 + gamma_0))."""
+    return np.einsum("st,...tc->...sc", 0.5 * (np.eye(4) + gamma(0)), v)
+
+
+def boundary_modes(op: Operator, v0: np.ndarray, t0: int, t1: int, g1: int, n_iter: int,
+                   tol: float = 1e-13) -> np.ndarray:
+    """N_m orthonormal projection vectors on the time slice g1 (the external boundary of Gamma*),
+    from n_iter inverse iterations of D on the slab L = t0..t1 (Sec. 5): starting from the slab
+    part of v0 (N_m, V, 4, 3), each iteration solves W_i = D_L^{-1} V_i for every column and
+    orthonormalises, V = orthonormalize(W); the result is phi = orthonormalize(P_+ V|_{g1})
+    (reading: the vectors live in the 6 L^3-dimensional space that D_dGamma* reads, Sec. 3.3).
+    Returns phi (N_m, S3, 4, 3)."""
+    s3 = op.V // op.T
+    m = op.slab(t0, t1)
+    n_m = v0.shape[0]
+    Vc = np.stack([v0[i].reshape(op.V, 12)[m].reshape(-1) for i in range(n_m)], axis=1)
+    for _ in range(n_iter):
+        W = np.empty_like(Vc)
+        for i in range(n_m):
+            full = np.zeros((op.V, 12), dtype=np.complex128)
+            full[m] = Vc[:, i].reshape(-1, 12)
+            x, _, _ = op.solve(full.reshape(op.V, 4, 3), t0, t1, tol=tol)
+            W[:, i] = x.reshape(op.V, 12)[m].reshape(-1)
+        Vc = orthonormalize(W)
+    lo = (g1 - t0) * s3
+    sl = Vc.reshape(-1, 12, n_m)[lo:lo + s3]                     # (S3, 12, N_m)
+    sl = np.moveaxis(sl, 2, 0).reshape(n_m, s3, 4, 3)
+    P = spin_project_plus(sl).reshape(n_m, s3 * 12).T
+    return orthonormalize(P).T.reshape(n_m, s3, 4, 3)
+
+
+def _on_slice(op: Operator, v: np.ndarray, t: int) -> np.ndarray:
+    """Place a slice vector (S3, 4, 3) on time slice t of a zero lattice vector."""
+    s3 = op.V // op.T
+    out = np.zeros((op.V, 4, 3), dtype=np.complex128)
+    out[t * s3:(t + 1) * s3] = v
+    return out
+
+
+def projected_factors(op: Operator, split: Split, phis: np.ndarray, tol: float = 1e-13):
+    """The two factors of eq. quark_prop_II_proj for projection vectors phi_i on the last slice
+    of Gamma (phis (N_m, S3, 4, 3)):
+        xi_i  = D_Gammabar^{-dag} phi_i, so that [phi_i^dag D_Gammabar^{-1}](x) = xi_i(x)^dag,
+        eta_i = D_Gamma*^{-1} D_dGamma* phi_i.
+    Returns (xi, eta), each (N_m, V, 4, 3)."""
+    g, gs, gb = split.gamma, split.gamma_star, split.gamma_bar
+    xi = np.zeros((phis.shape[0], op.V, 4, 3), dtype=np.complex128)
+    eta = np.zeros_like(xi)
+    for i, ph in enumerate(phis):
+        p = _on_slice(op, ph, g[1])
+        xi[i], _, _ = op.solve(p, *gb, dagger=True, tol=tol)
+        eta[i], _, _ = op.solve(op.boundary_hop(p, g, gs), *gs, tol=tol)
+    return xi, eta
+
+
+def projected_propagator(op: Operator, split: Split, xi: np.ndarray, eta: np.ndarray, x_src) -> np.ndarray:
+    """Case II of the factorized propagator with the quark line cut by P_L (eq. quark_prop_II_proj),
+    12 point sources at x_src: for y in Gamma*,
+        fact[b](y)[a] = -sum_i eta_i(y)[a] conj(xi_i(x)[b]),   b = 3 s0 + c0 the source column.
+    Returns (12, V, 4, 3), zero outside Gamma*."""
+    s3 = op.V // op.T
+    L = op.dims
+    x = ((x_src[0] * L[1] + x_src[1]) * L[2] + x_src[2]) * L[3] + x_src[3]
+    m = op.slab(*split.gamma_star)
+    E = eta.reshape(eta.shape[0], op.V, 12)
+    Xx = xi.reshape(xi.shape[0], op.V, 12)[:, x, :]             # (N_m, 12): xi_i(x)[b]
+    out = -np.einsum("iya,ib->bya", E, np.conj(Xx))
+    out[:, ~m] = 0
+    return out.reshape(12, op.V, 4, 3)
