@@ -66,8 +66,11 @@ def _args():
     ap.add_argument("--no-fp64-form", action="store_true", help="skip timing the plain FP64 form")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="factorized_16x32",
-                    choices=["factorized_16x32", "batched_32x64", "force_24x48", "factorized_48x96"])
+                    choices=["factorized_16x32", "batched_32x64", "force_24x48", "factorized_48x96",
+                             "disconnected_64x24", "projection_64x24"])
     ap.add_argument("--fields", type=int, default=8, help="inner-level fields of factorized_48x96")
+    ap.add_argument("--sources", type=int, default=100, help="Gaussian sources of disconnected_64x24")
+    ap.add_argument("--modes", type=int, default=120, help="projection vectors of projection_64x24")
     return ap.parse_args()
 
 
@@ -400,6 +403,157 @@ def run_factorized_48(args):
     lat.close()
 
 
+def _oracle_disconnected_sample(U, dims, kappa, doms, iters, sample_seconds=12.0):
+    """The oracle (plain FP64 C, one thread) on the host cores, for one source of the
+    disconnected estimator, from a bounded sample: the measured time of one oracle D
+    application on each slab, times (2 per BiCGStab iteration x the GPU solve's iteration
+    count on that slab + 8 hops + 1 for the residual), summed over the slabs; extrapolated."""
+    import oracle
+    from paper_1612_06424_gb300 import inputs
+
+    op = oracle.Operator(dims, U, kappa, 0.0)
+    psi = inputs.gaussian_spinor(dims, 98)[0]
+    per = sample_seconds / len(doms)
+    total, parts = 0.0, []
+    for (a, b), its in zip(doms, iters):
+        t0 = time.perf_counter()
+        n = 0
+        while time.perf_counter() - t0 < per or n < 2:
+            op.apply(psi, a, b)
+            n += 1
+        t = (time.perf_counter() - t0) / n
+        total += t * (2 * its + 9)
+        parts.append(f"slab {a}..{b}: {t:.3f} s x (2 x {its} + 9)")
+    return {"value": total, "unit": "s/source", "cores": 1, "kind": "oracle",
+            "sample": "oracle D applications per slab (" + "; ".join(parts) + "), iteration counts of the GPU "
+                      "solves; per source, extrapolated"}
+
+
+def run_disconnected(args):
+    """64x24^3 Wilson (c_sw = 0), kappa 0.1360, open time boundaries: the stochastic
+    disconnected traces of Sec. 4.1 with `--sources` Gaussian sources (100 in the paper) on
+    Gamma = t 0..32 and Gamma* = 33..63 (Dirichlet blocks) and on the full lattice, all
+    solved together; eight (kappa D_hop) hops and per-slice contractions on the GPU."""
+    import numpy as np
+    import torch
+
+    from paper_1612_06424_gb300 import build, inputs, lqcd
+
+    build.build()
+    dims = (64, 24, 24, 24)
+    kappa = 0.136
+    doms = [(0, 32), (33, 63), (0, 63)]
+    U = inputs.random_su3_field_device(dims, 0.4, 21, device="cuda")
+    lat = lqcd.Lattice(dims, "open")
+    lat.set_gauge(U, kappa, 0.0)
+    del U
+    eta = inputs.gaussian_spinor_device(dims, 22, args.sources, device="cuda")
+    params = lqcd.SolverParams(tol=1e-10, precision=args.precision)
+    for _ in range(max(1, args.warmup)):
+        lat.disconnected_trace(eta[:4], doms, 0, params)
+    torch.cuda.synchronize()
+    n0 = lqcd.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks() as clk:
+        e0.record()
+        for _ in range(args.steps):
+            tr, mean, st = lat.disconnected_trace(eta, doms, 0, params)
+        e1.record()
+        torch.cuda.synchronize()
+    launches = lqcd.kernel_launches() - n0
+    sec = e0.elapsed_time(e1) / 1e3 / args.steps
+    # roofline of the FP32 hop kernel on the same batch shape
+    n_rf = min(args.sources, 24)
+    ms, by, fl = lat.dslash_bench([d for _ in range(n_rf) for d in doms], [0] * (3 * n_rf), args.precision, 20)
+    hbm, hbm_src = _peaks()
+    mean_h = mean.cpu().numpy()
+    out = {
+        "metric": "s per Gaussian source of the disconnected estimator (Gamma, Gamma*, full) @ res 1e-10 (64x24^3)",
+        "value": sec / args.sources, "unit": "s/source", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": sec * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": {64: "f64", 32: "f32+f64", 16: "f16+f32+f64"}[args.precision], "data": "synthetic",
+        "config": {"workload": "64x24^3 Wilson disconnected traces", "dims": list(dims), "kappa": kappa, "c_sw": 0.0,
+                   "domains": [list(d) for d in doms], "sources": args.sources, "l2": "inputs larger than L2"},
+        "iters": {n: s["iters"] for n, s in zip(["gamma", "gamma_star", "full"], st)},
+        "true_residual_max": max(s["true_residual"] for s in st),
+        "sum_over_slices": {n: [float(np.sum(mean_h[d]).real), float(np.sum(mean_h[d]).imag)]
+                            for d, n in enumerate(["gamma", "gamma_star", "full"])},
+        "roofline": {"bound": "hbm", "achieved": by / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                     "frac": by / (ms * 1e-3) / 1e9 / hbm, "traffic": None, "peak_source": hbm_src,
+                     "kernel": f"FP{args.precision} hop kernel, {3 * n_rf} systems of this workload's slabs"},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline:
+        Uh = inputs.random_su3_field(dims, 0.4, 21)
+        out["cpu_baseline"] = _oracle_disconnected_sample(Uh, dims, kappa, doms, [s["iters"] for s in st])
+    print(json.dumps(out))
+    lat.close()
+
+
+def run_projection(args):
+    """64x24^3 Wilson (c_sw = 0), kappa 0.1360, open time boundaries: the quark-line cut of
+    Sec. 3.3 with the Sec. 5 setup for Delta = 8: Gammabar = t 0..31 (Gamma = 0..23,
+    DeltaGamma = 24..31), Gamma* = 24..63; N_m = `--modes` (120 in the paper) projection
+    vectors from 10 inverse iterations on t 16..31, cut on slice 23; the factors xi, eta
+    (2 N_m solves) and the projected case-II propagator for 12 point sources at (4,0,0,0)."""
+    import torch
+
+    from paper_1612_06424_gb300 import build, inputs, lqcd
+
+    build.build()
+    dims = (64, 24, 24, 24)
+    kappa = 0.136
+    G, DL, GS = (0, 23), (24, 31), (24, 63)
+    mdom, g1, n_iter = (16, 31), 23, 10
+    n_m = args.modes
+    U = inputs.random_su3_field_device(dims, 0.4, 31, device="cuda")
+    lat = lqcd.Lattice(dims, "open")
+    lat.set_gauge(U, kappa, 0.0)
+    del U
+    v0 = inputs.gaussian_spinor_device(dims, 32, n_m, device="cuda")
+    s3 = 24 ** 3
+    v0 = v0[:, mdom[0] * s3:(mdom[1] + 1) * s3].contiguous()
+    params = lqcd.SolverParams(tol=1e-10, precision=args.precision)
+    # warm-up on a few modes and one iteration
+    phi_w, _ = lat.boundary_modes(v0[:8], mdom, g1, 0, 1, params)
+    lat.projected_factors(phi_w, G, GS, DL, 0, params)
+    torch.cuda.synchronize()
+    n0 = lqcd.kernel_launches()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    with Clocks() as clk:
+        ev[0].record()
+        phi, st_m = lat.boundary_modes(v0, mdom, g1, 0, n_iter, params)
+        ev[1].record()
+        xi, eta, st_f = lat.projected_factors(phi, G, GS, DL, 0, params)
+        ev[2].record()
+        fact = lat.projected_propagator(xi, eta, G, GS, (4, 0, 0, 0), DL)
+        ev[3].record()
+        torch.cuda.synchronize()
+    launches = lqcd.kernel_launches() - n0
+    t = [ev[i].elapsed_time(ev[i + 1]) / 1e3 for i in range(3)]
+    out = {
+        "metric": "s per projected quark line (N_m modes, 10 inverse iterations, factors, 12-source case-II "
+                  "propagator) @ res 1e-10 (64x24^3)",
+        "value": sum(t), "unit": "s/projected propagator", "n_gpus": 1, "steps": 1, "warmup": 1,
+        "ms_per_step": sum(t) * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": {64: "f64", 32: "f32+f64", 16: "f16+f32+f64"}[args.precision], "data": "synthetic",
+        "config": {"workload": "64x24^3 Wilson quark-line projection, Delta = 8", "dims": list(dims), "kappa": kappa,
+                   "c_sw": 0.0, "gamma": list(G), "delta": list(DL), "gamma_star": list(GS), "modes": n_m,
+                   "mode_slab": list(mdom), "cut_slice": g1, "inverse_iterations": n_iter},
+        "seconds": {"modes": t[0], "factors": t[1], "contraction": t[2]},
+        "iters": {"modes_max": st_m["iters"], "gamma_bar": st_f["gamma_bar"]["iters"],
+                  "gamma_star": st_f["gamma_star"]["iters"]},
+        "true_residual_max": max(st_m["true_residual"], st_f["gamma_bar"]["true_residual"],
+                                 st_f["gamma_star"]["true_residual"]),
+        "fact_norm_gamma_star": float(torch.linalg.vector_norm(fact).item()),
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(out))
+    lat.close()
+
+
 def main():
     args = _args()
     if args.impl == "reference":
@@ -408,6 +562,10 @@ def main():
         return run_batched(args)
     if args.workload == "force_24x48":
         return run_force(args)
+    if args.workload == "disconnected_64x24":
+        return run_disconnected(args)
+    if args.workload == "projection_64x24":
+        return run_projection(args)
     if args.workload == "factorized_48x96":
         return run_factorized_48(args)
     import numpy as np

@@ -61,6 +61,7 @@ extern "C" {
 #define LQCD_ENAN (-6)         /* NaN or Inf in a residual                      */
 #define LQCD_ECUDA (-7)        /* a CUDA runtime call failed                    */
 #define LQCD_ENOFIELD (-8)     /* field index not loaded                        */
+#define LQCD_ERANK (-9)        /* vectors to orthonormalise are linearly dependent */
 
 #define LQCD_BC_OPEN 0
 #define LQCD_BC_PERIODIC 1
@@ -186,6 +187,74 @@ int lqcd_factorized_propagator(lqcd_lattice *lat, const lqcd_split *split, const
  * are recomputed on every call, never cached. */
 int lqcd_link_force(lqcd_lattice *lat, const lqcd_slab *dom, int field, const double *phi, double *force,
                     double *action, const lqcd_solver_params *params, lqcd_solver_stats *stats, void *stream);
+
+/* Projection vectors of the quark-line cut (Sec. 5: N_m orthonormal vectors
+ * from inverse iterations of the Dirac operator on a slab around the
+ * boundary).  Starting from v0 (device, n_modes slab vectors on dom back to
+ * back), each of the n_iter iterations solves D_L w_i = v_i (L = dom, all
+ * i together) and orthonormalises the w_i (Cholesky QR, twice: the unique
+ * orthonormal basis W with V = W R, R upper triangular with positive real
+ * diagonal).  Then phi = the same orthonormalisation of P_+ v_i restricted
+ * to time slice g1 (P_+ = (1 + g0)/2, the half of a spinor that the
+ * boundary block D_dGamma* reads when g1 is the last slice of Gamma; the
+ * span is the 6 L1 L2 L3-dimensional space of Sec. 3.3).
+ * phi: device [n_modes][L1 L2 L3][4][3] complex128, overwritten.
+ * Limits: 1 <= n_modes <= min(1024, 6 L1 L2 L3); g1 inside dom.
+ * stats: host, one entry aggregated over every solve, or NULL.
+ * Errors: LQCD_EBADARG, LQCD_ENOFIELD, LQCD_ERANK (v0 or its slice part
+ * linearly dependent), LQCD_ENOTCONVERGED, LQCD_ECUDA. */
+int lqcd_boundary_modes(lqcd_lattice *lat, const lqcd_slab *dom, int g1, int field, int n_modes, int n_iter,
+                        const double *v0, double *phi, const lqcd_solver_params *params, lqcd_solver_stats *stats,
+                        void *stream);
+
+/* The two factors of the projected quark line (Sec. 3.3 eq.
+ * quark_prop_II_proj) for projection vectors phi_i (device [n_modes][L1 L2
+ * L3][4][3], living on the last slice g1 of Gamma), on field `field`:
+ *   xi_i  = D_Gammabar^{-dag} phi_i   (so [phi_i^dag D_Gammabar^{-1}](x) = xi_i(x)^dag;
+ *                                      the paper's xi_i^T is xi_i^dag)
+ *   eta_i = D_Gamma*^{-1} D_dGamma* phi_i
+ * xi: device [n_modes] slab vectors on Gammabar; eta: device [n_modes] slab
+ * vectors on Gamma*.  Open time boundary only (LQCD_EBADARG otherwise).
+ * stats: host array of 2 entries (the Gammabar and the Gamma* solves) or NULL.
+ * Errors: LQCD_EBADARG, LQCD_ENOFIELD, LQCD_ENOTCONVERGED, LQCD_ECUDA. */
+int lqcd_projected_factors(lqcd_lattice *lat, const lqcd_split *split, int field, int n_modes, const double *phi,
+                           double *xi, double *eta, const lqcd_solver_params *params, lqcd_solver_stats *stats,
+                           void *stream);
+
+/* The projected factorized propagator on Gamma* (eq. quark_prop_II_proj,
+ * case II) for the 12 point sources at x_src (x_src[0] inside Gamma):
+ *   fact[b](y)[a] = - sum_i eta_i(y)[a] conj(xi_i(x)[b]),  b = 3 s0 + c0,
+ * from factors of lqcd_projected_factors (xi and eta may come from different
+ * gauge fields: the n1^2 pairs of the two-level average).  fact: device
+ * [12][V][4][3]; only the sites of Gamma* are written.  Synchronises.
+ * Errors: LQCD_EBADARG (1 <= n_modes <= 1024), LQCD_ECUDA. */
+int lqcd_projected_propagator(lqcd_lattice *lat, const lqcd_split *split, int n_modes, const double *xi,
+                              const double *eta, const int x_src[4], double *fact, void *stream);
+
+/* Stochastic estimator of the disconnected traces of Sec. 4.1 (eq.
+ * stochastic_estimator) on each slab L_d = doms[d], d < n_doms, of field
+ * `field` (Dirichlet blocks of Sec. 3, or the whole lattice for doms[d] =
+ * 0..T-1), all sources and slabs solved together:
+ *   trace[i][d][x0] = sum_{xvec} eta_i^dag(x) [(kappa D_hop)^8 D_L^{-1} g5 eta_i](x)
+ * for x0 in L_d (0 elsewhere), with kappa D_hop = 1 - 2 kappa D_L on the
+ * slab, g5 = diag(1, 1, -1, -1) in spin.  Its mean over i estimates
+ * sum_{xvec} tr{g5 D_L^{-1}(x,x)}; the eighth power (exact for Wilson
+ * quarks: every closed path shorter than 8 hops has a vanishing g5 trace)
+ * only lowers the noise.  Wilson operator only: the lattice's c_sw must be 0
+ * (else LQCD_EBADARG).
+ * eta: device [n_src][V][4][3] complex128, sources on the whole lattice
+ *   (only each slab's part enters; the caller draws them, e.g. Gaussian).
+ * trace: device [n_src][n_doms][T] complex128, overwritten.
+ * mean: device [n_doms][T] complex128 receiving (1/n_src) sum_i trace[i],
+ *   or NULL.
+ * D_L^{-1} g5 eta_i is solved to params->tol (relative residual); the eight
+ * hops and the contraction run in FP64.  stats: host array of n_doms
+ * entries (each aggregated over the sources), or NULL.  Solutions are not
+ * kept: systems run in waves that fit in free device memory.
+ * Errors: LQCD_EBADARG, LQCD_ENOFIELD, LQCD_ECUDA, LQCD_ENOTCONVERGED. */
+int lqcd_disconnected_trace(lqcd_lattice *lat, int n_doms, const lqcd_slab *doms, int field, int n_src,
+                            const double *eta, double *trace, double *mean, const lqcd_solver_params *params,
+                            lqcd_solver_stats *stats, void *stream);
 
 /* Timing hook of the stencil (no counterpart in the paper: a measurement
  * aid).  Builds the batch of systems (slab doms[k] on field field_ids[k]),

@@ -1102,6 +1102,347 @@ extern "C" int lqcd_link_force(lqcd_lattice* L, const lqcd_slab* dom, int field,
   return w;
 }
 
+// Sec. 4.1 eq. stochastic_estimator: per source i and slab d, solve
+// D_L psi = g5 eta_i, apply (kappa D_hop)^8 on the slab and contract with
+// eta_i per time slice.  Systems are ordered source-major (k = i * n_doms + d).
+extern "C" int lqcd_disconnected_trace(lqcd_lattice* L, int n_doms, const lqcd_slab* doms, int field, int n_src,
+                                       const double* eta, double* trace, double* mean,
+                                       const lqcd_solver_params* params, lqcd_solver_stats* stats, void* stream) {
+  RC(check_lat(L));
+  const int T = L->dims[0];
+  if (n_doms < 1 || n_src < 1 || !doms || !eta || !trace) {
+    lq_set_error("disconnected_trace: bad arguments");
+    return LQCD_EBADARG;
+  }
+  if (L->csw != 0.0) {
+    lq_set_error("disconnected_trace: the (kappa D_hop)^8 estimator needs the Wilson operator (c_sw = 0)");
+    return LQCD_EBADARG;
+  }
+  for (int d = 0; d < n_doms; d++)
+    if (doms[d].t0 < 0 || doms[d].t1 < doms[d].t0 || doms[d].t1 >= T) {
+      lq_set_error("disconnected_trace: slab " + std::to_string(d) + " outside the lattice or empty");
+      return LQCD_EBADARG;
+    }
+  if (field < 0 || field >= (int)L->fields.size()) {
+    lq_set_error("disconnected_trace: field index not loaded");
+    return LQCD_ENOFIELD;
+  }
+  const double t_start = now_s();
+  cudaStream_t st = (cudaStream_t)stream;
+  lqcd_solver_params prm = default_params(params);
+  const long long V = L->V, S3 = L->S3;
+  const long long per_src = (long long)n_doms * T;
+  CK(cudaMemsetAsync(trace, 0, sizeof(double2) * (size_t)(n_src * per_src), st));
+  std::vector<SysSpec> sp;
+  for (int i = 0; i < n_src; i++)
+    for (int d = 0; d < n_doms; d++) sp.push_back(SysSpec{doms[d], field, d, i, make_int4(0, 0, 0, 0)});
+  const double2* eta2 = (const double2*)eta;
+  FillFn fill = [&](BatchStore& B, int k0, double2* be, double2* bo) -> int {
+    std::vector<void*> p(B.b.nsys);
+    for (int q = 0; q < B.b.nsys; q++)
+      p[q] = (void*)(eta2 + (size_t)sp[k0 + q].col * V * 12 + (size_t)sp[k0 + q].dom.t0 * S3 * 12);
+    DBuf d;
+    RC(upload_ptrs(d, p, st));
+    return lq_nat_to_eo_g5(L, B.b, d.as<const double2*>(), be, bo, st);
+  };
+  SinkFn sink = [&](BatchStore& B, int k0, const double2* xe, const double2* xo) -> int {
+    Batch b = B.b;
+    b.active = nullptr;  // every system, converged or not
+    Pool64 h;
+    RC(h.alloc(b, 4, st));
+    // ping-pong (x -> a -> b -> a ...): eight applications of kappa D_hop
+    const double2* ie = xe;
+    const double2* io = xo;
+    for (int n = 0; n < 8; n++) {
+      double2* oe = h.v(n & 1 ? 2 : 0);
+      double2* oo = h.v(n & 1 ? 3 : 1);
+      RC(lq_hop_kappa(L, b, 0, io, oe, st));
+      RC(lq_hop_kappa(L, b, 1, ie, oo, st));
+      ie = oe;
+      io = oo;
+    }
+    std::vector<void*> p(b.nsys);
+    std::vector<int> slot(b.nsys);
+    for (int q = 0; q < b.nsys; q++) {
+      p[q] = (void*)(eta2 + (size_t)sp[k0 + q].col * V * 12);
+      slot[q] = sp[k0 + q].col * n_doms + sp[k0 + q].role;
+    }
+    DBuf d, ds;
+    RC(upload_ptrs(d, p, st));
+    RC(ds.alloc(sizeof(int) * slot.size(), st));
+    CK(cudaMemcpyAsync(ds.p, slot.data(), sizeof(int) * slot.size(), cudaMemcpyHostToDevice, st));
+    return lq_slice_dot(L, b, d.as<const double2*>(), ie, io, ds.as<int>(), (double2*)trace, st);
+  };
+  SolveOut o;
+  RC(solve_waves(L, sp, false, prm, fill, sink, o, st));
+  if (mean) RC(lq_mean_sources((const double2*)trace, n_src, per_src, (double2*)mean, st));
+  CK(cudaStreamSynchronize(st));
+  const double secs = now_s() - t_start;
+  if (stats)
+    for (int d = 0; d < n_doms; d++) {
+      SolveOut od;
+      for (int i = 0; i < n_src; i++) {
+        const int k = i * n_doms + d;
+        od.iters.push_back(o.iters[k]);
+        od.cycles.push_back(o.cycles[k]);
+        od.status.push_back(o.status[k]);
+        od.res.push_back(o.res[k]);
+      }
+      fill_stats(od, 0, n_src, secs, &stats[d]);
+    }
+  int w = worst_status(o);
+  if (w) lq_set_error("disconnected_trace: some solves did not reach the tolerance");
+  return w;
+}
+
+// ------------------------------------------------ quark-line projection
+namespace {
+
+// Gamma = 0..g1, Gamma* = g1+1..T-1, DeltaGamma = g1+1..d1 (d1 < T-1) or empty.
+int check_split(const lqcd_lattice* L, const lqcd_split* split, const char* who) {
+  const int T = L->dims[0];
+  const lqcd_slab G = split->gamma, Gs = split->gamma_star, Dl = split->delta;
+  const bool has_delta = Dl.t1 >= Dl.t0;
+  if (G.t0 != 0 || G.t1 < 0 || Gs.t0 != G.t1 + 1 || Gs.t1 != T - 1 ||
+      (has_delta && (Dl.t0 != G.t1 + 1 || Dl.t1 >= T - 1))) {
+    lq_set_error(std::string(who) + ": need Gamma = 0..g1, Gamma* = g1+1..T-1, DeltaGamma = g1+1..d1 (d1 < T-1)");
+    return LQCD_EBADARG;
+  }
+  return 0;
+}
+
+lqcd_slab gamma_bar_of(const lqcd_split* split) {
+  const bool has_delta = split->delta.t1 >= split->delta.t0;
+  return lqcd_slab{0, has_delta ? split->delta.t1 : split->gamma.t1};
+}
+
+void merge_stats(const SolveOut& o, double secs, lqcd_solver_stats* acc, bool first) {
+  lqcd_solver_stats s;
+  fill_stats(o, 0, (int)o.iters.size(), secs, &s);
+  if (first) {
+    *acc = s;
+    return;
+  }
+  acc->iters = std::max(acc->iters, s.iters);
+  acc->cycles = std::max(acc->cycles, s.cycles);
+  acc->true_residual = std::max(acc->true_residual, s.true_residual);
+  if (acc->status == 0) acc->status = s.status;
+  acc->seconds = secs;
+}
+
+}  // namespace
+
+// Sec. 5: projection vectors on the time slice g1 from n_iter inverse
+// iterations of D_L, L = dom, each followed by an orthonormalisation; then
+// phi = orthonormalise(P_+ V|_{g1}).
+extern "C" int lqcd_boundary_modes(lqcd_lattice* L, const lqcd_slab* dom, int g1, int field, int n_modes, int n_iter,
+                                   const double* v0, double* phi, const lqcd_solver_params* params,
+                                   lqcd_solver_stats* stats, void* stream) {
+  RC(check_lat(L));
+  if (!dom || !v0 || !phi || n_iter < 0 || dom->t0 < 0 || dom->t1 < dom->t0 || dom->t1 >= L->dims[0] ||
+      g1 < dom->t0 || g1 > dom->t1) {
+    lq_set_error("boundary_modes: bad arguments (need a slab inside the lattice containing slice g1)");
+    return LQCD_EBADARG;
+  }
+  if (n_modes < 1 || n_modes > 1024 || (long long)n_modes > 6 * L->S3) {
+    lq_set_error("boundary_modes: need 1 <= n_modes <= min(1024, 6 L1 L2 L3)");
+    return LQCD_EBADARG;
+  }
+  if (field < 0 || field >= (int)L->fields.size()) {
+    lq_set_error("boundary_modes: field index not loaded");
+    return LQCD_ENOFIELD;
+  }
+  const double t_start = now_s();
+  cudaStream_t st = (cudaStream_t)stream;
+  lqcd_solver_params prm = default_params(params);
+  const int N = n_modes;
+  std::vector<lqcd_slab> doms(N, *dom);
+  std::vector<int> fields(N, field);
+  BatchStore A;
+  RC(A.build(L, N, doms.data(), fields.data(), st));
+  const long long n = A.h_sys[0].n;  // sites per parity of one system
+  const long long words = 12 * n;    // one system's block in an even or odd pool
+  Pool64 P;
+  RC(P.alloc(A.b, 4, st));  // V_e, V_o, T_e, T_o
+  double2 *Ve = P.v(0), *Vo = P.v(1), *Te = P.v(2), *To = P.v(3);
+  {
+    const long long len = (long long)(dom->t1 - dom->t0 + 1) * L->S3 * 12;
+    std::vector<void*> p(N);
+    for (int k = 0; k < N; k++) p[k] = (void*)((const double2*)v0 + k * len);
+    DBuf d;
+    RC(upload_ptrs(d, p, st));
+    RC(lq_nat_to_eo(L, A.b, d.as<const double2*>(), Ve, Vo, st));
+  }
+  ColMat V, Tm;
+  V.nseg = Tm.nseg = 2;
+  V.ncol = Tm.ncol = N;
+  V.p[0] = Ve;
+  V.p[1] = Vo;
+  Tm.p[0] = Te;
+  Tm.p[1] = To;
+  for (int s = 0; s < 2; s++) V.ld[s] = V.rows[s] = Tm.ld[s] = Tm.rows[s] = words;
+  std::vector<SysSpec> sp(N);
+  for (int k = 0; k < N; k++) sp[k] = SysSpec{*dom, field, 0, k, make_int4(0, 0, 0, 0)};
+  // a wave's pools hold its systems back to back, as V does: plain copies
+  FillFn fill = [&](BatchStore& B, int k0, double2* be, double2* bo) -> int {
+    const size_t bytes = sizeof(double2) * (size_t)(B.b.nsys * words);
+    CK(cudaMemcpyAsync(be, Ve + k0 * words, bytes, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(bo, Vo + k0 * words, bytes, cudaMemcpyDeviceToDevice, st));
+    return 0;
+  };
+  SinkFn sink = [&](BatchStore& B, int k0, const double2* xe, const double2* xo) -> int {
+    const size_t bytes = sizeof(double2) * (size_t)(B.b.nsys * words);
+    CK(cudaMemcpyAsync(Ve + k0 * words, xe, bytes, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(Vo + k0 * words, xo, bytes, cudaMemcpyDeviceToDevice, st));
+    return 0;
+  };
+  lqcd_solver_stats acc{};
+  int worst = 0;
+  for (int it = 0; it < n_iter; it++) {
+    SolveOut o;
+    RC(solve_waves(L, sp, false, prm, fill, sink, o, st));
+    merge_stats(o, now_s() - t_start, &acc, it == 0);
+    if (!worst) worst = worst_status(o);
+    RC(lq_orthonormalize(V, Tm, st));
+  }
+  RC(lq_slice_plus(L, A.b, g1, Ve, Vo, (double2*)phi, st));
+  ColMat F, Ft;
+  F.nseg = Ft.nseg = 1;
+  F.ncol = Ft.ncol = N;
+  F.p[0] = (double2*)phi;
+  Ft.p[0] = Te;  // T_e and T_o are adjacent: 2 N 12 n = N 12 S3 (t1 - t0 + 1) entries
+  F.ld[0] = F.rows[0] = Ft.ld[0] = Ft.rows[0] = 12 * L->S3;
+  RC(lq_orthonormalize(F, Ft, st));
+  CK(cudaStreamSynchronize(st));
+  if (stats) {
+    *stats = acc;
+    stats->seconds = now_s() - t_start;
+  }
+  if (worst) lq_set_error("boundary_modes: some solves did not reach the tolerance");
+  return worst;
+}
+
+// Sec. 3.3 eq. quark_prop_II_proj: xi_i = D_Gammabar^{-dag} phi_i and
+// eta_i = D_Gamma*^{-1} D_dGamma* phi_i for phi_i on the last slice of Gamma.
+extern "C" int lqcd_projected_factors(lqcd_lattice* L, const lqcd_split* split, int field, int n_modes,
+                                      const double* phi, double* xi, double* eta, const lqcd_solver_params* params,
+                                      lqcd_solver_stats* stats, void* stream) {
+  RC(check_lat(L));
+  if (!split || !phi || !xi || !eta || n_modes < 1) {
+    lq_set_error("projected_factors: bad arguments");
+    return LQCD_EBADARG;
+  }
+  RC(check_split(L, split, "projected_factors"));
+  if (L->bc != LQCD_BC_OPEN) {
+    lq_set_error("projected_factors: needs the open time boundary (the boundary block is one time hop)");
+    return LQCD_EBADARG;
+  }
+  if (field < 0 || field >= (int)L->fields.size()) {
+    lq_set_error("projected_factors: field index not loaded");
+    return LQCD_ENOFIELD;
+  }
+  const double t_start = now_s();
+  cudaStream_t st = (cudaStream_t)stream;
+  lqcd_solver_params prm = default_params(params);
+  const int N = n_modes;
+  const int g1 = split->gamma.t1;
+  const lqcd_slab Gb = gamma_bar_of(split), Gs = split->gamma_star;
+  const long long S3 = L->S3;
+  const long long len_gb = (long long)(Gb.t1 - Gb.t0 + 1) * S3 * 12, len_gs = (long long)(Gs.t1 - Gs.t0 + 1) * S3 * 12;
+  DBuf ids;
+  {
+    std::vector<int> h(N);
+    for (int k = 0; k < N; k++) h[k] = k;
+    RC(ids.alloc(sizeof(int) * N, st));
+    CK(cudaMemcpyAsync(ids.p, h.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+  }
+  const double2* phi2 = (const double2*)phi;
+  // xi: dagger solves on Gammabar from phi on slice g1
+  std::vector<SysSpec> sa(N), sb(N);
+  for (int k = 0; k < N; k++) {
+    sa[k] = SysSpec{Gb, field, 0, k, make_int4(0, 0, 0, 0)};
+    sb[k] = SysSpec{Gs, field, 0, k, make_int4(0, 0, 0, 0)};
+  }
+  FillFn fill_a = [&](BatchStore& B, int k0, double2* be, double2* bo) -> int {
+    return lq_slice_source(L, B.b, ids.as<int>() + k0, g1, phi2, be, bo, st);
+  };
+  SinkFn sink_a = [&](BatchStore& B, int k0, const double2* xe, const double2* xo) -> int {
+    std::vector<void*> p(B.b.nsys);
+    for (int q = 0; q < B.b.nsys; q++) p[q] = (void*)((double2*)xi + (k0 + q) * len_gb);
+    DBuf d;
+    RC(upload_ptrs(d, p, st));
+    return lq_eo_to_nat(L, B.b, xe, xo, d.as<double2* const>(), 1.0, st);
+  };
+  SolveOut oa;
+  RC(solve_waves(L, sa, true, prm, fill_a, sink_a, oa, st));
+  const double t_a = now_s() - t_start;
+  // chi_i = D_dGamma* phi_i (slot 0: the time hop from slice g1 to g1+1)
+  DBuf chi;
+  RC(chi.alloc(sizeof(double2) * (size_t)N * 2 * S3 * 12, st));
+  {
+    std::vector<lqcd_slab> d1(N, lqcd_slab{g1, g1});
+    std::vector<int> f1(N, field);
+    BatchStore P;
+    RC(P.build(L, N, d1.data(), f1.data(), st));
+    Pool64 pv;
+    RC(pv.alloc(P.b, 2, st));
+    RC(lq_slice_source(L, P.b, ids.as<int>(), g1, phi2, pv.v(0), pv.v(1), st));
+    RC(lq_boundary_chi(L, P.b, ids.as<int>(), g1, pv.v(0), pv.v(1), chi.as<double2>(), st));
+  }
+  FillFn fill_b = [&](BatchStore& B, int k0, double2* be, double2* bo) -> int {
+    return lq_chi_to_eo(L, B.b, ids.as<int>() + k0, g1, chi.as<double2>(), be, bo, st);
+  };
+  SinkFn sink_b = [&](BatchStore& B, int k0, const double2* xe, const double2* xo) -> int {
+    std::vector<void*> p(B.b.nsys);
+    for (int q = 0; q < B.b.nsys; q++) p[q] = (void*)((double2*)eta + (k0 + q) * len_gs);
+    DBuf d;
+    RC(upload_ptrs(d, p, st));
+    return lq_eo_to_nat(L, B.b, xe, xo, d.as<double2* const>(), 1.0, st);
+  };
+  SolveOut ob;
+  RC(solve_waves(L, sb, false, prm, fill_b, sink_b, ob, st));
+  CK(cudaStreamSynchronize(st));
+  const double secs = now_s() - t_start;
+  if (stats) {
+    fill_stats(oa, 0, N, t_a, &stats[0]);
+    fill_stats(ob, 0, N, secs, &stats[1]);
+  }
+  int w = worst_status(oa);
+  if (!w) w = worst_status(ob);
+  if (w) lq_set_error("projected_factors: some solves did not reach the tolerance");
+  return w;
+}
+
+// Case II of eq. quark_prop_II_proj on Gamma* for the 12 point sources at x:
+// fact[b][y][a] = -sum_i eta_i(y)[a] conj(xi_i(x)[b]).
+extern "C" int lqcd_projected_propagator(lqcd_lattice* L, const lqcd_split* split, int n_modes, const double* xi,
+                                         const double* eta, const int x_src[4], double* fact, void* stream) {
+  RC(check_lat(L));
+  if (!split || !xi || !eta || !x_src || !fact || n_modes < 1 || n_modes > 1024) {
+    lq_set_error("projected_propagator: bad arguments (1 <= n_modes <= 1024)");
+    return LQCD_EBADARG;
+  }
+  RC(check_split(L, split, "projected_propagator"));
+  if (x_src[0] < split->gamma.t0 || x_src[0] > split->gamma.t1) {
+    lq_set_error("projected_propagator: the source must lie in Gamma");
+    return LQCD_EBADARG;
+  }
+  for (int k = 1; k < 4; k++)
+    if (x_src[k] < 0 || x_src[k] >= L->dims[k]) {
+      lq_set_error("projected_propagator: source outside the lattice");
+      return LQCD_EBADARG;
+    }
+  cudaStream_t st = (cudaStream_t)stream;
+  const lqcd_slab Gb = gamma_bar_of(split), Gs = split->gamma_star;
+  const long long S3 = L->S3;
+  const long long xnat = (((long long)x_src[0] * L->dims[1] + x_src[1]) * L->dims[2] + x_src[2]) * L->dims[3] + x_src[3];
+  RC(lq_proj_prop(L, n_modes, (long long)(Gb.t1 - Gb.t0 + 1) * S3, xnat - (long long)Gb.t0 * S3,
+                  (const double2*)xi, (long long)(Gs.t1 - Gs.t0 + 1) * S3, (long long)Gs.t0 * S3,
+                  (const double2*)eta, (double2*)fact, st));
+  CK(cudaStreamSynchronize(st));
+  return 0;
+}
+
 extern "C" int lqcd_dslash_bench(lqcd_lattice* L, int n_sys, const lqcd_slab* doms, const int* field_ids,
                                  int precision, int reps, double* ms_per_launch, double* bytes_per_launch,
                                  double* flops_per_launch, void* stream) {

@@ -96,6 +96,29 @@ int lq_convert(int Pin, int Pout, const Batch& b, VecP in, VecP out, cudaStream_
 // layout conversion: natural complex128 slab vectors <-> even-odd FP64 pools
 int lq_nat_to_eo(const lqcd_lattice* L, const Batch& b, const double2* const* src, double2* ve, double2* vo,
                  cudaStream_t st);
+int lq_nat_to_eo_g5(const lqcd_lattice* L, const Batch& b, const double2* const* src, double2* ve, double2* vo,
+                    cudaStream_t st);
+int lq_hop_kappa(const lqcd_lattice* L, const Batch& b, int pout, const double2* x, double2* out, cudaStream_t st);
+int lq_slice_dot(const lqcd_lattice* L, const Batch& b, const double2* const* eta, const double2* ye,
+                 const double2* yo, const int* slot, double2* trace, cudaStream_t st);
+int lq_mean_sources(const double2* trace, int n_src, long long per_src, double2* mean, cudaStream_t st);
+// N complex FP64 columns over one or two row segments (e.g. the even and odd
+// halves of a batch of equal systems): column k of segment s starts at
+// p[s] + k * ld[s] and holds rows[s] entries.
+struct ColMat {
+  double2* p[2] = {nullptr, nullptr};
+  long long ld[2] = {0, 0};
+  long long rows[2] = {0, 0};
+  int nseg = 1;
+  int ncol = 0;
+};
+int lq_orthonormalize(ColMat v, ColMat tmp, cudaStream_t st);
+int lq_slice_plus(const lqcd_lattice* L, const Batch& b, int g1, const double2* ve, const double2* vo, double2* phi,
+                  cudaStream_t st);
+int lq_slice_source(const lqcd_lattice* L, const Batch& b, const int* d_ids, int g1, const double2* phi, double2* ve,
+                    double2* vo, cudaStream_t st);
+int lq_proj_prop(const lqcd_lattice* L, int n, long long nsite_gb, long long xloc, const double2* xi, long long nsite_gs,
+                 long long y0, const double2* eta, double2* fact, cudaStream_t st);
 int lq_eo_to_nat(const lqcd_lattice* L, const Batch& b, const double2* ve, const double2* vo, double2* const* dst,
                  double scale, cudaStream_t st);
 // point sources: system k gets the unit vector of column cols[k] at xsrc[k]

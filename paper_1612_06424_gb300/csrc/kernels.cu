@@ -188,6 +188,18 @@ int lq_hop_clinv(int P, bool dag, bool clov, const lqcd_lattice* L, const Batch&
   return launched();
 }
 
+// out_p = kappa D_hop x (the Wilson hopping term on the slab, Dirichlet at
+// its ends), output parity pout, FP64: the clover-free inverse-diagonal
+// kernel with alpha = 1/2, since 1 / diag = 2 kappa.
+int lq_hop_kappa(const lqcd_lattice* L, const Batch& b, int pout, const double2* x, double2* out, cudaStream_t st) {
+  HopArgs a = hop_args(L, b, pout);
+  a.x = x;
+  a.out = out;
+  a.alpha = 0.5;
+  k_hop_clinv<64, false, false, EPI_X><<<grid_of(b), LQ_BLOCK, 0, st>>>(a);
+  return launched();
+}
+
 static VecArgs vec_args(const Batch& b) {
   VecArgs v;
   v.sys = b.sys;
@@ -274,7 +286,9 @@ int lq_convert(int Pin, int Pout, const Batch& b, VecP in, VecP out, cudaStream_
 
 // ------------------------------------------------------------ layout kernels
 // Natural slab vector of system s (src[s], sites t0*S3 .. (t1+1)*S3 - 1)
-// <-> the system's even and odd FP64 vectors.
+// <-> the system's even and odd FP64 vectors.  G5: multiply by gamma_5
+// (spin components 2, 3 negated) on the way in.
+template <bool G5>
 __global__ void __launch_bounds__(128) k_nat_to_eo(Geom g, int nsys, const SysDesc* sys, const int* active,
                                                    const double2* const* src, double2* ve, double2* vo) {
   int s, by;
@@ -291,7 +305,10 @@ __global__ void __launch_bounds__(128) k_nat_to_eo(Geom g, int nsys, const SysDe
   const double2* in = src[s] + loc * 12;
   double2* out = (p == 0 ? ve : vo) + sd.off * 12;
 #pragma unroll
-  for (int k = 0; k < 12; k++) out[k * sd.n + j] = in[k];
+  for (int k = 0; k < 12; k++) {
+    const double2 v = in[k];
+    out[k * sd.n + j] = (G5 && k >= 6) ? make_double2(-v.x, -v.y) : v;
+  }
 }
 
 __global__ void __launch_bounds__(128) k_eo_to_nat(Geom g, int nsys, const SysDesc* sys, const double2* ve,
@@ -317,7 +334,13 @@ __global__ void __launch_bounds__(128) k_eo_to_nat(Geom g, int nsys, const SysDe
 
 int lq_nat_to_eo(const lqcd_lattice* L, const Batch& b, const double2* const* src, double2* ve, double2* vo,
                  cudaStream_t st) {
-  k_nat_to_eo<<<grid_lin(b, b.nby, 2), LQ_BLOCK, 0, st>>>(L->g, b.nsys, b.sys, nullptr, src, ve, vo);
+  k_nat_to_eo<false><<<grid_lin(b, b.nby, 2), LQ_BLOCK, 0, st>>>(L->g, b.nsys, b.sys, nullptr, src, ve, vo);
+  return launched();
+}
+
+int lq_nat_to_eo_g5(const lqcd_lattice* L, const Batch& b, const double2* const* src, double2* ve, double2* vo,
+                    cudaStream_t st) {
+  k_nat_to_eo<true><<<grid_lin(b, b.nby, 2), LQ_BLOCK, 0, st>>>(L->g, b.nsys, b.sys, nullptr, src, ve, vo);
   return launched();
 }
 

@@ -197,6 +197,21 @@ def gaussian_spinor(dims, seed: int, n: int = 1, stream: int = 0) -> np.ndarray:
     return z[..., 0] + 1j * z[..., 1]
 
 
+def gaussian_spinor_device(dims, seed: int, n: int = 1, device="cuda"):
+    """n complex Gaussian spinor fields with the law of gaussian_spinor (Re, Im ~ N(0, 1/2)),
+    drawn by torch's seeded generator on `device` (different draws from the numpy path);
+    complex128 tensor (n, V, 4, 3).  For many sources on large lattices."""
+    import torch
+
+    V = int(np.prod(dims))
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    out = torch.empty((n, V, 4, 3), dtype=torch.complex128, device=device)
+    for i in range(n):
+        out[i] = torch.randn((V, 4, 3), dtype=torch.complex128, device=device, generator=g)
+    return out
+
+
 def slab_sites(dims, t0: int, t1: int) -> slice:
     """Natural-order site range of the time slab t0..t1 (time is slowest)."""
     s3 = int(dims[1] * dims[2] * dims[3])

@@ -21,7 +21,7 @@ BC = {"open": 0, "periodic": 1, "antiperiodic": 2}
 
 ERRORS = {
     -1: "EBADARG", -2: "ENOMEM", -3: "ENONUNITARY", -4: "ENOTCONVERGED",
-    -5: "EBREAKDOWN", -6: "ENAN", -7: "ECUDA", -8: "ENOFIELD",
+    -5: "EBREAKDOWN", -6: "ENAN", -7: "ECUDA", -8: "ENOFIELD", -9: "ERANK",
 }
 
 
@@ -92,6 +92,13 @@ def lib() -> ctypes.CDLL:
     L.lqcd_point_propagators.argtypes = [vp, c, ctypes.POINTER(Slab), ip, ip, ip, vp, ctypes.POINTER(ParamsC),
                                          ctypes.POINTER(StatsC), vp]
     L.lqcd_dslash_bench.argtypes = [vp, c, ctypes.POINTER(Slab), ip, c, c, dp, dp, dp, vp]
+    L.lqcd_boundary_modes.argtypes = [vp, ctypes.POINTER(Slab), c, c, c, c, vp, vp, ctypes.POINTER(ParamsC),
+                                      ctypes.POINTER(StatsC), vp]
+    L.lqcd_projected_factors.argtypes = [vp, ctypes.POINTER(SplitC), c, c, vp, vp, vp, ctypes.POINTER(ParamsC),
+                                         ctypes.POINTER(StatsC), vp]
+    L.lqcd_projected_propagator.argtypes = [vp, ctypes.POINTER(SplitC), c, vp, vp, ip, vp, vp]
+    L.lqcd_disconnected_trace.argtypes = [vp, c, ctypes.POINTER(Slab), c, c, vp, vp, vp, ctypes.POINTER(ParamsC),
+                                          ctypes.POINTER(StatsC), vp]
     L.lqcd_last_error.restype = ctypes.c_char_p
     L.lqcd_kernel_launches.restype = ctypes.c_longlong
     _lib = L
@@ -260,6 +267,70 @@ class Lattice:
                                      ctypes.c_void_p(F.data_ptr()) if F is not None else None, ctypes.byref(S),
                                      ctypes.byref(p), st, _stream(stream)))
         return F, S.value, [s.as_dict() for s in st]
+
+    def disconnected_trace(self, eta: torch.Tensor, doms, field: int = 0, params: SolverParams | None = None,
+                           stream=None):
+        """Sec. 4.1 eq. stochastic_estimator on each slab of `doms` (Wilson operator, c_sw = 0).
+
+        eta: device complex128 [n_src, V, 4, 3] sources.  Returns (trace, mean, stats):
+        trace [n_src, n_doms, T] per source and time slice, mean [n_doms, T] over the
+        sources (both complex128 on eta's device), stats per slab."""
+        n_src = eta.shape[0]
+        n = len(doms)
+        sl = (Slab * n)(*[Slab(*d) for d in doms])
+        T = self.dims[0]
+        tr = torch.empty((n_src, n, T), dtype=torch.complex128, device=eta.device)
+        mean = torch.empty((n, T), dtype=torch.complex128, device=eta.device)
+        st = (StatsC * n)()
+        p = (params or SolverParams()).c()
+        _check(lib().lqcd_disconnected_trace(self._h, n, sl, field, n_src, _dev(eta, "eta"), _dev(tr, "trace"),
+                                             _dev(mean, "mean"), ctypes.byref(p), st, _stream(stream)))
+        return tr, mean, [s.as_dict() for s in st]
+
+    def boundary_modes(self, v0: torch.Tensor, dom, g1: int, field: int = 0, n_iter: int = 10,
+                       params: SolverParams | None = None, stream=None):
+        """Sec. 5 projection vectors: n_iter inverse iterations of D on the slab `dom` from the
+        starting vectors v0 (complex128 [n_modes, slab sites, 4, 3]), each followed by an
+        orthonormalisation; phi = orthonormalised (1 + g0)/2 V on slice g1.
+        Returns (phi [n_modes, L1 L2 L3, 4, 3], stats)."""
+        n = v0.shape[0]
+        phi = torch.empty((n, self.S3, 4, 3), dtype=torch.complex128, device=v0.device)
+        st = StatsC()
+        p = (params or SolverParams()).c()
+        _check(lib().lqcd_boundary_modes(self._h, ctypes.byref(Slab(*dom)), g1, field, n, n_iter, _dev(v0, "v0"),
+                                         _dev(phi, "phi"), ctypes.byref(p), ctypes.byref(st), _stream(stream)))
+        return phi, st.as_dict()
+
+    def _split(self, gamma, gamma_star, delta):
+        d = delta if delta is not None else (gamma[1] + 1, gamma[1])
+        return SplitC(Slab(*gamma), Slab(*d), Slab(*gamma_star))
+
+    def projected_factors(self, phi: torch.Tensor, gamma, gamma_star, delta=None, field: int = 0,
+                          params: SolverParams | None = None, stream=None):
+        """Factors of eq. quark_prop_II_proj for projection vectors phi [N, L1 L2 L3, 4, 3] on the last
+        slice of Gamma: xi = D_Gammabar^{-dag} phi (slab vectors on Gammabar) and
+        eta = D_Gamma*^{-1} D_dGamma* phi (slab vectors on Gamma*).  Returns (xi, eta, stats)."""
+        n = phi.shape[0]
+        gb = (0, delta[1] if delta is not None and delta[1] >= delta[0] else gamma[1])
+        xi = torch.empty((n, self.slab_len(*gb), 4, 3), dtype=torch.complex128, device=phi.device)
+        eta = torch.empty((n, self.slab_len(*gamma_star), 4, 3), dtype=torch.complex128, device=phi.device)
+        st = (StatsC * 2)()
+        p = (params or SolverParams()).c()
+        sp = self._split(gamma, gamma_star, delta)
+        _check(lib().lqcd_projected_factors(self._h, ctypes.byref(sp), field, n, _dev(phi, "phi"), _dev(xi, "xi"),
+                                            _dev(eta, "eta"), ctypes.byref(p), st, _stream(stream)))
+        return xi, eta, {"gamma_bar": st[0].as_dict(), "gamma_star": st[1].as_dict()}
+
+    def projected_propagator(self, xi: torch.Tensor, eta: torch.Tensor, gamma, gamma_star, x_src, delta=None,
+                             out: torch.Tensor | None = None, stream=None):
+        """Case II with the quark line cut (eq. quark_prop_II_proj): fact[b](y) = -sum_i eta_i(y) xi_i(x)^dag[b]
+        on Gamma* for the 12 point sources at x_src; fact [12, V, 4, 3] (zero elsewhere if out is None)."""
+        fact = out if out is not None else torch.zeros((12, self.V, 4, 3), dtype=torch.complex128, device=xi.device)
+        sp = self._split(gamma, gamma_star, delta)
+        _check(lib().lqcd_projected_propagator(self._h, ctypes.byref(sp), xi.shape[0], _dev(xi, "xi"),
+                                               _dev(eta, "eta"), (ctypes.c_int * 4)(*x_src), _dev(fact, "fact"),
+                                               _stream(stream)))
+        return fact
 
 
 class DomainPseudofermionAction(torch.autograd.Function):

@@ -211,3 +211,42 @@ def test_factorized_48x96_sampled_sites():
         r = eta[in_g] - oracle.dirac_at_sites(dims, U, 0.135, 1.0, oracle.BC_OPEN, G, in_g, fg)
         assert np.abs(r).max() <= 1e-10
     lat.close()
+
+
+def test_disconnected_64x24_against_oracle_contraction():
+    """The 64x24^3 Wilson disconnected-trace workload (kappa 0.136), one Gaussian source on
+    Gamma* = t 33..63 and on the full lattice.  A separate solve psi = D_L^{-1} g5 eta
+    (solve_block, residual 1e-12) is checked with the oracle's D; the oracle then applies
+    its own eight hops and contraction (eq. stochastic_estimator) to psi.  Both solves
+    reach 1e-12, so the traces differ by at most cond(D_L) * 2e-12 * |eta_L|^2; with
+    cond(D_L) < 500 the test allows 1e-9 * |eta_L|^2 per slice."""
+    from paper_1612_06424_gb300 import build, lqcd
+
+    build.build()
+    dims = (64, 24, 24, 24)
+    kappa = 0.136
+    U = inputs.random_su3_field(dims, 0.4, 21)
+    lat = lqcd.Lattice(dims, "open")
+    lat.set_gauge(torch.from_numpy(U).cuda(), kappa, 0.0)
+    eta = inputs.gaussian_spinor(dims, 23, 1)
+    doms = [(33, 63), (0, 63)]
+    prm = lqcd.SolverParams(tol=1e-12, precision=32)
+    tr, _, st = lat.disconnected_trace(torch.from_numpy(eta).cuda(), doms, 0, prm)
+    assert all(s["status"] == 0 for s in st), st
+    tr = tr.cpu().numpy()
+    op = oracle.Operator(dims, U, kappa, 0.0)
+    s3 = 24 ** 3
+    g5 = np.array([1.0, 1.0, -1.0, -1.0])[None, :, None]
+    for d, (t0, t1) in enumerate(doms):
+        sl = inputs.slab_sites(dims, t0, t1)
+        b = np.zeros_like(eta[0])
+        b[sl] = g5 * eta[0][sl]
+        x, _ = lat.solve_block(torch.from_numpy(np.ascontiguousarray(b[sl])).cuda(), [(t0, t1)], [0], prm)
+        psi = np.zeros_like(b)
+        psi[sl] = x.cpu().numpy()
+        assert _res(op, b, psi, (t0, t1)) <= 1.05e-12
+        ref = oracle.disconnected_contract(op, eta, psi[None], t0, t1)
+        eta2 = np.sum(np.abs(eta[0][sl]) ** 2)
+        assert np.abs(tr[0, d] - ref).max() <= 1e-9 * eta2, d
+        assert np.abs(ref[t0:t1 + 1]).min() > 0
+    lat.close()
