@@ -361,3 +361,43 @@ def projected_propagator(op: Operator, split: Split, xi: np.ndarray, eta: np.nda
     out = -np.einsum("iya,ib->bya", E, np.conj(Xx))
     out[:, ~m] = 0
     return out.reshape(12, op.V, 4, 3)
+
+
+# --------------------------------------------------------------------------
+# Nucleon blocks on projected quark lines (Sec. 3.3 eq. nucleon_prop_factorized)
+
+def charge_conjugation() -> np.ndarray:
+    """C = gamma_0 gamma_2 (real, antisymmetric, unitary, C gamma_mu C^{-1} = -gamma_mu^T in this basis)."""
+    return gamma(0) @ gamma(2)
+
+
+EPS3 = np.zeros((3, 3, 3))
+EPS3[0, 1, 2] = EPS3[1, 2, 0] = EPS3[2, 0, 1] = 1.0
+EPS3[0, 2, 1] = EPS3[2, 1, 0] = EPS3[1, 0, 2] = -1.0
+
+
+def nucleon_block(op: Operator, s: np.ndarray, t: int) -> np.ndarray:
+    """B[i, j, k, alpha] = sum over the sites x of time slice t of
+        eps^{abc} {[s_i^T]^a(x) C gamma_5 [s_j]^b(x)} [s_k]^c_alpha(x)
+    (the colourless spinor of eq. nucleon_prop_factorized), for the N fields s (N, V, 4, 3)."""
+    s3 = op.V // op.T
+    cg5 = charge_conjugation() @ gamma(4)
+    f = s[:, t * s3:(t + 1) * s3]                                     # (N, S3, 4, 3)
+    diq = np.einsum("abc,ixma,mn,jxnb->ijxc", EPS3, f, cg5, f)        # (N, N, S3, 3)
+    return np.einsum("ijxc,kxdc->ijkd", diq, f)
+
+
+def nucleon_factorized(op: Operator, xi: np.ndarray, eta: np.ndarray, x0: int, y0: int):
+    """W1, W2 of eq. nucleon_prop_factorized summed over the sites of slices x0 (source, in Gammabar)
+    and y0 (sink, in Gamma*):
+        W1 = -sum_ijk B_xi[j, i, k](x0)^T g5 P_- B_eta[i, j, k](y0),
+        W2 = -sum_ijk B_xi[k, i, j](x0)^T g5 P_- B_eta[i, j, k](y0),
+    with the paper's row factor xi_i^T(x) = [phi_i^dag D_Gammabar^{-1}](x) = conj(xi_i(x)) (xi as
+    returned by projected_factors), P_- = (1 - gamma_0)/2.  Returns (W1, W2); the factorized
+    nucleon correlator is C_N^(f)(y0, x0) = (W1 - W2) / L^3."""
+    g5pm = gamma(4) @ (0.5 * (np.eye(4) - gamma(0)))
+    bx = nucleon_block(op, np.conj(xi), x0)
+    be = nucleon_block(op, eta, y0)
+    w1 = -np.einsum("jikg,gd,ijkd->", bx, g5pm, be)
+    w2 = -np.einsum("kijg,gd,ijkd->", bx, g5pm, be)
+    return w1, w2

@@ -1,0 +1,76 @@
+"""Pins of the oracle's factorized nucleon contraction (Sec. 3.3 eq. nucleon_prop_factorized).
+
+- C = gamma_0 gamma_2 is a charge-conjugation matrix of this basis: C gamma_mu C^{-1} = -gamma_mu^T;
+- the block B is the eps/C-gamma_5 contraction written out site by site and index by index in plain
+  loops on a tiny case;
+- the factorized W1, W2 equal the propagator form of the two nucleon Wick contractions evaluated with
+  the projected propagator S(y,x)[a,b] = -sum_i eta_i(y)[a] xi_i^T(x)[b] for every pair (x, y) of
+  the two slices (substituting S into the contraction gives the block form, so any index slip in the
+  blocks breaks the equality):
+    W1 = sum eps^{abc} eps^{a'b'c'} (Cg5)_{mu nu} (Cg5)_{mu' nu'} (g5 P_-)_{gam del}
+             S^{a b'}_{mu nu'} S^{b a'}_{nu mu'} S^{c c'}_{del gam}
+    W2 = same with S^{a b'}_{mu nu'} S^{b c'}_{nu gam} S^{c a'}_{del mu'}.
+"""
+import itertools
+
+import numpy as np
+
+import oracle
+from paper_1612_06424_gb300 import inputs
+
+DIMS = (4, 2, 2, 2)
+S3 = 8
+
+
+def _op():
+    U = inputs.random_su3_field(DIMS, 0.3, 41)
+    return oracle.Operator(DIMS, U, 0.12, 0.0)
+
+
+def test_charge_conjugation():
+    C = oracle.charge_conjugation()
+    for mu in range(4):
+        g = oracle.gamma(mu)
+        assert np.abs(C @ g @ np.linalg.inv(C) + g.T).max() < 1e-14
+    assert np.abs(C.conj().T @ C - np.eye(4)).max() < 1e-14
+
+
+def test_block_matches_explicit_loops():
+    op = _op()
+    rng = np.random.default_rng(3)
+    n = 3
+    s = rng.standard_normal((n, 32, 4, 3)) + 1j * rng.standard_normal((n, 32, 4, 3))
+    B = oracle.nucleon_block(op, s, 2)
+    cg5 = oracle.charge_conjugation() @ oracle.gamma(4)
+    want = np.zeros((n, n, n, 4), complex)
+    for i, j, k in itertools.product(range(n), repeat=3):
+        for x in range(2 * S3, 3 * S3):
+            for a, b, c in itertools.permutations(range(3)):
+                e = oracle.EPS3[a, b, c]
+                d = sum(s[i, x, m, a] * cg5[m, q] * s[j, x, q, b] for m in range(4) for q in range(4))
+                want[i, j, k] += e * d * s[k, x, :, c]
+    assert np.abs(B - want).max() < 1e-12 * np.abs(want).max()
+
+
+def test_factorized_equals_propagator_form():
+    op = _op()
+    rng = np.random.default_rng(5)
+    n = 4
+    xi = rng.standard_normal((n, 32, 4, 3)) + 1j * rng.standard_normal((n, 32, 4, 3))
+    eta = rng.standard_normal((n, 32, 4, 3)) + 1j * rng.standard_normal((n, 32, 4, 3))
+    x0, y0 = 1, 3
+    w1, w2 = oracle.nucleon_factorized(op, xi, eta, x0, y0)
+    C = oracle.charge_conjugation()
+    cg5 = C @ oracle.gamma(4)
+    g5pm = oracle.gamma(4) @ (0.5 * (np.eye(4) - oracle.gamma(0)))
+    E = oracle.EPS3
+    r1 = r2 = 0.0
+    for x in range(x0 * S3, (x0 + 1) * S3):
+        for y in range(y0 * S3, (y0 + 1) * S3):
+            # S[mu, a, nu, b] = -sum_i eta_i(y)[mu, a] conj(xi_i(x))[nu, b]
+            S = -np.einsum("ima,inb->manb", eta[:, y], np.conj(xi[:, x]))
+            r1 += np.einsum("abc,ABC,mn,MN,gd,maNB,nbMA,dcgC->", E, E, cg5, cg5, g5pm, S, S, S)
+            r2 += np.einsum("abc,ABC,mn,MN,gd,maNB,nbgC,dcMA->", E, E, cg5, cg5, g5pm, S, S, S)
+    assert abs(w1 - r1) < 1e-11 * abs(r1) and abs(r1) > 1e-6
+    assert abs(w2 - r2) < 1e-11 * abs(r2) and abs(r2) > 1e-6
+    assert abs(w1 - w2) > 1e-6 * abs(w1)        # the two contractions differ
