@@ -231,6 +231,40 @@ int lqcd_projected_factors(lqcd_lattice *lat, const lqcd_split *split, int field
 int lqcd_projected_propagator(lqcd_lattice *lat, const lqcd_split *split, int n_modes, const double *xi,
                               const double *eta, const int x_src[4], double *fact, void *stream);
 
+/* Nucleon blocks of the factorized nucleon propagator (Sec. 3.3 eq.
+ * nucleon_prop_factorized) for n fields s_i (device [n] slab vectors on
+ * `slab`, complex128; conj = 1 uses conj(s_i), e.g. the xi of
+ * lqcd_projected_factors, whose conjugate is the paper's row xi_i^T), for the
+ * time slices t0 .. t0+n_t-1 (inside the slab):
+ *   B[t][i][j][k][alpha] = sum_{xvec} eps^{abc} {[s_i^T]^a(x) C g5 [s_j]^b(x)} [s_k]^c_alpha(x)
+ * with C = g0 g2 (C g_mu C^{-1} = -g_mu^T in the basis above).  B: device
+ * [n_t][n][n][n][4] complex128, overwritten.  Arithmetic: the diquark and the
+ * (x, c) contraction in FP32 (inputs rounded from FP64), summed in two
+ * levels (partial sums over 64 sites, then their running sum; relative error
+ * about (200 + L1 L2 L3 / 64) 2^-24 of the sum of |terms|), stored as FP64.
+ * 1 <= n <= 1024.  Stream-ordered, no
+ * synchronisation.  Errors: LQCD_EBADARG, LQCD_ECUDA. */
+int lqcd_nucleon_blocks(lqcd_lattice *lat, const lqcd_slab *slab, int n, const double *s, int conj, int t0, int n_t,
+                        double *B, void *stream);
+
+/* The two factorized Wick contractions for every pair (source slice ix of
+ * B_xi, sink slice iy of B_eta) (eq. nucleon_prop_factorized):
+ *   W[ix][iy][0] = W1 = -sum_ijk B_xi[ix][j][i][k]^T g5 P_- B_eta[iy][i][j][k]
+ *   W[ix][iy][1] = W2 = -sum_ijk B_xi[ix][k][i][j]^T g5 P_- B_eta[iy][i][j][k]
+ * with P_- = (1 - g0)/2, in FP64; C_N^(f)(y0, x0) = (W1 - W2) / (L1 L2 L3).
+ * B_xi: device [n_x][n][n][n][4], B_eta: device [n_y][n][n][n][4] complex128
+ * (level-1 averages of blocks may be passed for the two-level estimator);
+ * W: device [n_x][n_y][2] complex128.  Errors: LQCD_EBADARG, LQCD_ECUDA. */
+int lqcd_nucleon_contract(int n, int n_x, const double *B_xi, int n_y, const double *B_eta, double *W, void *stream);
+
+/* Level-1 average of the two-level estimator (Sec. 2.2 eq.
+ * multilevel_estimator): out[e] = (1/count) sum_{j<count} in[j*size + e] for
+ * count arrays of `size` complex128 entries stored back to back (device), in
+ * FP64 and in j order.  Averaging the blocks (or factors) of each region over
+ * its n1 level-1 fields before contracting gives the product of the two
+ * level-1 averages.  Errors: LQCD_EBADARG, LQCD_ECUDA. */
+int lqcd_level_mean(long long size, int count, const double *in, double *out, void *stream);
+
 /* Stochastic estimator of the disconnected traces of Sec. 4.1 (eq.
  * stochastic_estimator) on each slab L_d = doms[d], d < n_doms, of field
  * `field` (Dirichlet blocks of Sec. 3, or the whole lattice for doms[d] =

@@ -401,3 +401,19 @@ def nucleon_factorized(op: Operator, xi: np.ndarray, eta: np.ndarray, x0: int, y
     w1 = -np.einsum("jikg,gd,ijkd->", bx, g5pm, be)
     w2 = -np.einsum("kijg,gd,ijkd->", bx, g5pm, be)
     return w1, w2
+
+
+def multilevel_estimator(o_gamma, o_gamma_star, o_corr, product=np.multiply):
+    """Eq. multilevel_estimator (Sec. 2.2): for level-0 fields i and their level-1 fields j, k, l,
+        (1/n0) sum_i { [(1/n1) sum_j O_Gamma[i,j]] . [(1/n1) sum_k O_Gamma*[i,k]] + (1/n1) sum_l O_corr[i,l] },
+    with `.` the product that joins the two regions' factors (elementwise for scalars; a
+    contraction for tensors).  Inputs indexed [i][j] (lists or arrays)."""
+    n0 = len(o_gamma)
+    total = None
+    for i in range(n0):
+        g = sum(o_gamma[i]) / len(o_gamma[i])
+        gs = sum(o_gamma_star[i]) / len(o_gamma_star[i])
+        c = sum(o_corr[i]) / len(o_corr[i])
+        term = product(g, gs) + c
+        total = term if total is None else total + term
+    return total / n0

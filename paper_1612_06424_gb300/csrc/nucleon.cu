@@ -1,0 +1,274 @@
+// Nucleon blocks on projected quark lines (Sec. 3.3 eq. nucleon_prop_factorized):
+//   B[i][j][k][alpha](t) = sum_{x in slice t} eps^{abc} {[s_i^T]^a(x) C g5 [s_j]^b(x)} [s_k]^c_alpha(x)
+// as a contraction over (x, c) of the diquark D[(i,j)][(x,c)] with
+// S[(x,c)][(k,alpha)] = s_k(x)[alpha][c]: a dense O(N^3 L^3) product, run on
+// the FP32 pipes (the GB300's FP64 rate is 1/62 of FP32): per-thread FP32
+// partial sums over 64 sites are added into FP32 running sums (two-level
+// summation); the diquark tiles are generated in shared memory and never stored.  Then the two Wick contractions
+//   W1 = -sum_ijk B_xi[j,i,k]^T g5 P_- B_eta[i,j,k],  W2 = -sum_ijk B_xi[k,i,j]^T g5 P_- B_eta[i,j,k].
+#include "internal.h"
+
+using namespace lq;
+
+namespace {
+
+constexpr int TI = 8, TJ = 8;  // (i, j) pair tile: 64 rows
+constexpr int TK = 16;         // k tile: 64 (k, alpha) columns
+constexpr int XS = 8;          // sites per shared-memory stage
+constexpr int FLUSH = 8;       // stages per first-level partial sum (64 sites)
+constexpr int TOT_BYTES = 16 * 256 * 8;  // dynamic shared memory of the second-level sums
+
+int launched_here() {
+  lq_count_launch();
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    lq_set_error(std::string("kernel launch: ") + cudaGetErrorString(e));
+    return LQCD_ECUDA;
+  }
+  return 0;
+}
+
+// C g5 with C = g0 g2 in the chiral basis of lqcd.h (g0 = [[0,-1],[-1,0]],
+// g2 = [[0,-i s2],[i s2,0]], g5 = diag(1,1,-1,-1)): its non-zero entries are
+// (0,1) = -1, (1,0) = +1, (2,3) = -1, (3,2) = +1, so
+// s^T C g5 t = -s0 t1 + s1 t0 - s2 t3 + s3 t2   (spin indices).
+LQ_DI float2 cg5_pair(const float2* si, const float2* tj, int a, int b) {
+  // si, tj: 12 complex [spin*3 + colour]; colour a of s, colour b of t
+  float2 r = make_float2(0.f, 0.f);
+  const int sp[4][2] = {{0, 1}, {1, 0}, {2, 3}, {3, 2}};
+  const float sg[4] = {-1.f, 1.f, -1.f, 1.f};
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    const float2 u = si[sp[q][0] * 3 + a], v = tj[sp[q][1] * 3 + b];
+    r.x += sg[q] * (u.x * v.x - u.y * v.y);
+    r.y += sg[q] * (u.x * v.y + u.y * v.x);
+  }
+  return r;
+}
+
+// One block: a 64 x 64 tile of B[(i,j)][(k,alpha)] of one time slice.
+// s: n slab vectors (FP64, [n][nsite][12]); slice blockIdx.z covers the
+// slab-local sites lo0 + z * t_stride_sites .. + S3.
+__global__ void __launch_bounds__(256, 2) k_nucleon_block(int n, long long nsite, const double2* s, int conj,
+                                                       int S3, long long lo0, int t_stride_sites, double2* B) {
+  __shared__ float2 fi[XS][TI][12], fj[XS][TJ][12];
+  __shared__ float2 Ds[XS * 3][TI * TJ + 1], Ss[XS * 3][TK * 4 + 1];
+  extern __shared__ float2 tot[];  // [16][256]: second-level sums of each thread's 4 x 4 tile
+  const int nti = (n + TI - 1) / TI, ntj = (n + TJ - 1) / TJ;
+  const int tile = blockIdx.x;
+  const int i0 = (tile % nti) * TI, j0 = ((tile / nti) % ntj) * TJ;
+  const int k0 = blockIdx.y * TK;
+  const int t = blockIdx.z;
+  const long long lo = lo0 + (long long)t * t_stride_sites;
+  const int tr = threadIdx.x / 16, tc = threadIdx.x % 16;  // rows tr*4.., cols tc*4..
+  float2 acc[4][4];
+#pragma unroll
+  for (int p = 0; p < 4; p++)
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      acc[p][q] = make_float2(0.f, 0.f);
+      tot[(p * 4 + q) * 256 + threadIdx.x] = make_float2(0.f, 0.f);
+    }
+  const float cs = conj ? -1.f : 1.f;
+  int stage = 0;
+  for (int x0 = 0; x0 < S3; x0 += XS, stage++) {
+    // the i and j fields of the stage's sites, FP64 -> FP32 (conjugated for the xi side)
+    for (int e = threadIdx.x; e < XS * (TI + TJ) * 12; e += blockDim.x) {
+      const int comp = e % 12, r = e / 12;
+      const int x = r % XS, w = r / XS;  // w: 0..TI+TJ-1
+      const int f = w < TI ? i0 + w : j0 + w - TI;
+      float2 v = make_float2(0.f, 0.f);
+      if (f < n && x0 + x < S3) {
+        const double2 d = s[((long long)f * nsite + lo + x0 + x) * 12 + comp];
+        v = make_float2((float)d.x, cs * (float)d.y);
+      }
+      if (w < TI) fi[x][w][comp] = v;
+      else fj[x][w - TI][comp] = v;
+    }
+    // S[(x, c)][(k, alpha)] = s_k(x)[alpha][c]; consecutive threads read one site's 12 components
+    for (int e = threadIdx.x; e < XS * TK * 12; e += blockDim.x) {
+      const int comp = e % 12, r = e / 12;
+      const int x = r % XS, kk = r / XS;
+      const int al = comp / 3, c = comp % 3;
+      const int k = k0 + kk;
+      float2 v = make_float2(0.f, 0.f);
+      if (k < n && x0 + x < S3) {
+        const double2 d = s[((long long)k * nsite + lo + x0 + x) * 12 + comp];
+        v = make_float2((float)d.x, cs * (float)d.y);
+      }
+      Ss[x * 3 + c][kk * 4 + al] = v;
+    }
+    __syncthreads();
+    // diquark D[(x, c)][(i, j)]
+    for (int e = threadIdx.x; e < XS * 3 * TI * TJ; e += blockDim.x) {
+      const int pr = e % (TI * TJ), xc = e / (TI * TJ);
+      const int x = xc / 3, c = xc % 3;
+      const int ii = pr / TJ, jj = pr % TJ;
+      const int a = (c + 1) % 3, b = (c + 2) % 3;  // eps^{abc} = +1 for (a, b) and -1 for (b, a)
+      const float2 p = cg5_pair(fi[x][ii], fj[x][jj], a, b), m = cg5_pair(fi[x][ii], fj[x][jj], b, a);
+      Ds[xc][pr] = make_float2(p.x - m.x, p.y - m.y);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int r = 0; r < XS * 3; r++) {
+      float2 av[4], bv[4];
+#pragma unroll
+      for (int p = 0; p < 4; p++) {
+        av[p] = Ds[r][tr * 4 + p];
+        bv[p] = Ss[r][tc * 4 + p];
+      }
+#pragma unroll
+      for (int p = 0; p < 4; p++)
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          acc[p][q].x = fmaf(av[p].x, bv[q].x, fmaf(-av[p].y, bv[q].y, acc[p][q].x));
+          acc[p][q].y = fmaf(av[p].x, bv[q].y, fmaf(av[p].y, bv[q].x, acc[p][q].y));
+        }
+    }
+    __syncthreads();
+    if ((stage + 1) % FLUSH == 0) {
+#pragma unroll
+      for (int p = 0; p < 4; p++)
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          float2& t2 = tot[(p * 4 + q) * 256 + threadIdx.x];
+          t2.x += acc[p][q].x;
+          t2.y += acc[p][q].y;
+          acc[p][q] = make_float2(0.f, 0.f);
+        }
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < 4; p++) {
+    const int pr = tr * 4 + p;
+    const int i = i0 + pr / TJ, j = j0 + pr % TJ;
+    if (i >= n || j >= n) continue;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int col = tc * 4 + q;
+      const int k = k0 + col / 4, al = col % 4;
+      if (k >= n) continue;
+      const float2 t2 = tot[(p * 4 + q) * 256 + threadIdx.x];
+      const double2 v = make_double2((double)t2.x + acc[p][q].x, (double)t2.y + acc[p][q].y);
+      B[((((long long)t * n + i) * n + j) * n + k) * 4 + al] = v;
+    }
+  }
+}
+
+// W[ix][iy] = (W1, W2) for slices ix of B_xi and iy of B_eta; one block per
+// (ix, iy), FP64.  g5 P_- = g5 (1 - g0)/2 in the chiral basis: rows
+// (1/2)[[1,0,1,0],[0,1,0,1],[1,0,1,0],[0,1,0,1]] times diag(1,1,-1,-1) on the
+// left: M = (1/2)[[1,0,1,0],[0,1,0,1],[-1,0,-1,0],[0,-1,0,-1]].
+__global__ void __launch_bounds__(256) k_nucleon_contract(int n, int ny, const double2* Bx, const double2* By,
+                                                          double2* W) {
+  const int ix = blockIdx.x / ny, iy = blockIdx.x % ny;
+  const long long n3 = (long long)n * n * n;
+  const double2* bx = Bx + (long long)ix * n3 * 4;
+  const double2* by = By + (long long)iy * n3 * 4;
+  const double M[4][4] = {{0.5, 0, 0.5, 0}, {0, 0.5, 0, 0.5}, {-0.5, 0, -0.5, 0}, {0, -0.5, 0, -0.5}};
+  double w1r = 0, w1i = 0, w2r = 0, w2i = 0;
+  for (long long e = threadIdx.x; e < n3; e += blockDim.x) {
+    const int k = (int)(e % n), j = (int)((e / n) % n), i = (int)(e / ((long long)n * n));
+    const double2* yv = by + e * 4;                                      // B_eta[i][j][k]
+    const double2* x1 = bx + ((((long long)j * n + i) * n) + k) * 4;   // B_xi[j][i][k]
+    const double2* x2 = bx + ((((long long)k * n + i) * n) + j) * 4;   // B_xi[k][i][j]
+    double2 my[4];
+#pragma unroll
+    for (int g = 0; g < 4; g++) {
+      double re = 0, im = 0;
+#pragma unroll
+      for (int d = 0; d < 4; d++) {
+        re += M[g][d] * yv[d].x;
+        im += M[g][d] * yv[d].y;
+      }
+      my[g] = make_double2(re, im);
+    }
+#pragma unroll
+    for (int g = 0; g < 4; g++) {
+      const double2 a = x1[g], b = x2[g];
+      w1r += a.x * my[g].x - a.y * my[g].y;
+      w1i += a.x * my[g].y + a.y * my[g].x;
+      w2r += b.x * my[g].x - b.y * my[g].y;
+      w2i += b.x * my[g].y + b.y * my[g].x;
+    }
+  }
+  __shared__ double sh[4][8];
+  double v[4] = {w1r, w1i, w2r, w2i};
+#pragma unroll
+  for (int q = 0; q < 4; q++)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int q = 0; q < 4; q++) sh[q][threadIdx.x >> 5] = v[q];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r[4] = {0, 0, 0, 0};
+    for (int q = 0; q < 4; q++)
+      for (int w = 0; w < 8; w++) r[q] += sh[q][w];
+    W[(long long)blockIdx.x * 2] = make_double2(-r[0], -r[1]);
+    W[(long long)blockIdx.x * 2 + 1] = make_double2(-r[2], -r[3]);
+  }
+}
+
+// out[e] = (1/count) sum_j in[j * size + e], summed in j order (FP64).
+__global__ void k_level_mean(long long size, int count, const double2* in, double2* out) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < size;
+       e += (long long)gridDim.x * blockDim.x) {
+    double re = 0.0, im = 0.0;
+    for (int j = 0; j < count; j++) {
+      const double2 v = in[(long long)j * size + e];
+      re += v.x;
+      im += v.y;
+    }
+    out[e] = make_double2(re / count, im / count);
+  }
+}
+
+}  // namespace
+
+extern "C" int lqcd_level_mean(long long size, int count, const double* in, double* out, void* stream) {
+  if (!in || !out || size < 1 || count < 1) {
+    lq_set_error("level_mean: bad arguments");
+    return LQCD_EBADARG;
+  }
+  long long blocks = (size + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  k_level_mean<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(size, count, (const double2*)in, (double2*)out);
+  return launched_here();
+}
+
+extern "C" int lqcd_nucleon_blocks(lqcd_lattice* L, const lqcd_slab* slab, int n, const double* s, int conj, int t0,
+                                   int n_t, double* B, void* stream) {
+  if (!L || !slab || !s || !B || n < 1 || n > 1024 || n_t < 1 || slab->t0 < 0 || slab->t1 < slab->t0 ||
+      slab->t1 >= L->dims[0] || t0 < slab->t0 || t0 + n_t - 1 > slab->t1) {
+    lq_set_error("nucleon_blocks: bad arguments (1 <= n <= 1024, slices t0..t0+n_t-1 inside the slab)");
+    return LQCD_EBADARG;
+  }
+  const int S3 = (int)L->S3;
+  const long long nsite = (long long)(slab->t1 - slab->t0 + 1) * S3;
+  const int nti = (n + TI - 1) / TI, ntj = (n + TJ - 1) / TJ, ntk = (n + TK - 1) / TK;
+  static bool attr = false;  // static + dynamic shared memory exceed the 48 KB default
+  if (!attr) {
+    if (cudaFuncSetAttribute(k_nucleon_block, cudaFuncAttributeMaxDynamicSharedMemorySize, TOT_BYTES) != cudaSuccess) {
+      cudaGetLastError();
+      lq_set_error("nucleon_blocks: shared-memory opt-in failed");
+      return LQCD_ECUDA;
+    }
+    attr = true;
+  }
+  k_nucleon_block<<<dim3((unsigned)(nti * ntj), (unsigned)ntk, (unsigned)n_t), 256, TOT_BYTES, (cudaStream_t)stream>>>(
+      n, nsite, (const double2*)s, conj, S3, (long long)(t0 - slab->t0) * S3, S3, (double2*)B);
+  return launched_here();
+}
+
+extern "C" int lqcd_nucleon_contract(int n, int n_x, const double* B_xi, int n_y, const double* B_eta, double* W,
+                                     void* stream) {
+  if (!B_xi || !B_eta || !W || n < 1 || n > 1024 || n_x < 1 || n_y < 1 || (long long)n_x * n_y >= (1LL << 31)) {
+    lq_set_error("nucleon_contract: bad arguments");
+    return LQCD_EBADARG;
+  }
+  k_nucleon_contract<<<(unsigned)(n_x * n_y), 256, 0, (cudaStream_t)stream>>>(n, n_y, (const double2*)B_xi,
+                                                                              (const double2*)B_eta, (double2*)W);
+  return launched_here();
+}

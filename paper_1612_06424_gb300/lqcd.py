@@ -97,6 +97,9 @@ def lib() -> ctypes.CDLL:
     L.lqcd_projected_factors.argtypes = [vp, ctypes.POINTER(SplitC), c, c, vp, vp, vp, ctypes.POINTER(ParamsC),
                                          ctypes.POINTER(StatsC), vp]
     L.lqcd_projected_propagator.argtypes = [vp, ctypes.POINTER(SplitC), c, vp, vp, ip, vp, vp]
+    L.lqcd_nucleon_blocks.argtypes = [vp, ctypes.POINTER(Slab), c, vp, c, c, c, vp, vp]
+    L.lqcd_nucleon_contract.argtypes = [c, c, vp, c, vp, vp, vp]
+    L.lqcd_level_mean.argtypes = [ctypes.c_longlong, c, vp, vp, vp]
     L.lqcd_disconnected_trace.argtypes = [vp, c, ctypes.POINTER(Slab), c, c, vp, vp, vp, ctypes.POINTER(ParamsC),
                                           ctypes.POINTER(StatsC), vp]
     L.lqcd_last_error.restype = ctypes.c_char_p
@@ -331,6 +334,42 @@ class Lattice:
                                                _dev(eta, "eta"), (ctypes.c_int * 4)(*x_src), _dev(fact, "fact"),
                                                _stream(stream)))
         return fact
+
+    def nucleon_blocks(self, s: torch.Tensor, slab, t0: int, n_t: int = 1, conj: bool = False, stream=None):
+        """Blocks B[t][i][j][k][alpha] of eq. nucleon_prop_factorized for the fields s (complex128
+        [n, slab sites, 4, 3] on `slab`; conj=True for the xi factors), slices t0 .. t0+n_t-1."""
+        n = s.shape[0]
+        B = torch.empty((n_t, n, n, n, 4), dtype=torch.complex128, device=s.device)
+        _check(lib().lqcd_nucleon_blocks(self._h, ctypes.byref(Slab(*slab)), n, _dev(s, "s"), int(bool(conj)), t0,
+                                         n_t, _dev(B, "B"), _stream(stream)))
+        return B
+
+
+def nucleon_contract(B_xi: torch.Tensor, B_eta: torch.Tensor, stream=None) -> torch.Tensor:
+    """W[ix][iy] = (W1, W2) of eq. nucleon_prop_factorized for blocks B_xi [n_x, n, n, n, 4] (source
+    slices) and B_eta [n_y, n, n, n, 4] (sink slices); complex128 [n_x, n_y, 2]."""
+    nx, n = B_xi.shape[0], B_xi.shape[1]
+    ny = B_eta.shape[0]
+    W = torch.empty((nx, ny, 2), dtype=torch.complex128, device=B_xi.device)
+    _check(lib().lqcd_nucleon_contract(n, nx, _dev(B_xi, "B_xi"), ny, _dev(B_eta, "B_eta"), _dev(W, "W"),
+                                       _stream(stream)))
+    return W
+
+
+def level_mean(t: torch.Tensor, stream=None) -> torch.Tensor:
+    """Mean over the leading (level-1) axis of a complex128 CUDA tensor, in the library's kernel."""
+    n1 = t.shape[0]
+    out = torch.empty(t.shape[1:], dtype=torch.complex128, device=t.device)
+    _check(lib().lqcd_level_mean(out.numel(), n1, _dev(t, "in"), _dev(out, "out"), _stream(stream)))
+    return out
+
+
+def multilevel_nucleon(B_xi_levels: torch.Tensor, B_eta_levels: torch.Tensor, stream=None) -> torch.Tensor:
+    """Level-1 part of eq. multilevel_estimator for the factorized nucleon (Sec. 2.2, Sec. 3.3): the
+    blocks of each region averaged over their n1 level-1 fields (B_xi_levels [n1, n_x, n, n, n, 4],
+    B_eta_levels [n1, n_y, n, n, n, 4]), then contracted: W [n_x, n_y, 2] (W1, W2).  The contraction
+    is bilinear, so this equals the mean of the n1^2 contractions of level-1 pairs."""
+    return nucleon_contract(level_mean(B_xi_levels, stream), level_mean(B_eta_levels, stream), stream)
 
 
 class DomainPseudofermionAction(torch.autograd.Function):

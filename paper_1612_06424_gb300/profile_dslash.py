@@ -8,7 +8,10 @@ Prints ms per launch, algorithmic GB/s and TFLOP/s.  Each launch is one
 k_hop_lin (out_o = A_oo y_o - 1/4 D_hop x_e) over every system of the batch.
 With --factorized it instead runs one 12-source factorized propagator with
 correction on the 16^3x32 workload (Gamma 0..13, DeltaGamma 14..17, Gamma*
-14..31, source (2,0,0,0)), i.e. every kernel of the solver.
+14..31, source (2,0,0,0)), i.e. every kernel of the solver.  With
+--nucleon N it runs the nucleon-block kernel for N random fields on
+--nucleon-slices time slices of the lattice (e.g. --dims 64 24 24 24
+--nucleon 120 --nucleon-slices 1) `--reps` times.
 """
 import argparse
 import os
@@ -29,6 +32,8 @@ def main():
     ap.add_argument("--kappa", type=float, default=0.13)
     ap.add_argument("--csw", type=float, default=1.0)
     ap.add_argument("--factorized", action="store_true")
+    ap.add_argument("--nucleon", type=int, default=0)
+    ap.add_argument("--nucleon-slices", type=int, default=1)
     a = ap.parse_args()
     from paper_1612_06424_gb300 import build, inputs, lqcd
 
@@ -38,6 +43,29 @@ def main():
         rng, n = s.split("x")
         t0, t1 = (int(v) for v in rng.split(":"))
         doms += [(t0, t1)] * int(n)
+    if a.nucleon:
+        import torch
+
+        lat = lqcd.Lattice(tuple(a.dims), "open")
+        s3 = a.dims[1] * a.dims[2] * a.dims[3]
+        ns = a.nucleon_slices
+        g = torch.Generator(device="cuda")
+        g.manual_seed(3)
+        s = torch.randn((a.nucleon, ns * s3, 4, 3), dtype=torch.complex128, device="cuda", generator=g)
+        lat.nucleon_blocks(s, (0, ns - 1), 0, ns, conj=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(a.reps):
+            lat.nucleon_blocks(s, (0, ns - 1), 0, ns, conj=True)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / a.reps
+        fl = 8.0 * 12 * a.nucleon ** 3 * s3 * ns
+        print(f"nucleon blocks N={a.nucleon} slices={ns} of {s3} sites: {ms:.3f} ms/launch, "
+              f"{fl / ms / 1e9:.2f} TFLOP/s (8 flop per complex FMA of the (x, c) contraction)")
+        lat.close()
+        return
     U = inputs.random_su3_field(tuple(a.dims), 0.4, 1)
     lat = lqcd.Lattice(tuple(a.dims), "open")
     lat.set_gauge(U, a.kappa, a.csw)

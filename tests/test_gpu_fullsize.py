@@ -250,3 +250,30 @@ def test_disconnected_64x24_against_oracle_contraction():
         assert np.abs(tr[0, d] - ref).max() <= 1e-9 * eta2, d
         assert np.abs(ref[t0:t1 + 1]).min() > 0
     lat.close()
+
+
+def test_nucleon_blocks_120_modes_24cube_sampled():
+    """k_nucleon_block in the launch configuration of the 64x24^3 projection workload (N_m = 120,
+    a 24^3 slice, ragged k tile): sampled (i, j) rows of B against the oracle's definition written
+    for those rows, with the FP32 tolerance of tests/test_gpu_nucleon.py for a 24^3 slice
+    ((3 + 192 + 216) u32 = 2.4e-5 of the bound built from |s|; 3e-5 allowed)."""
+    from paper_1612_06424_gb300 import build, lqcd
+
+    build.build()
+    dims = (64, 24, 24, 24)
+    s3 = 24 ** 3
+    n = 120
+    lat = lqcd.Lattice(dims, "open")
+    rng = np.random.default_rng(17)
+    s = (rng.standard_normal((n, s3, 4, 3)) + 1j * rng.standard_normal((n, s3, 4, 3))) / np.sqrt(2)
+    B = lat.nucleon_blocks(torch.from_numpy(s).cuda(), (4, 4), 4, 1, conj=True)[0]
+    f = np.conj(s)
+    cg5 = oracle.charge_conjugation() @ oracle.gamma(4)
+    for i, j in [(0, 5), (61, 77), (119, 118), (8, 8)]:
+        d = np.einsum("abc,xma,mn,xnb->xc", oracle.EPS3, f[i], cg5, f[j])
+        want = np.einsum("xc,kxdc->kd", d, f)
+        db = np.einsum("abc,xma,mn,xnb->xc", np.abs(oracle.EPS3), np.abs(f[i]), np.abs(cg5), np.abs(f[j]))
+        bound = np.einsum("xc,kxdc->kd", db, np.abs(f))
+        got = B[i, j].cpu().numpy()
+        assert np.all(np.abs(got - want) <= 3e-5 * bound), (i, j)
+    lat.close()

@@ -74,3 +74,23 @@ def test_factorized_equals_propagator_form():
     assert abs(w1 - r1) < 1e-11 * abs(r1) and abs(r1) > 1e-6
     assert abs(w2 - r2) < 1e-11 * abs(r2) and abs(r2) > 1e-6
     assert abs(w1 - w2) > 1e-6 * abs(w1)        # the two contractions differ
+
+
+def test_multilevel_estimator_special_cases():
+    """n1 = 1 gives the plain estimator mean_i(O_G O_G* + O_corr); for a bilinear product the
+    level-1 average equals the mean over all n1^2 (j, k) pairs (the exchange that makes the
+    two-level average an n1^2 sample)."""
+    rng = np.random.default_rng(8)
+    n0, n1 = 3, 4
+    og = rng.standard_normal((n0, 1))
+    ogs = rng.standard_normal((n0, 1))
+    oc = rng.standard_normal((n0, 1))
+    assert abs(oracle.multilevel_estimator(og, ogs, oc) - np.mean(og[:, 0] * ogs[:, 0] + oc[:, 0])) < 1e-15
+    A = rng.standard_normal((n0, n1, 3, 5))
+    Bm = rng.standard_normal((n0, n1, 5))
+    C = np.zeros((n0, n1, 3))
+    prod = lambda a, b: a @ b
+    got = oracle.multilevel_estimator(A, Bm, C, prod)
+    want = np.mean([np.mean([A[i, j] @ Bm[i, k] for j in range(n1) for k in range(n1)], axis=0)
+                    for i in range(n0)], axis=0)
+    assert np.abs(got - want).max() < 1e-13
