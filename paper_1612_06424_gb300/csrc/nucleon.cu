@@ -51,8 +51,8 @@ LQ_DI float2 cg5_pair(const float2* si, const float2* tj, int a, int b) {
 // slab-local sites lo0 + z * t_stride_sites .. + S3.
 __global__ void __launch_bounds__(256, 2) k_nucleon_block(int n, long long nsite, const double2* s, int conj,
                                                        int S3, long long lo0, int t_stride_sites, double2* B) {
-  __shared__ float2 fi[XS][TI][12], fj[XS][TJ][12];
-  __shared__ float2 Ds[XS * 3][TI * TJ + 1], Ss[XS * 3][TK * 4 + 1];
+  __shared__ float2 fi[XS][TI][13], fj[XS][TJ][13];  // 13: rows on distinct banks
+  __shared__ __align__(16) float2 Ds[XS * 3][TI * TJ], Ss[XS * 3][TK * 4];
   extern __shared__ float2 tot[];  // [16][256]: second-level sums of each thread's 4 x 4 tile
   const int nti = (n + TI - 1) / TI, ntj = (n + TJ - 1) / TJ;
   const int tile = blockIdx.x;
@@ -60,7 +60,9 @@ __global__ void __launch_bounds__(256, 2) k_nucleon_block(int n, long long nsite
   const int k0 = blockIdx.y * TK;
   const int t = blockIdx.z;
   const long long lo = lo0 + (long long)t * t_stride_sites;
-  const int tr = threadIdx.x / 16, tc = threadIdx.x % 16;  // rows tr*4.., cols tc*4..
+  // thread tile: rows tr*4 .. tr*4+3 and columns 2tc, 2tc+1, 32+2tc, 32+2tc+1 (so that the
+  // 16 threads of a row read 256 contiguous bytes of S per 16-byte load)
+  const int tr = threadIdx.x / 16, tc = threadIdx.x % 16;
   float2 acc[4][4];
 #pragma unroll
   for (int p = 0; p < 4; p++)
@@ -99,23 +101,40 @@ __global__ void __launch_bounds__(256, 2) k_nucleon_block(int n, long long nsite
       Ss[x * 3 + c][kk * 4 + al] = v;
     }
     __syncthreads();
-    // diquark D[(x, c)][(i, j)]
-    for (int e = threadIdx.x; e < XS * 3 * TI * TJ; e += blockDim.x) {
-      const int pr = e % (TI * TJ), xc = e / (TI * TJ);
-      const int x = xc / 3, c = xc % 3;
+    // diquark D[(x, c)][(i, j)], the three colours c of one (x, i, j) from one read of s_i(x), s_j(x)
+    for (int e = threadIdx.x; e < XS * TI * TJ; e += blockDim.x) {
+      const int pr = e % (TI * TJ), x = e / (TI * TJ);
       const int ii = pr / TJ, jj = pr % TJ;
-      const int a = (c + 1) % 3, b = (c + 2) % 3;  // eps^{abc} = +1 for (a, b) and -1 for (b, a)
-      const float2 p = cg5_pair(fi[x][ii], fj[x][jj], a, b), m = cg5_pair(fi[x][ii], fj[x][jj], b, a);
-      Ds[xc][pr] = make_float2(p.x - m.x, p.y - m.y);
+      float2 u[12], v[12];
+#pragma unroll
+      for (int q = 0; q < 12; q++) {
+        u[q] = fi[x][ii][q];
+        v[q] = fj[x][jj][q];
+      }
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        const int a = (c + 1) % 3, b = (c + 2) % 3;  // eps^{abc} = +1 for (a, b) and -1 for (b, a)
+        const float2 p = cg5_pair(u, v, a, b), m = cg5_pair(u, v, b, a);
+        Ds[x * 3 + c][pr] = make_float2(p.x - m.x, p.y - m.y);
+      }
     }
     __syncthreads();
 #pragma unroll 4
     for (int r = 0; r < XS * 3; r++) {
       float2 av[4], bv[4];
-#pragma unroll
-      for (int p = 0; p < 4; p++) {
-        av[p] = Ds[r][tr * 4 + p];
-        bv[p] = Ss[r][tc * 4 + p];
+      {
+        const float4* pa = reinterpret_cast<const float4*>(&Ds[r][tr * 4]);
+        const float4 a0 = pa[0], a1 = pa[1];
+        const float4 b0 = *reinterpret_cast<const float4*>(&Ss[r][2 * tc]);
+        const float4 b1 = *reinterpret_cast<const float4*>(&Ss[r][32 + 2 * tc]);
+        av[0] = make_float2(a0.x, a0.y);
+        av[1] = make_float2(a0.z, a0.w);
+        av[2] = make_float2(a1.x, a1.y);
+        av[3] = make_float2(a1.z, a1.w);
+        bv[0] = make_float2(b0.x, b0.y);
+        bv[1] = make_float2(b0.z, b0.w);
+        bv[2] = make_float2(b1.x, b1.y);
+        bv[3] = make_float2(b1.z, b1.w);
       }
 #pragma unroll
       for (int p = 0; p < 4; p++)
@@ -145,7 +164,7 @@ __global__ void __launch_bounds__(256, 2) k_nucleon_block(int n, long long nsite
     if (i >= n || j >= n) continue;
 #pragma unroll
     for (int q = 0; q < 4; q++) {
-      const int col = tc * 4 + q;
+      const int col = q < 2 ? 2 * tc + q : 32 + 2 * tc + q - 2;
       const int k = k0 + col / 4, al = col % 4;
       if (k >= n) continue;
       const float2 t2 = tot[(p * 4 + q) * 256 + threadIdx.x];
