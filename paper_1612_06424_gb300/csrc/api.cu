@@ -614,6 +614,12 @@ extern "C" int lqcd_create_lattice(const int dims[4], int bc_t, lqcd_lattice** o
       lq_set_error("lattice too large for one GPU field (V/2 * 72 must stay below 2^31)");
       return LQCD_EBADARG;
     }
+    // site coordinates use one multiply-high per division (fast_div): exact while index * divisor < 2^32
+    const long long dmax = std::max({(long long)dims[1], (long long)dims[2], (long long)dims[3] / 2});
+    if ((V / 2) * dmax >= (1LL << 32)) {
+      lq_set_error("spatial extent too large for this lattice volume (V/2 * max(L1, L2, L3/2) must stay below 2^32)");
+      return LQCD_EBADARG;
+    }
   }
   lqcd_lattice* L = new lqcd_lattice();
   for (int k = 0; k < 4; k++) L->dims[k] = dims[k];
@@ -627,6 +633,9 @@ extern "C" int lqcd_create_lattice(const int dims[4], int bc_t, lqcd_lattice** o
   L->g.Vh = (int)L->Vh;
   L->g.S3h = (int)L->S3h;
   L->g.bc_t = bc_t;
+  L->g.m3h = lq::fast_magic((unsigned)L->g.L3h);
+  L->g.m2 = lq::fast_magic((unsigned)dims[2]);
+  L->g.m1 = lq::fast_magic((unsigned)dims[1]);
   cudaGetDevice(&L->device);
   // Solver work vectors come from the device's stream-ordered pool; keep its
   // memory mapped across synchronisations instead of returning it to the

@@ -111,17 +111,27 @@ struct Geom {
   int Vh;   // sites per parity
   int S3h;  // sites per parity and time slice
   int bc_t;   // 0 open, 1 periodic, 2 antiperiodic
+  unsigned m3h, m2, m1;  // division magics of L3h, L2, L1 (fast_magic)
 };
+
+// n / d by one multiply-high: with m = ceil(2^32 / d) (d >= 2),
+// floor(n m / 2^32) = floor(n / d) whenever n d < 2^32, because
+// n m / 2^32 - n / d < n / 2^32 < 1 / d.  m = 0 stands for d = 1.  The
+// lattice constructor checks n d < 2^32 for every site index n.
+LQ_HDI unsigned fast_magic(unsigned d) { return d <= 1 ? 0u : (unsigned)((0x100000000ull + d - 1) / d); }
+LQ_DI int fast_div(int n, unsigned m) { return m ? (int)__umulhi((unsigned)n, m) : n; }
 
 // Coordinates of checkerboard site cb of parity p.
 LQ_DI void eo_coords(const Geom& g, int cb, int p, int x[4]) {
-  int r = cb;
-  int x3h = (int)(r % g.L3h);
-  r /= g.L3h;
-  x[2] = (int)(r % g.L[2]);
-  r /= g.L[2];
-  x[1] = (int)(r % g.L[1]);
-  x[0] = (int)(r / g.L[1]);
+  int q = fast_div(cb, g.m3h);
+  const int x3h = cb - q * g.L3h;
+  int r = q;
+  q = fast_div(r, g.m2);
+  x[2] = r - q * g.L[2];
+  r = q;
+  q = fast_div(r, g.m1);
+  x[1] = r - q * g.L[1];
+  x[0] = q;
   x[3] = 2 * x3h + ((x[0] + x[1] + x[2] + p) & 1);
 }
 

@@ -187,10 +187,282 @@ LQ_DI void hop_sum_f(const Geom& g, const SysDesc& sd, const FieldPtrs& f, int p
   hop_dir_f<P, DAG, 3>(g, sd, f, pout, cb, x, fetch, acc);
 }
 
+// ---------------------------------------------------------------------------
+// Software-pipelined hop sum (FP32 / FP16).  The eight hops are taken in a
+// fixed order k = 2*mu + (0 forward, 1 backward); the raw words of hop k+D
+// (neighbour spinor and link, as stored) are loaded before hop k is
+// computed, so up to D hops' loads are in flight while the thread does
+// arithmetic.  Loads are unconditional: a hop that leaves the slab (or
+// crosses the open time boundary) reads the thread's own in-range words and
+// is then weighted by 0, so the pipeline has no branches.
+#ifndef LQ_HOP_PIPE
+#define LQ_HOP_PIPE 1
+#endif
+
+template <int P>
+struct HopRaw;
+template <>
+struct HopRaw<32> {
+  float4 s[6];
+  float4 u[3];
+};
+template <>
+struct HopRaw<16> {
+  uint4 s[3];
+  float nu;
+  uint2 u[3];
+};
+
+// Pipeline depth per precision (hops whose loads are in flight while one is
+// computed): bounded by the register cap of the stencil kernels.
+#ifndef LQ_HOP_DEPTH32
+#define LQ_HOP_DEPTH32 2
+#endif
+#ifndef LQ_HOP_DEPTH16
+#define LQ_HOP_DEPTH16 2
+#endif
+template <int P>
+struct HopDepth {
+  static constexpr int value = P == 16 ? LQ_HOP_DEPTH16 : LQ_HOP_DEPTH32;
+};
+
+LQ_DI void raw_load(HopRaw<32>& r, const void* in, const float*, int n, int q, const FieldPtrs& f, int p, int mu,
+                    int Vh, int cl) {
+  const float4* sp = (const float4*)in + q;
+#pragma unroll
+  for (int k = 0; k < 6; k++) r.s[k] = __ldg(sp + k * n);
+  const float4* b = f.U32 + (p * 4 + mu) * 3 * Vh + cl;
+#pragma unroll
+  for (int k = 0; k < 3; k++) r.u[k] = ld_once(b + k * Vh);
+}
+LQ_DI void raw_load(HopRaw<16>& r, const void* in, const float* inn, int n, int q, const FieldPtrs& f, int p, int mu,
+                    int Vh, int cl) {
+  const uint4* sp = (const uint4*)in + q;
+#pragma unroll
+  for (int k = 0; k < 3; k++) r.s[k] = __ldg(sp + k * n);
+  r.nu = __ldg(inn + q);
+  const uint2* b = f.U16 + (p * 4 + mu) * 3 * Vh + cl;
+#pragma unroll
+  for (int k = 0; k < 3; k++) r.u[k] = ld_once(b + k * Vh);
+}
+
+LQ_DI void raw_spinor(const HopRaw<32>& r, cx<float> s[12]) {
+#pragma unroll
+  for (int k = 0; k < 6; k++) {
+    s[2 * k] = {r.s[k].x, r.s[k].y};
+    s[2 * k + 1] = {r.s[k].z, r.s[k].w};
+  }
+}
+LQ_DI void raw_spinor(const HopRaw<16>& r, cx<float> s[12]) {
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    const uint32_t w[4] = {r.s[k].x, r.s[k].y, r.s[k].z, r.s[k].w};
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      float2 v = __half22float2(*reinterpret_cast<const __half2*>(&w[q]));
+      s[4 * k + q] = {v.x * r.nu, v.y * r.nu};
+    }
+  }
+}
+
+LQ_DI su3<float> raw_link(const HopRaw<32>& r) {
+  su3<float> u;
+  u.m[0][0] = {r.u[0].x, r.u[0].y};
+  u.m[0][1] = {r.u[0].z, r.u[0].w};
+  u.m[0][2] = {r.u[1].x, r.u[1].y};
+  u.m[1][0] = {r.u[1].z, r.u[1].w};
+  u.m[1][1] = {r.u[2].x, r.u[2].y};
+  u.m[1][2] = {r.u[2].z, r.u[2].w};
+  reconstruct_row2(u);
+  return u;
+}
+LQ_DI su3<float> raw_link(const HopRaw<16>& r) {
+  su3<float> u;
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    float2 a = __half22float2(*reinterpret_cast<const __half2*>(&r.u[k].x));
+    float2 b = __half22float2(*reinterpret_cast<const __half2*>(&r.u[k].y));
+    u.m[(2 * k) / 3][(2 * k) % 3] = {a.x, a.y};
+    u.m[(2 * k + 1) / 3][(2 * k + 1) % 3] = {b.x, b.y};
+  }
+  reconstruct_row2(u);
+  return u;
+}
+
+// Where hop k reads: neighbour index q within the system's input vector,
+// link site and parity, and the weight (0 for a dropped hop, +-1 else).
+struct HopTgt {
+  int q, cl, pl;
+  float w;
+};
+
+template <int K>
+LQ_DI HopTgt hop_target(const Geom& g, const SysDesc& sd, int pout, int cb, int j, const int x[4]) {
+  constexpr int MU = K >> 1;
+  constexpr bool FWD = (K & 1) == 0;
+  int y[4] = {x[0], x[1], x[2], x[3]};
+  bool ok = true;
+  float sgn = 1.f;
+  if (MU == 0) {
+    if (FWD) {
+      if (x[0] == sd.t1) {
+        ok = sd.wrap;
+        y[0] = 0;
+        sgn = sd.tsign;
+      } else {
+        y[0] = x[0] + 1;
+      }
+    } else {
+      if (x[0] == sd.t0) {
+        ok = sd.wrap;
+        y[0] = g.L[0] - 1;
+        sgn = sd.tsign;
+      } else {
+        y[0] = x[0] - 1;
+      }
+    }
+  } else if (FWD) {
+    y[MU] = (x[MU] + 1 == g.L[MU]) ? 0 : x[MU] + 1;
+  } else {
+    y[MU] = (x[MU] == 0) ? g.L[MU] - 1 : x[MU] - 1;
+  }
+  HopTgt t;
+  const int cy = eo_index(g, y);
+  t.q = ok ? cy - sd.cb0 : j;
+  t.cl = FWD ? cb : (ok ? cy : cb);
+  t.pl = FWD ? pout : pout ^ 1;
+  t.w = ok ? sgn : 0.f;
+  return t;
+}
+
+template <int P, int K>
+LQ_DI void raw_fetch(HopRaw<P>& r, const Geom& g, const SysDesc& sd, const FieldPtrs& f, int pout, int cb, int j,
+                     const int x[4], const void* in, const float* inn) {
+  const HopTgt t = hop_target<K>(g, sd, pout, cb, j, x);
+  raw_load(r, in, inn, sd.n, t.q, f, t.pl, K >> 1, g.Vh, t.cl);
+}
+
+// Packed FP32 pairs (f32x2 arithmetic of sm_100+): one instruction operates
+// on two FP32 values held in an aligned register pair.
+typedef unsigned long long f2_t;
+LQ_DI f2_t f2_pack(float a, float b) {
+  f2_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+LQ_DI void f2_unpack(f2_t r, float& a, float& b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r)); }
+LQ_DI f2_t f2_fma(f2_t a, f2_t b, f2_t c) {
+  f2_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+LQ_DI f2_t f2_mul(f2_t a, f2_t b) {
+  f2_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+#ifndef LQ_HOP_PACK
+#define LQ_HOP_PACK 0
+#endif
+// Colour transport of the two spins of a half spinor with packed pairs: the
+// pair index is the spin, so one link element (broadcast to both halves)
+// multiplies both spins in one instruction.  w[sp][a] = sum_c U[a][c] h[sp][c]
+// (forward) or sum_c conj(U[c][a]) h[sp][c] (backward).
+template <bool FWD>
+LQ_DI void mul_u_pairs(const su3<float>& u, const cx<float> h[6], cx<float> w[6]) {
+  f2_t hr[3], hi[3], hn[3];
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    hr[c] = f2_pack(h[c].re, h[3 + c].re);
+    hi[c] = f2_pack(h[c].im, h[3 + c].im);
+    hn[c] = f2_pack(FWD ? -h[c].im : -h[c].re, FWD ? -h[3 + c].im : -h[3 + c].re);
+  }
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    f2_t wr = 0ull, wi = 0ull;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      const cx<float> e = FWD ? u.m[a][c] : u.m[c][a];
+      const f2_t br = f2_pack(e.re, e.re), bi = f2_pack(e.im, e.im);
+      if (FWD) {  // (er + i ei)(hr + i hi)
+        wr = c ? f2_fma(br, hr[c], wr) : f2_mul(br, hr[c]);
+        wr = f2_fma(bi, hn[c], wr);
+        wi = c ? f2_fma(br, hi[c], wi) : f2_mul(br, hi[c]);
+        wi = f2_fma(bi, hr[c], wi);
+      } else {  // (er - i ei)(hr + i hi)
+        wr = c ? f2_fma(br, hr[c], wr) : f2_mul(br, hr[c]);
+        wr = f2_fma(bi, hi[c], wr);
+        wi = c ? f2_fma(br, hi[c], wi) : f2_mul(br, hi[c]);
+        wi = f2_fma(bi, hn[c], wi);
+      }
+    }
+    f2_unpack(wr, w[a].re, w[3 + a].re);
+    f2_unpack(wi, w[a].im, w[3 + a].im);
+  }
+}
+
+// Hop k from its raw words: acc += weight * (1 -+ g_mu) U psi (forward) or
+// (1 +- g_mu) U^dag psi (backward).
+template <int P, bool DAG, int K>
+LQ_DI void hop_apply(const HopRaw<P>& r, float wgt, cx<float> acc[12]) {
+  constexpr int MU = K >> 1;
+  constexpr bool FWD = (K & 1) == 0;
+  constexpr int SF = DAG ? +1 : -1;
+  constexpr int S = FWD ? SF : -SF;
+  cx<float> h[6], w[6];
+  {
+    cx<float> psi[12];
+    raw_spinor(r, psi);
+    project<MU, S>(psi, h);
+  }
+  const su3<float> u = raw_link(r);
+  if (LQ_HOP_PACK)
+    mul_u_pairs<FWD>(u, h, w);
+  else if (FWD)
+    mul_u(u, h, w);
+  else
+    mul_udag(u, h, w);
+  if (MU == 0) {
+#pragma unroll
+    for (int k = 0; k < 6; k++) w[k] = wgt * w[k];
+  }
+  expand_add<MU, S>(acc, w);
+}
+
+// One step of the pipeline: issue the loads of hop K + D, then compute hop K.
+// Only the time hops (K = 0, 1) carry a weight other than 1.
+template <int P, bool DAG, int K, int D>
+LQ_DI void hop_pipe_step(HopRaw<P> (&buf)[D + 1], const Geom& g, const SysDesc& sd, const FieldPtrs& f, int pout,
+                         int cb, int j, const int x[4], const void* in, const float* inn, float w0, float w1,
+                         cx<float> acc[12]) {
+  if constexpr (K + D < 8) raw_fetch<P, K + D>(buf[(K + D) % (D + 1)], g, sd, f, pout, cb, j, x, in, inn);
+  hop_apply<P, DAG, K>(buf[K % (D + 1)], K == 0 ? w0 : w1, acc);
+  if constexpr (K + 1 < 8) hop_pipe_step<P, DAG, K + 1, D>(buf, g, sd, f, pout, cb, j, x, in, inn, w0, w1, acc);
+}
+
 template <int P, bool DAG>
-LQ_DI void hop_sum(const Geom& g, const SysDesc& sd, const FieldPtrs& f, int pout, int cb, const int x[4],
+LQ_DI void hop_sum_pipe(const Geom& g, const SysDesc& sd, const FieldPtrs& f, int pout, int cb, int j, const int x[4],
+                        const void* in, const float* inn, cx<float> acc[12]) {
+  constexpr int D = HopDepth<P>::value;
+  HopRaw<P> buf[D + 1];
+  raw_fetch<P, 0>(buf[0], g, sd, f, pout, cb, j, x, in, inn);
+  if constexpr (D > 1) raw_fetch<P, 1>(buf[1], g, sd, f, pout, cb, j, x, in, inn);
+  if constexpr (D > 2) raw_fetch<P, 2>(buf[2], g, sd, f, pout, cb, j, x, in, inn);
+  static_assert(D >= 1 && D <= 3, "pipeline depth");
+  const float w0 = hop_target<0>(g, sd, pout, cb, j, x).w, w1 = hop_target<1>(g, sd, pout, cb, j, x).w;
+#pragma unroll
+  for (int k = 0; k < 12; k++) acc[k] = {0.f, 0.f};
+  hop_pipe_step<P, DAG, 0, D>(buf, g, sd, f, pout, cb, j, x, in, inn, w0, w1, acc);
+}
+
+template <int P, bool DAG>
+LQ_DI void hop_sum(const Geom& g, const SysDesc& sd, const FieldPtrs& f, int pout, int cb, int j, const int x[4],
                    const void* in, const float* inn, cx<typename Prec<P>::R> acc[12]) {
-  hop_sum_f<P, DAG>(g, sd, f, pout, cb, x, GlobalFetch<P>{in, inn, sd.n}, acc);
+  if constexpr (P != 64 && LQ_HOP_PIPE)
+    hop_sum_pipe<P, DAG>(g, sd, f, pout, cb, j, x, in, inn, acc);
+  else
+    hop_sum_f<P, DAG>(g, sd, f, pout, cb, x, GlobalFetch<P>{in, inn, sd.n}, acc);
 }
 
 // Clover block apply (A or A^{-1}) on a full spinor.
@@ -301,17 +573,18 @@ __global__ void __launch_bounds__(128, HopMinBlocks<P>::value) k_hop_lin(HopArgs
   grid_pos(a.nsys, s, by);
   if (a.active && !a.active[s]) return;
   const SysDesc sd = a.sys[s];
-  if (by * (int)blockDim.x >= sd.n) return;  // whole block beyond this system
-  const int j = by * blockDim.x + threadIdx.x;
+  const int j0 = by * blockDim.x;
+  if (j0 >= sd.n) return;  // whole block beyond this system
+  const int j = j0 + threadIdx.x;
+  const FieldPtrs f = a.fields[sd.field];
   R red[3] = {0, 0, 0};
   if (j < sd.n) {
-    const FieldPtrs f = a.fields[sd.field];
     const int cb = sd.cb0 + j;
     cx<R> res[12];
     if (EPI & EPI_X) {
       int x[4];
       eo_coords(a.g, cb, a.pout, x);
-      hop_sum<P, DAG>(a.g, sd, f, a.pout, cb, x, sys_ptr<P>(a.x, sd.off), nrm_ptr(a.xn, sd.off), res);
+      hop_sum<P, DAG>(a.g, sd, f, a.pout, cb, j, x, sys_ptr<P>(a.x, sd.off), nrm_ptr(a.xn, sd.off), res);
       const R al = (R)a.alpha;
 #pragma unroll
       for (int k = 0; k < 12; k++) res[k] = al * res[k];
@@ -376,15 +649,17 @@ __global__ void __launch_bounds__(128, HopMinBlocks<P>::value) k_hop_clinv(HopAr
   grid_pos(a.nsys, s, by);
   if (a.active && !a.active[s]) return;
   const SysDesc sd = a.sys[s];
-  const int j = by * blockDim.x + threadIdx.x;
-  if (j >= sd.n) return;
+  const int j0 = by * blockDim.x;
+  if (j0 >= sd.n) return;
+  const int j = j0 + threadIdx.x;
   const FieldPtrs f = a.fields[sd.field];
+  if (j >= sd.n) return;
   const int cb = sd.cb0 + j;
   cx<R> res[12];
   if (EPI & EPI_X) {
     int x[4];
     eo_coords(a.g, cb, a.pout, x);
-    hop_sum<P, DAG>(a.g, sd, f, a.pout, cb, x, sys_ptr<P>(a.x, sd.off), nrm_ptr(a.xn, sd.off), res);
+    hop_sum<P, DAG>(a.g, sd, f, a.pout, cb, j, x, sys_ptr<P>(a.x, sd.off), nrm_ptr(a.xn, sd.off), res);
     const R al = (R)a.alpha;
 #pragma unroll
     for (int k = 0; k < 12; k++) res[k] = al * res[k];

@@ -94,15 +94,20 @@ static int launch_clinv2(int epi, dim3 gr, const HopArgs& a, cudaStream_t st) {
   return 0;
 }
 
+template <int P>
+static void hop_go(void (*k)(HopArgs), dim3 gr, const HopArgs& a, cudaStream_t st) {
+  k<<<gr, LQ_BLOCK, 0, st>>>(a);
+}
+
 // (reduction, epilogue) pairs the solver uses
 template <int P, bool DAG, bool CLOV>
 static int launch_lin(int red, int epi, dim3 gr, const HopArgs& a, cudaStream_t st) {
   constexpr int XY = EPI_X | EPI_Y, XZ = EPI_X | EPI_Z, XYZ = EPI_X | EPI_Y | EPI_Z;
-  if (red == RED_NONE && epi == XY) k_hop_lin<P, DAG, CLOV, RED_NONE, XY><<<gr, LQ_BLOCK, 0, st>>>(a);
-  else if (red == RED_NONE && epi == XZ) k_hop_lin<P, DAG, CLOV, RED_NONE, XZ><<<gr, LQ_BLOCK, 0, st>>>(a);
-  else if (red == RED_DOT_W && epi == XY) k_hop_lin<P, DAG, CLOV, RED_DOT_W, XY><<<gr, LQ_BLOCK, 0, st>>>(a);
-  else if (red == RED_TS && epi == XY) k_hop_lin<P, DAG, CLOV, RED_TS, XY><<<gr, LQ_BLOCK, 0, st>>>(a);
-  else if (red == RED_NORM && epi == XYZ) k_hop_lin<P, DAG, CLOV, RED_NORM, XYZ><<<gr, LQ_BLOCK, 0, st>>>(a);
+  if (red == RED_NONE && epi == XY) hop_go<P>(k_hop_lin<P, DAG, CLOV, RED_NONE, XY>, gr, a, st);
+  else if (red == RED_NONE && epi == XZ) hop_go<P>(k_hop_lin<P, DAG, CLOV, RED_NONE, XZ>, gr, a, st);
+  else if (red == RED_DOT_W && epi == XY) hop_go<P>(k_hop_lin<P, DAG, CLOV, RED_DOT_W, XY>, gr, a, st);
+  else if (red == RED_TS && epi == XY) hop_go<P>(k_hop_lin<P, DAG, CLOV, RED_TS, XY>, gr, a, st);
+  else if (red == RED_NORM && epi == XYZ) hop_go<P>(k_hop_lin<P, DAG, CLOV, RED_NORM, XYZ>, gr, a, st);
   else return -1;
   return 0;
 }
@@ -146,9 +151,9 @@ int lq_hop_lin(int P, bool dag, bool clov, int red, const lqcd_lattice* L, const
 
 template <int P, bool DAG, bool CLOV>
 static int launch_clinv(int epi, dim3 gr, const HopArgs& a, cudaStream_t st) {
-  if (epi == EPI_X) k_hop_clinv<P, DAG, CLOV, EPI_X><<<gr, LQ_BLOCK, 0, st>>>(a);
-  else if (epi == EPI_Y) k_hop_clinv<P, DAG, CLOV, EPI_Y><<<gr, LQ_BLOCK, 0, st>>>(a);
-  else if (epi == (EPI_X | EPI_Y)) k_hop_clinv<P, DAG, CLOV, EPI_X | EPI_Y><<<gr, LQ_BLOCK, 0, st>>>(a);
+  if (epi == EPI_X) hop_go<P>(k_hop_clinv<P, DAG, CLOV, EPI_X>, gr, a, st);
+  else if (epi == EPI_Y) hop_go<P>(k_hop_clinv<P, DAG, CLOV, EPI_Y>, gr, a, st);
+  else if (epi == (EPI_X | EPI_Y)) hop_go<P>(k_hop_clinv<P, DAG, CLOV, EPI_X | EPI_Y>, gr, a, st);
   else return -1;
   return 0;
 }

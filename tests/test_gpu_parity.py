@@ -53,17 +53,26 @@ def test_dslash_fp64_matches_oracle(dims, bc, csw):
 
 
 @pytest.mark.parametrize("prec,tol", [(32, 2e-6), (16, 3e-3)])
-def test_dslash_reduced_precision(prec, tol):
+@pytest.mark.parametrize("bc", ["open", "antiperiodic"])
+def test_dslash_reduced_precision(prec, tol, bc):
+    """FP32 / FP16 stencil on the whole lattice (wrapping time hops for the
+    antiperiodic case) and on Dirichlet slabs touching either end, both D and
+    D^dag: every dropped or sign-carrying hop of the stencil is exercised."""
     lqcd = _lq()
     dims = (8, 6, 6, 4)
     U = inputs.random_su3_field(dims, 0.4, 5)
-    lat = lqcd.Lattice(dims, "open")
+    lat = lqcd.Lattice(dims, bc)
     lat.set_gauge(U, 0.13, 1.0)
-    op = oracle.Operator(dims, U, 0.13, 1.0)
+    op = oracle.Operator(dims, U, 0.13, 1.0, BCS[bc])
     psi = inputs.gaussian_spinor(dims, 6)[0]
-    ref = op.apply(psi)
-    got = lat.dslash(_cuda(psi), 0, None, False, prec).cpu().numpy()
-    assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
+    T = dims[0]
+    for dom in [None, (0, 2), (3, T - 1), (2, 5)]:
+        for dag in (False, True):
+            t0, t1 = dom if dom else (0, T - 1)
+            sl = inputs.slab_sites(dims, t0, t1)
+            ref = op.apply(op.masked(psi, t0, t1), t0, t1, dagger=dag)[sl]
+            got = lat.dslash(_cuda(psi[sl]), 0, dom, dag, prec).cpu().numpy()
+            assert np.abs(got - ref).max() <= tol * np.abs(ref).max(), (dom, dag)
 
 
 @pytest.mark.parametrize("prec", [64, 32, 16])

@@ -1,0 +1,74 @@
+"""Every stencil variant the autotuner can pick, checked against the FP64 oracle.
+
+The variant is forced per process through LQCD_HOP_SPLIT (read once by the
+library), so each case runs in a child process:
+  1: one thread per site, 128 sites of one system per block;
+  2: two threads per site (FP32 only; FP16 falls back to 1).
+Each child applies the FP32 / FP16 operator on the whole lattice and on
+Dirichlet slabs (D and D^dag; tolerances of tests/test_gpu_parity.py) and
+solves a batch of five systems on mixed slabs in FP32 and FP16 to true
+residual 1e-10, checked with the oracle's operator.  8x6x6x4: 576 sites per
+parity, several blocks and a ragged tail for every variant.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+CHILD = r"""
+import sys
+import numpy as np
+import torch
+sys.path.insert(0, ROOT)
+import oracle
+from paper_1612_06424_gb300 import build, inputs
+build.build()
+from paper_1612_06424_gb300 import lqcd
+
+dims = (8, 6, 6, 4)
+U = inputs.random_su3_field(dims, 0.4, 5)
+lat = lqcd.Lattice(dims, "open")
+lat.set_gauge(U, 0.13, 1.0)
+op = oracle.Operator(dims, U, 0.13, 1.0)
+psi = inputs.gaussian_spinor(dims, 6)[0]
+for prec, tol in ((32, 2e-6), (16, 3e-3)):
+    for dom in (None, (0, 2), (3, 7), (2, 5)):
+        for dag in (False, True):
+            t0, t1 = dom if dom else (0, 7)
+            sl = inputs.slab_sites(dims, t0, t1)
+            ref = op.apply(op.masked(psi, t0, t1), t0, t1, dagger=dag)[sl]
+            got = lat.dslash(torch.from_numpy(np.ascontiguousarray(psi[sl])).cuda(), 0, dom, dag, prec).cpu().numpy()
+            err = np.abs(got - ref).max() / np.abs(ref).max()
+            assert err <= tol, (prec, dom, dag, err)
+doms = [(0, 3), (2, 7), (0, 7), (4, 7), (1, 5)]
+srcs = inputs.gaussian_spinor(dims, 8, len(doms))
+packed = np.concatenate([srcs[k][inputs.slab_sites(dims, *d)] for k, d in enumerate(doms)])
+for prec in (32, 16):
+    sol, stats = lat.solve_block(torch.from_numpy(packed).cuda(), doms, [0] * len(doms),
+                                 lqcd.SolverParams(tol=1e-10, precision=prec))
+    sol = sol.cpu().numpy()
+    off = 0
+    for k, d in enumerate(doms):
+        sl = inputs.slab_sites(dims, *d)
+        n = sl.stop - sl.start
+        got = np.zeros((op.V, 4, 3), complex)
+        got[sl] = sol[off:off + n]
+        off += n
+        b = op.masked(srcs[k], *d)
+        res = np.linalg.norm(b - op.apply(got, *d)) / np.linalg.norm(b)
+        assert res <= 1.5e-10 and stats[k]["status"] == 0, (prec, d, res, stats[k])
+print("variant ok")
+"""
+
+
+@pytest.mark.parametrize("variant", ["1", "2"])
+def test_stencil_variant_parity(variant):
+    env = dict(os.environ, LQCD_HOP_SPLIT=variant)
+    r = subprocess.run([sys.executable, "-c", CHILD.replace("ROOT", repr(ROOT))], env=env, capture_output=True,
+                       text=True, timeout=900)
+    assert r.returncode == 0 and "variant ok" in r.stdout, r.stdout[-2000:] + r.stderr[-4000:]
