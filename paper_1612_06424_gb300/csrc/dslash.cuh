@@ -362,15 +362,18 @@ LQ_DI f2_t f2_mul(f2_t a, f2_t b) {
   return d;
 }
 
+// LQ_HOP_PACK 1: the FP32 / FP16 hop sum transports and accumulates spin
+// pairs with f32x2 arithmetic (measured 2-6% faster on GB300 than scalar
+// FP32); 0: scalar.
 #ifndef LQ_HOP_PACK
-#define LQ_HOP_PACK 0
+#define LQ_HOP_PACK 1
 #endif
 // Colour transport of the two spins of a half spinor with packed pairs: the
 // pair index is the spin, so one link element (broadcast to both halves)
 // multiplies both spins in one instruction.  w[sp][a] = sum_c U[a][c] h[sp][c]
 // (forward) or sum_c conj(U[c][a]) h[sp][c] (backward).
 template <bool FWD>
-LQ_DI void mul_u_pairs(const su3<float>& u, const cx<float> h[6], cx<float> w[6]) {
+LQ_DI void mul_u_pairs(const su3<float>& u, const cx<float> h[6], f2_t wr[3], f2_t wi[3]) {
   f2_t hr[3], hi[3], hn[3];
 #pragma unroll
   for (int c = 0; c < 3; c++) {
@@ -380,32 +383,86 @@ LQ_DI void mul_u_pairs(const su3<float>& u, const cx<float> h[6], cx<float> w[6]
   }
 #pragma unroll
   for (int a = 0; a < 3; a++) {
-    f2_t wr = 0ull, wi = 0ull;
+    f2_t r = 0ull, i = 0ull;
 #pragma unroll
     for (int c = 0; c < 3; c++) {
       const cx<float> e = FWD ? u.m[a][c] : u.m[c][a];
       const f2_t br = f2_pack(e.re, e.re), bi = f2_pack(e.im, e.im);
       if (FWD) {  // (er + i ei)(hr + i hi)
-        wr = c ? f2_fma(br, hr[c], wr) : f2_mul(br, hr[c]);
-        wr = f2_fma(bi, hn[c], wr);
-        wi = c ? f2_fma(br, hi[c], wi) : f2_mul(br, hi[c]);
-        wi = f2_fma(bi, hr[c], wi);
+        r = c ? f2_fma(br, hr[c], r) : f2_mul(br, hr[c]);
+        r = f2_fma(bi, hn[c], r);
+        i = c ? f2_fma(br, hi[c], i) : f2_mul(br, hi[c]);
+        i = f2_fma(bi, hr[c], i);
       } else {  // (er - i ei)(hr + i hi)
-        wr = c ? f2_fma(br, hr[c], wr) : f2_mul(br, hr[c]);
-        wr = f2_fma(bi, hi[c], wr);
-        wi = c ? f2_fma(br, hi[c], wi) : f2_mul(br, hi[c]);
-        wi = f2_fma(bi, hn[c], wi);
+        r = c ? f2_fma(br, hr[c], r) : f2_mul(br, hr[c]);
+        r = f2_fma(bi, hi[c], r);
+        i = c ? f2_fma(br, hi[c], i) : f2_mul(br, hi[c]);
+        i = f2_fma(bi, hn[c], i);
       }
     }
-    f2_unpack(wr, w[a].re, w[3 + a].re);
-    f2_unpack(wi, w[a].im, w[3 + a].im);
+    wr[a] = r;
+    wi[a] = i;
+  }
+}
+
+LQ_DI f2_t f2_add(f2_t a, f2_t b) {
+  f2_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+LQ_DI f2_t f2_sub(f2_t a, f2_t b) {
+  f2_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+// Accumulator of the packed hop sum: for colour a the spin pairs
+// (acc[s=0][a], acc[s=1][a]) and (acc[2][a], acc[3][a]), real and imaginary.
+struct AccP {
+  f2_t ur[3], ui[3], lr[3], li[3];
+};
+
+// acc += (1 + S g_mu) expanded from the transported half spinor w (pairs).
+template <int MU, int S>
+LQ_DI void expand_add_p(AccP& A, const f2_t wr[3], const f2_t wi[3]) {
+  const float s = (float)S;
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    A.ur[c] = f2_add(A.ur[c], wr[c]);
+    A.ui[c] = f2_add(A.ui[c], wi[c]);
+    if (MU == 0) {  // lower += -s (w0, w1)
+      A.lr[c] = S > 0 ? f2_sub(A.lr[c], wr[c]) : f2_add(A.lr[c], wr[c]);
+      A.li[c] = S > 0 ? f2_sub(A.li[c], wi[c]) : f2_add(A.li[c], wi[c]);
+    } else if (MU == 3) {  // lower += (s, -s) i (w0, w1)
+      A.lr[c] = f2_fma(f2_pack(-s, s), wi[c], A.lr[c]);
+      A.li[c] = f2_fma(f2_pack(s, -s), wr[c], A.li[c]);
+    } else {  // spins swapped: scalar updates of the pair halves
+      float l0r, l1r, l0i, l1i, w0r, w1r, w0i, w1i;
+      f2_unpack(A.lr[c], l0r, l1r);
+      f2_unpack(A.li[c], l0i, l1i);
+      f2_unpack(wr[c], w0r, w1r);
+      f2_unpack(wi[c], w0i, w1i);
+      if (MU == 1) {  // lower0 += s i w1, lower1 += s i w0
+        l0r -= s * w1i;
+        l0i += s * w1r;
+        l1r -= s * w0i;
+        l1i += s * w0r;
+      } else {  // MU == 2: lower0 += s w1, lower1 -= s w0
+        l0r += s * w1r;
+        l0i += s * w1i;
+        l1r -= s * w0r;
+        l1i -= s * w0i;
+      }
+      A.lr[c] = f2_pack(l0r, l1r);
+      A.li[c] = f2_pack(l0i, l1i);
+    }
   }
 }
 
 // Hop k from its raw words: acc += weight * (1 -+ g_mu) U psi (forward) or
 // (1 +- g_mu) U^dag psi (backward).
 template <int P, bool DAG, int K>
-LQ_DI void hop_apply(const HopRaw<P>& r, float wgt, cx<float> acc[12]) {
+LQ_DI void hop_apply(const HopRaw<P>& r, float wgt, cx<float> (&acc)[12]) {
   constexpr int MU = K >> 1;
   constexpr bool FWD = (K & 1) == 0;
   constexpr int SF = DAG ? +1 : -1;
@@ -417,9 +474,7 @@ LQ_DI void hop_apply(const HopRaw<P>& r, float wgt, cx<float> acc[12]) {
     project<MU, S>(psi, h);
   }
   const su3<float> u = raw_link(r);
-  if (LQ_HOP_PACK)
-    mul_u_pairs<FWD>(u, h, w);
-  else if (FWD)
+  if (FWD)
     mul_u(u, h, w);
   else
     mul_udag(u, h, w);
@@ -430,12 +485,39 @@ LQ_DI void hop_apply(const HopRaw<P>& r, float wgt, cx<float> acc[12]) {
   expand_add<MU, S>(acc, w);
 }
 
+// hop_apply with the packed accumulator.
+template <int P, bool DAG, int K>
+LQ_DI void hop_apply(const HopRaw<P>& r, float wgt, AccP& A) {
+  constexpr int MU = K >> 1;
+  constexpr bool FWD = (K & 1) == 0;
+  constexpr int SF = DAG ? +1 : -1;
+  constexpr int S = FWD ? SF : -SF;
+  cx<float> h[6];
+  {
+    cx<float> psi[12];
+    raw_spinor(r, psi);
+    project<MU, S>(psi, h);
+  }
+  const su3<float> u = raw_link(r);
+  f2_t wr[3], wi[3];
+  mul_u_pairs<FWD>(u, h, wr, wi);
+  if (MU == 0) {
+    const f2_t bw = f2_pack(wgt, wgt);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      wr[c] = f2_mul(bw, wr[c]);
+      wi[c] = f2_mul(bw, wi[c]);
+    }
+  }
+  expand_add_p<MU, S>(A, wr, wi);
+}
+
 // One step of the pipeline: issue the loads of hop K + D, then compute hop K.
 // Only the time hops (K = 0, 1) carry a weight other than 1.
-template <int P, bool DAG, int K, int D>
+template <int P, bool DAG, int K, int D, typename ACC>
 LQ_DI void hop_pipe_step(HopRaw<P> (&buf)[D + 1], const Geom& g, const SysDesc& sd, const FieldPtrs& f, int pout,
                          int cb, int j, const int x[4], const void* in, const float* inn, float w0, float w1,
-                         cx<float> acc[12]) {
+                         ACC& acc) {
   if constexpr (K + D < 8) raw_fetch<P, K + D>(buf[(K + D) % (D + 1)], g, sd, f, pout, cb, j, x, in, inn);
   hop_apply<P, DAG, K>(buf[K % (D + 1)], K == 0 ? w0 : w1, acc);
   if constexpr (K + 1 < 8) hop_pipe_step<P, DAG, K + 1, D>(buf, g, sd, f, pout, cb, j, x, in, inn, w0, w1, acc);
@@ -451,9 +533,24 @@ LQ_DI void hop_sum_pipe(const Geom& g, const SysDesc& sd, const FieldPtrs& f, in
   if constexpr (D > 2) raw_fetch<P, 2>(buf[2], g, sd, f, pout, cb, j, x, in, inn);
   static_assert(D >= 1 && D <= 3, "pipeline depth");
   const float w0 = hop_target<0>(g, sd, pout, cb, j, x).w, w1 = hop_target<1>(g, sd, pout, cb, j, x).w;
+  if constexpr (LQ_HOP_PACK) {
+    AccP A;
 #pragma unroll
-  for (int k = 0; k < 12; k++) acc[k] = {0.f, 0.f};
-  hop_pipe_step<P, DAG, 0, D>(buf, g, sd, f, pout, cb, j, x, in, inn, w0, w1, acc);
+    for (int c = 0; c < 3; c++) A.ur[c] = A.ui[c] = A.lr[c] = A.li[c] = 0ull;
+    hop_pipe_step<P, DAG, 0, D>(buf, g, sd, f, pout, cb, j, x, in, inn, w0, w1, A);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      f2_unpack(A.ur[c], acc[c].re, acc[3 + c].re);
+      f2_unpack(A.ui[c], acc[c].im, acc[3 + c].im);
+      f2_unpack(A.lr[c], acc[6 + c].re, acc[9 + c].re);
+      f2_unpack(A.li[c], acc[6 + c].im, acc[9 + c].im);
+    }
+  } else {
+    cx<float>(&a12)[12] = *reinterpret_cast<cx<float>(*)[12]>(acc);
+#pragma unroll
+    for (int k = 0; k < 12; k++) a12[k] = {0.f, 0.f};
+    hop_pipe_step<P, DAG, 0, D>(buf, g, sd, f, pout, cb, j, x, in, inn, w0, w1, a12);
+  }
 }
 
 template <int P, bool DAG>
