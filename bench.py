@@ -83,11 +83,21 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def _strip_comments(src: str) -> str:
+    """C++ source without // comments and blank lines (a comment edit does not change the kernel)."""
+    out = []
+    for line in src.splitlines():
+        code = line.split("//", 1)[0].rstrip()
+        if code.strip():
+            out.append(code)
+    return "\n".join(out)
+
+
 def _kernel_hash():
     h = hashlib.sha256()
     for f in ("common.cuh", "dslash.cuh"):
-        with open(os.path.join(ROOT, "paper_1612_06424_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1612_06424_gb300", "csrc", f), encoding="utf-8") as fh:
+            h.update(_strip_comments(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -214,7 +214,9 @@ struct HopRaw<16> {
 };
 
 // Pipeline depth per precision (hops whose loads are in flight while one is
-// computed): bounded by the register cap of the stencil kernels.
+// computed): bounded by the register cap of the stencil kernels.  FP32 depth
+// 2 at 4 blocks per SM measured best on GB300 (depth 1: -3%; depth 2 or 3 at
+// 3 blocks per SM: -5% and -13%).
 #ifndef LQ_HOP_DEPTH32
 #define LQ_HOP_DEPTH32 2
 #endif
@@ -605,10 +607,11 @@ struct HopArgs {
 enum { EPI_X = 1, EPI_Y = 2, EPI_Z = 4 };
 
 // Registers are capped so that HopMinBlocks<P> blocks of 128 threads fit on
-// an SM: the FP32 / FP16 stencil is latency-bound, and occupancy is what
-// hides its loads (4 and 5 blocks measured best on GB300; LQ_HOP_MINB
-// overrides both for experiments).  FP64 is ALU-bound and left uncapped
-// (a cap makes it spill).
+// an SM: the FP32 / FP16 stencil is latency-bound, and occupancy together
+// with the hop pipeline is what hides its loads (with the depth-2 pipeline,
+// 4 blocks measured best for FP32 on GB300: 5 blocks spill and lose 10%;
+// LQ_HOP_MINB overrides both for experiments).  FP64 is ALU-bound and left
+// uncapped (a cap makes it spill).
 template <int P>
 struct HopMinBlocks {
 #ifdef LQ_HOP_MINB
