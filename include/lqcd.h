@@ -108,7 +108,10 @@ typedef struct {
 
 /* Create a lattice of the given dims with time boundary condition bc_t.
  * *out receives an opaque handle owned by the library.  Selects the current
- * CUDA device.  Errors: LQCD_EBADARG (odd or non-positive extent). */
+ * CUDA device.  Errors: LQCD_EBADARG (an extent odd or below 2; V/2 * 72 at
+ * or above 2^31, since site indices of the packed link / clover arrays are
+ * 32-bit; V/2 * max(L1, L2, L3/2) at or above 2^32, since site coordinates
+ * are recovered with one multiply-high per division). */
 int lqcd_create_lattice(const int dims[4], int bc_t, lqcd_lattice **out);
 
 /* Free every device buffer of the lattice; the handle becomes invalid. */
