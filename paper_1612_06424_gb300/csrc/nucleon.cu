@@ -6,6 +6,10 @@
 // partial sums over 64 sites are added into FP32 running sums (two-level
 // summation); the diquark tiles are generated in shared memory and never stored.  Then the two Wick contractions
 //   W1 = -sum_ijk B_xi[j,i,k]^T g5 P_- B_eta[i,j,k],  W2 = -sum_ijk B_xi[k,i,j]^T g5 P_- B_eta[i,j,k].
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
 #include "internal.h"
 
 using namespace lq;
@@ -267,14 +271,26 @@ extern "C" int lqcd_nucleon_blocks(lqcd_lattice* L, const lqcd_slab* slab, int n
   const int S3 = (int)L->S3;
   const long long nsite = (long long)(slab->t1 - slab->t0 + 1) * S3;
   const int nti = (n + TI - 1) / TI, ntj = (n + TJ - 1) / TJ, ntk = (n + TK - 1) / TK;
-  static bool attr = false;  // static + dynamic shared memory exceed the 48 KB default
-  if (!attr) {
-    if (cudaFuncSetAttribute(k_nucleon_block, cudaFuncAttributeMaxDynamicSharedMemorySize, TOT_BYTES) != cudaSuccess) {
+  {
+    // static + dynamic shared memory exceed the 48 KB default: opt in once per device
+    static std::mutex mu;
+    static std::vector<int> opted;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
       cudaGetLastError();
-      lq_set_error("nucleon_blocks: shared-memory opt-in failed");
+      lq_set_error("nucleon_blocks: no current device");
       return LQCD_ECUDA;
     }
-    attr = true;
+    std::lock_guard<std::mutex> lk(mu);
+    if (std::find(opted.begin(), opted.end(), dev) == opted.end()) {
+      if (cudaFuncSetAttribute(k_nucleon_block, cudaFuncAttributeMaxDynamicSharedMemorySize, TOT_BYTES) !=
+          cudaSuccess) {
+        cudaGetLastError();
+        lq_set_error("nucleon_blocks: shared-memory opt-in failed");
+        return LQCD_ECUDA;
+      }
+      opted.push_back(dev);
+    }
   }
   k_nucleon_block<<<dim3((unsigned)(nti * ntj), (unsigned)ntk, (unsigned)n_t), 256, TOT_BYTES, (cudaStream_t)stream>>>(
       n, nsite, (const double2*)s, conj, S3, (long long)(t0 - slab->t0) * S3, S3, (double2*)B);
