@@ -375,22 +375,38 @@ def multilevel_nucleon(B_xi_levels: torch.Tensor, B_eta_levels: torch.Tensor, st
 class DomainPseudofermionAction(torch.autograd.Function):
     """S(omega) = phi^dag (D_L^dag D_L)^{-1} phi with U_mu(x) -> exp(i omega^a_mu(x) T_a) U_mu(x).
 
-    forward(omega, lattice, dom, field, phi, params) evaluates S at omega = 0
-    (omega is a zero tensor [V,4,8] standing for the Lie-algebra coordinates
-    of every link) with one D^dag solve; backward recomputes X and Y with two
-    solves and returns grad_S * F, F the link force from the CUDA kernels.
-    Nothing of size V is kept between forward and backward.
+    forward(omega, lattice, dom, field, phi, params, store) evaluates S at
+    omega = 0 (omega is a zero tensor [V,4,8] standing for the Lie-algebra
+    coordinates of every link); backward returns grad_S * F, F the link force
+    from the CUDA kernels.  Two ways to get F:
+      store=True:  forward already solves for X and Y and computes F, which is
+                   kept for backward (2 solves in all, one [V,4,8] FP64 tensor
+                   held in between);
+      store=False: forward solves D^dag only (S = |Y|^2) and backward
+                   recomputes X and Y (3 solves, nothing of size V held);
+      store=None:  store when F and three times its size of headroom fit in
+                   the device's free memory, else recompute.
     """
 
     @staticmethod
-    def forward(ctx, omega, lattice: Lattice, dom, field: int, phi: torch.Tensor, params=None):
-        _, S, _ = lattice.link_force(phi, dom, field, params, want_force=False)
-        ctx.lattice, ctx.dom, ctx.field, ctx.params = lattice, dom, field, params
-        ctx.save_for_backward(phi)
+    def forward(ctx, omega, lattice: Lattice, dom, field: int, phi: torch.Tensor, params=None, store=None):
+        if store is None:
+            free, _ = torch.cuda.mem_get_info(omega.device)
+            store = 4 * lattice.V * 4 * 8 * 8 < free
+        ctx.lattice, ctx.dom, ctx.field, ctx.params, ctx.store = lattice, dom, field, params, bool(store)
+        if store:
+            F, S, _ = lattice.link_force(phi, dom, field, params, want_force=True)
+            ctx.save_for_backward(phi, F)
+        else:
+            _, S, _ = lattice.link_force(phi, dom, field, params, want_force=False)
+            ctx.save_for_backward(phi)
         return torch.tensor(S, dtype=torch.float64, device=omega.device)
 
     @staticmethod
     def backward(ctx, grad_S):
-        (phi,) = ctx.saved_tensors
-        F, _, _ = ctx.lattice.link_force(phi, ctx.dom, ctx.field, ctx.params, want_force=True)
-        return grad_S * F, None, None, None, None, None
+        if ctx.store:
+            _, F = ctx.saved_tensors
+        else:
+            (phi,) = ctx.saved_tensors
+            F, _, _ = ctx.lattice.link_force(phi, ctx.dom, ctx.field, ctx.params, want_force=True)
+        return grad_S * F, None, None, None, None, None, None

@@ -168,7 +168,10 @@ def test_link_force_matches_oracle(csw, dom):
     assert np.abs(F - F_ref).max() <= 1e-9 * np.abs(F_ref).max()
 
 
-def test_autograd_function_returns_force():
+@pytest.mark.parametrize("store", [None, True, False])
+def test_autograd_function_returns_force(store):
+    """Both ways of the autograd Function (force kept from forward, or X and Y
+    recomputed in backward) give the link force of the C ABI."""
     lqcd = _lq()
     dims = (4, 4, 4, 4)
     U = inputs.random_su3_field(dims, 0.4, 61)
@@ -177,7 +180,7 @@ def test_autograd_function_returns_force():
     phi = _cuda(inputs.gaussian_spinor(dims, 62)[0][inputs.slab_sites(dims, 0, 2)])
     omega = torch.zeros((lat.V, 4, 8), dtype=torch.float64, device="cuda", requires_grad=True)
     params = lqcd.SolverParams(tol=1e-13)
-    S = lqcd.DomainPseudofermionAction.apply(omega, lat, (0, 2), 0, phi, params)
+    S = lqcd.DomainPseudofermionAction.apply(omega, lat, (0, 2), 0, phi, params, store)
     S.backward()
     F, S2, _ = lat.link_force(phi, (0, 2), 0, params)
     assert abs(S.item() - S2) <= 1e-12 * abs(S2)
