@@ -1,0 +1,68 @@
+"""Host-side helpers of bench.py that the reported JSON line depends on (no GPU):
+the comment-free kernel hash that keys the committed DRAM-traffic record, the
+lookup of that record, and the summary of the clock samples taken during the
+timed region (throttle reasons flagged)."""
+import json
+import os
+import shutil
+
+import pytest
+
+import bench
+
+CSRC = os.path.join(bench.ROOT, "paper_1612_06424_gb300", "csrc")
+
+
+def test_strip_comments():
+    src = "int a = 1;  // one\n// a whole comment line\n\n  float b;   \n"
+    assert bench._strip_comments(src) == "int a = 1;\n  float b;"
+
+
+@pytest.fixture
+def fake_root(tmp_path, monkeypatch):
+    d = tmp_path / "paper_1612_06424_gb300" / "csrc"
+    d.mkdir(parents=True)
+    for f in ("common.cuh", "dslash.cuh"):
+        shutil.copy(os.path.join(CSRC, f), d / f)
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    return tmp_path
+
+
+def test_kernel_hash_ignores_comments_only(fake_root):
+    h0 = bench._kernel_hash()
+    p = fake_root / "paper_1612_06424_gb300" / "csrc" / "dslash.cuh"
+    p.write_text(p.read_text() + "\n// a note that changes no code\n")
+    assert bench._kernel_hash() == h0
+    p.write_text(p.read_text() + "\nnamespace lq { constexpr int k_extra = 1; }\n")
+    assert bench._kernel_hash() != h0
+
+
+def test_traffic_record_used_only_for_matching_source(fake_root):
+    rec = {"32": {"kernel_hash": bench._kernel_hash(), "dram_bytes_per_launch": 123456}}
+    path = fake_root / "profiles" / "dslash_traffic.json"
+    path.write_text(json.dumps(rec))
+    assert bench._traffic(32) == 123456.0
+    assert bench._traffic(16) is None
+    rec["32"]["kernel_hash"] = "0" * 16
+    path.write_text(json.dumps(rec))
+    assert bench._traffic(32) is None
+
+
+def test_clock_summary_flags_throttle_reasons():
+    c = bench.Clocks()
+    rows = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "0, 2055, 2070, 1350.0, 0x4, Not Active, Not Active, Not Active, Active",
+            "0, 1980, 2070, 1390.5, 0x8, Active, Not Active, Not Active, Not Active"]
+    c.f.write("\n".join(rows) + "\n")
+    s = c.summary()
+    os.unlink(c.f.name)
+    assert s["sm_mhz"] == 2055.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
+    assert s["reasons"] == ["hw_slowdown", "sw_power_cap"]
+
+
+def test_clock_summary_without_samples():
+    c = bench.Clocks()
+    s = c.summary()
+    os.unlink(c.f.name)
+    assert s["reasons"] == ["unsampled"] and s["sm_mhz"] is None
