@@ -3,30 +3,35 @@
 
 Metric: seconds per 12-source factorized propagator (factorized part of
 Sec. 3 plus the full-lattice correction) at true FP64 residual 1e-10, and
-the Wilson-clover Dslash's achieved HBM bandwidth against the measured peak.
+the Wilson-clover stencil's achieved HBM bandwidth against the measured peak.
 
-Workload (one "step"): the 16^3x32 lattice, random SU(3) links
-U = exp(i 0.4 H) (a stand-in for the paper's quenched ensembles), Wilson-clover
-kappa = 0.1300, c_sw = 1.0, open time boundary; Gamma = t 0..13,
-DeltaGamma = 14..17 (frozen), Gamma* = 14..31; 12 point sources at
-x = (2,0,0,0).  A step loads the gauge field (even-odd packing, compression,
-clover blocks and their inverses), solves the Gamma, Gammabar, Gamma* domain
-systems and the full lattice for all 12 sources (batched), assembles
-fact = D_Gamma^{-1} on Gamma and -D_Gamma*^{-1} D_dGamma* D_Gammabar^{-1} on
-Gamma*, and corr = D^{-1} - fact.
+Default workload (one "step"): the 48^3x96 lattice, Wilson-clover kappa =
+0.1350, c_sw = 1.0, open time boundary; Gamma = t 0..43, DeltaGamma = 44..51
+(frozen), Gamma* = 44..95; 12 point sources at x = (2,0,0,0).  Eight
+inner-level gauge fields (the level-0 field U = exp(i 0.4 H), a stand-in for
+the paper's quenched ensembles, with the links of Gamma and of t 52..95
+redrawn; links starting or ending in the frozen slab kept) stay resident in
+HBM; step i takes field i mod 8.  A step loads that field (even-odd packing,
+compression, clover blocks and their inverses), solves the Gamma, Gammabar,
+Gamma* domain systems and the full lattice for all 12 sources (batched),
+assembles fact = D_Gamma^{-1} on Gamma and -D_Gamma*^{-1} D_dGamma*
+D_Gammabar^{-1} on Gamma*, and corr = D^{-1} - fact.  The propagators of a
+field (fact + corr, 49 GB) and its packed copy (23 GB) leave no room for a
+second field's, so the fields run one per step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision 64|32|16]
   python bench.py --impl reference     # the CPU oracle on the host cores
+  python bench.py --workload factorized_16x32  # 16^3x32 factorized propagator + correction
   python bench.py --workload batched_32x64   # 8 slabs x 12 sources x 16 inner-level fields
   python bench.py --workload force_24x48     # domain pseudofermion link force, 4 domains
-  python bench.py --workload factorized_48x96  # 8 inner-level fields x 12 sources, 48^3x96
 
 Multi-GPU (torchrun): every rank computes its own propagators (its own
-gauge field, independent problems); there is no collective on the data path.
+gauge fields, independent problems); there is no collective on the data path.
 """
 from __future__ import annotations
 
 import argparse
+import concurrent.futures as cf
 import hashlib
 import json
 import os
@@ -41,6 +46,19 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 WL = {
+    "name": "48^3x96 Wilson-clover factorized propagator + correction, 8 inner-level fields",
+    "dims": (96, 48, 48, 48),
+    "kappa": 0.135,
+    "csw": 1.0,
+    "eps": 0.4,
+    "gamma": (0, 43),
+    "delta": (44, 51),
+    "gamma_star": (44, 95),
+    "x_src": (2, 0, 0, 0),
+    "tol": 1e-10,
+    "fields": 8,
+}
+WL16 = {
     "name": "16^3x32 Wilson-clover factorized propagator + correction",
     "dims": (32, 16, 16, 16),
     "kappa": 0.13,
@@ -54,6 +72,12 @@ WL = {
 }
 METRIC = "s per 12-source factorized propagator @ res 1e-10 (Dslash HBM GB/s vs peak in roofline)"
 UNIT = "s/propagator"
+# kernels of one BiCGStab iteration as lqcd_stencil_bench numbers them, with their launches per iteration
+HOP_KERNELS = {1: ("k_hop_clinv (A_ee^-1 D_hop, first half of D^)", 2), 2: ("k_hop_lin + <r0,v>", 1),
+               3: ("k_hop_lin + <t,s>, |t|^2", 1)}
+BLAS_KERNELS = {4: ("k_bicg_s_w (s = r - alpha v)", 1), 5: ("k_bicg_xr_w (x, r update + 2 dots)", 1),
+                6: ("k_bicg_p_w (p update)", 1)}
+DTYPE = {64: "f64", 32: "f32+f64", 16: "f16+f32+f64"}
 
 
 def _args():
@@ -65,8 +89,9 @@ def _args():
     ap.add_argument("--precision", type=int, default=32, choices=[64, 32, 16])
     ap.add_argument("--no-fp64-form", action="store_true", help="skip timing the plain FP64 form")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="factorized_16x32",
-                    choices=["factorized_16x32", "batched_32x64", "force_24x48", "factorized_48x96",
+    ap.add_argument("--no-extra", action="store_true", help="skip the 16^3x32 figures of the default line")
+    ap.add_argument("--workload", default="factorized_48x96",
+                    choices=["factorized_48x96", "factorized_16x32", "batched_32x64", "force_24x48",
                              "disconnected_64x24", "projection_64x24"])
     ap.add_argument("--fields", type=int, default=8, help="inner-level fields of factorized_48x96")
     ap.add_argument("--sources", type=int, default=100, help="Gaussian sources of disconnected_64x24")
@@ -101,15 +126,16 @@ def _kernel_hash():
     return h.hexdigest()[:16]
 
 
-def _traffic(precision):
-    """Per-launch DRAM bytes of the hop kernel from the committed ncu summary,
-    or None if absent or taken on a different kernel source."""
+def _traffic(precision, kernel):
+    """DRAM bytes per system site of one kernel of the solver's iteration (lqcd_stencil_bench
+    numbering) from the committed ncu record, or None if absent or taken on a different
+    kernel source."""
     try:
         with open(os.path.join(ROOT, "profiles", "dslash_traffic.json")) as fh:
             t = json.load(fh)
-        e = t.get(str(precision))
+        e = t.get(f"{precision}:{kernel}")
         if e and e.get("kernel_hash") == _kernel_hash():
-            return float(e["dram_bytes_per_launch"])
+            return float(e["dram_bytes_per_launch"]) / float(e["system_sites"])
     except Exception:
         pass
     return None
@@ -166,75 +192,175 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
-_ORACLE_ITERS = {}
+def _stage_sites(wl):
+    """Sites of each solve of a factorized propagator (Gamma, Gammabar, Gamma*, full)."""
+    s3 = wl["dims"][1] * wl["dims"][2] * wl["dims"][3]
+    T = wl["dims"][0]
+    slabs = {"gamma": wl["gamma"], "gamma_bar": (0, wl["delta"][1]), "gamma_star": wl["gamma_star"],
+             "full": (0, T - 1)}
+    return {k: (b - a + 1) * s3 for k, (a, b) in slabs.items()}
 
 
-def _oracle_iterations(op):
-    """Iterations the oracle's own BiCGStab needs on this workload to residual
-    1e-10: one column solved on Gamma (t 0..13) to 1e-5, doubled (the residual
-    falls geometrically), measured once per process (about 20 s)."""
-    from paper_1612_06424_gb300 import inputs
+class OracleIterations:
+    """The oracle's own BiCGStab iteration count to residual 1e-10 for one column of the
+    16^3x32 Gamma system (kappa 0.13, c_sw 1, t 0..13, source (2,0,0,0), spin-colour 0),
+    counted in a background host thread (the oracle's C code runs without the GIL) so that
+    it overlaps the GPU work; about half a minute on one core."""
 
-    if "gamma" not in _ORACLE_ITERS:
-        eta = inputs.point_sources(WL["dims"], WL["x_src"])[0]
+    def __init__(self):
+        self.result = None
+        self.seconds = None
+        self._ex = cf.ThreadPoolExecutor(1)
+        self._fut = self._ex.submit(self._run)
+
+    def _run(self):
+        import oracle
+        from paper_1612_06424_gb300 import inputs
+
+        U = inputs.random_su3_field(WL16["dims"], WL16["eps"], 1)
+        op = oracle.Operator(WL16["dims"], U, WL16["kappa"], WL16["csw"])
+        eta = inputs.point_sources(WL16["dims"], WL16["x_src"])[0]
         t0 = time.perf_counter()
-        _, its, _ = op.solve(eta, *WL["gamma"], tol=1e-5)
-        _ORACLE_ITERS["gamma"] = 2 * its
-        _ORACLE_ITERS["seconds"] = time.perf_counter() - t0
-    return _ORACLE_ITERS["gamma"]
+        _, its, _ = op.solve(eta, *WL16["gamma"], tol=1e-10)
+        self.seconds = time.perf_counter() - t0
+        return its
+
+    def get(self):
+        its = self._fut.result()
+        self._ex.shutdown()
+        return its
 
 
-def _cpu_baseline(U, sample_seconds=8.0):
-    """The oracle (plain FP64 C, one thread) on the host cores, for one
-    12-source factorized propagator with correction on the 16^3x32 workload,
-    from a bounded sample: the time of one oracle D application on each solve
-    domain (Gamma, Gammabar, Gamma*, full lattice), measured, times
-    2 applications per BiCGStab iteration x the oracle's iteration count
-    (measured on Gamma, one column, residual 1e-10) x 12 columns."""
+SAMPLE_SLICES = 2  # time slices of the workload's field in the oracle's timing sample
+
+
+def _oracle_sample_operator(U_slab, dims, kappa, csw):
+    """The oracle's operator on the sample lattice (periodic in time, so that every site does
+    all eight hops like the bulk of the workload's lattice); returns (op, clover build seconds)."""
     import oracle
+
+    oracle.gamma(0)  # the oracle's static tables, filled once before any thread starts
+    t0 = time.perf_counter()
+    op = oracle.Operator(dims, U_slab, kappa, csw, oracle.BC_PERIODIC)
+    return op, time.perf_counter() - t0
+
+
+def _oracle_apply_sample(op, psis, threads, min_seconds=4.0):
+    """Wall seconds of the oracle's D (plain FP64 C, as it stands) applied to the 12 distinct spinor
+    columns psis at once, one column per host thread (`threads` threads); repeated until
+    min_seconds have passed (at least once).  Returns seconds per round of 12 applications."""
+    rounds = 0
+    with cf.ThreadPoolExecutor(threads) as ex:
+        t0 = time.perf_counter()
+        while rounds < 1 or time.perf_counter() - t0 < min_seconds:
+            list(ex.map(lambda c: op.apply(psis[c]), range(12)))
+            rounds += 1
+        return (time.perf_counter() - t0) / rounds
+
+
+def _cpu_threads():
+    n = os.cpu_count() or 1
+    try:
+        n = len(os.sched_getaffinity(0))
+    except Exception:
+        pass
+    return max(1, min(12, n))
+
+
+def _cpu_model():
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                k = line.split(":")[0].strip().lower()
+                if k in ("model name", "cpu part", "hardware"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+
+    return platform.machine()
+
+
+def _cpu_cost(wall_round, sample_sites, wl, iters):
+    """Extrapolated oracle seconds for one 12-source factorized propagator + correction: every
+    column runs on its own thread (12 columns per round), and a column's solves apply D twice per
+    BiCGStab iteration plus twice for the initial and final true residuals, on each solve's sites."""
+    sites = _stage_sites(wl)
+    apps = sum(sites[k] * (2 * iters[k] + 2) for k in sites)
+    return wall_round * apps / sample_sites
+
+
+def _cpu_baseline(U_sample, wl, gpu_iters, ratio, ora_its, ora_secs, gpu16_its):
+    """The oracle on the host cores for the default workload, from a bounded sample: its D applied
+    to 12 columns at once on U_sample, the first SAMPLE_SLICES time slices of a step's field
+    (host array), measured, times the
+    site-applications of the propagator's four solves, with the oracle's iteration count taken as
+    the GPU's count on each solve times the oracle/GPU iteration ratio measured on the 16^3x32
+    Gamma system (one column, residual 1e-10)."""
     from paper_1612_06424_gb300 import inputs
 
-    dims = WL["dims"]
-    op = oracle.Operator(dims, U, WL["kappa"], WL["csw"])
-    its = _oracle_iterations(op)
-    psi = inputs.gaussian_spinor(dims, 99)[0]
-    T = dims[0]
-    groups = {"gamma": WL["gamma"], "gamma_bar": (0, WL["delta"][1]), "gamma_star": WL["gamma_star"], "full": (0, T - 1)}
-    per = sample_seconds / len(groups)
-    t_apply = {}
-    for k, (a, b) in groups.items():
-        t0 = time.perf_counter()
-        n = 0
-        while time.perf_counter() - t0 < per or n < 2:
-            op.apply(psi, a, b)
-            n += 1
-        t_apply[k] = (time.perf_counter() - t0) / n
-    total = sum(12 * 2 * its * t for t in t_apply.values())
-    return {"value": total, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"oracle D applications on each solve domain ({', '.join(f'{k} {v:.3f} s' for k, v in t_apply.items())}) "
-                      f"x 2 x {its} oracle BiCGStab iterations to 1e-10 (twice those measured for one column on Gamma "
-                      f"to 1e-5, {_ORACLE_ITERS.get('seconds', 0):.0f} s) x 12 columns; extrapolated"}
+    ns = SAMPLE_SLICES
+    dims_s = (ns,) + tuple(wl["dims"][1:])
+    s3 = wl["dims"][1] * wl["dims"][2] * wl["dims"][3]
+    op, t_cl = _oracle_sample_operator(U_sample, dims_s, wl["kappa"], wl["csw"])
+    threads = _cpu_threads()
+    wall = _oracle_apply_sample(op, inputs.gaussian_spinor(dims_s, 97, 12), threads)
+    iters = {k: int(round(v * ratio)) for k, v in gpu_iters.items()}
+    value = _cpu_cost(wall, ns * s3, wl, iters)
+    return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "cpu_model": _cpu_model(),
+            "nproc": os.cpu_count(),
+            "sample": f"oracle D on 12 columns at once ({threads} threads) over the first {ns} time slices of the "
+                      f"48^3x96 field: {wall:.2f} s per round of 12 (clover build {t_cl:.1f} s, not counted); "
+                      f"x the site-applications of the four solves per column (2 per iteration + 2) with "
+                      f"oracle iteration counts {iters} = GPU counts {gpu_iters} x {ratio:.3f}, the oracle/GPU "
+                      f"ratio on the 16^3x32 Gamma system (oracle {ora_its} iterations to 1e-10 in "
+                      f"{ora_secs:.0f} s on one core, GPU {gpu16_its}); extrapolated"}
 
 
 def run_reference(args):
-    """--impl reference: the CPU oracle, as it stands, on the host cores."""
+    """--impl reference: the CPU oracle, as it stands, on the host cores.  Each step is the bounded
+    sample of _cpu_baseline (the oracle's D on 12 columns at once over a few time slices of a
+    48^3x96-shaped field); the iteration count of every solve is the oracle's own, measured once on the
+    16^3x32 Gamma system (kappa 0.13): a lower bound for the kappa 0.135 systems of the workload."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     from paper_1612_06424_gb300 import inputs
 
-    U = inputs.random_su3_field(WL["dims"], WL["eps"], 1)
+    wl = WL
+    ns = SAMPLE_SLICES
+    dims_s = (ns,) + tuple(wl["dims"][1:])
+    s3 = wl["dims"][1] * wl["dims"][2] * wl["dims"][3]
+    its_job = OracleIterations()
+    op, _ = _oracle_sample_operator(inputs.random_su3_field(dims_s, wl["eps"], 7), dims_s, wl["kappa"], wl["csw"])
+    threads = _cpu_threads()
+    ora_its = its_job.get()
+    iters = {k: ora_its for k in ("gamma", "gamma_bar", "gamma_star", "full")}
+
+    psis = inputs.gaussian_spinor(dims_s, 97, 12)
+
+    def one():
+        wall = _oracle_apply_sample(op, psis, threads, min_seconds=0.0)
+        return _cpu_cost(wall, ns * s3, wl, iters), wall
+
     for _ in range(args.warmup):
-        _cpu_baseline(U, sample_seconds=2.0)
-    vals = [_cpu_baseline(U, sample_seconds=4.0) for _ in range(args.steps)]
-    v = statistics.median(x["value"] for x in vals)
-    cb = dict(vals[-1])
-    cb["value"] = v
+        one()
+    t0 = time.perf_counter()
+    vals = [one() for _ in range(args.steps)]
+    elapsed = time.perf_counter() - t0
+    v = statistics.median(x[0] for x in vals)
+    cb = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "cpu_model": _cpu_model(),
+          "nproc": os.cpu_count(),
+          "sample": f"per step: oracle D on 12 columns at once ({threads} threads) over {ns} time slices of a "
+                    f"48^3x96-shaped field (median {statistics.median(x[1] for x in vals):.2f} s per round), x the "
+                    f"site-applications of the four solves with the oracle's iteration count {ora_its} (measured "
+                    f"to 1e-10 on the 16^3x32 Gamma system in {its_job.seconds:.0f} s); extrapolated; "
+                    f"the {args.steps} sampled steps took {elapsed:.0f} s"}
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WL["name"], "dims": list(WL["dims"]), "kappa": WL["kappa"], "c_sw": WL["csw"]},
+        "config": {"workload": wl["name"], "dims": list(wl["dims"]), "kappa": wl["kappa"], "c_sw": wl["csw"]},
         "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0}))
 
@@ -363,54 +489,299 @@ def run_force(args):
     lat.close()
 
 
-def run_factorized_48(args):
-    """48^3x96, kappa 0.1350, c_sw 1.0: Gamma = t 0..43, frozen DeltaGamma = 44..51,
-    Gamma* = 44..95; 12 point sources at (2,0,0,0) on each of `--fields` inner-level
-    fields (the level-0 field with the links of Gamma and of t 52..95 redrawn; links
-    starting or ending in the frozen slab kept), factorized propagator plus the
-    full-lattice correction per field.  The fields run one after another (each
-    packed field is 23 GB; fact + corr are 49 GB)."""
+def _dist_setup():
+    """(world, rank, local rank, torch.distributed or None) of a torchrun launch (NCCL for N > 1)."""
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local, dist
+
+
+def _timed(step, prec, K, W, dist):
+    """W untimed steps, then K timed steps between a barrier and a synchronize on both sides,
+    CUDA events on the current stream; returns (ms of the K steps, max over ranks; kernel
+    launches of this rank in the timed region; statistics of the last step)."""
+    import torch
+
+    from paper_1612_06424_gb300 import lqcd
+
+    for _ in range(W):
+        step(prec)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    l0 = lqcd.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    stats = None
+    for _ in range(K):
+        stats = step(prec)
+    e1.record()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms = _max_over_ranks(e0.elapsed_time(e1), dist)
+    return ms, lqcd.kernel_launches() - l0, stats
+
+
+def _iteration_roofline(lat, doms, fields, precision, reps=10):
+    """The kernels of one BiCGStab iteration, each timed alone on the solver's batch `doms`
+    (lqcd_stencil_bench): the hop kernels (2 x k_hop_clinv, k_hop_lin with <r0,v>, k_hop_lin with
+    <t,s>, |t|^2) weighted by their launches per iteration give the stencil roofline; the three
+    vector updates give the BLAS figures."""
+    peak, peak_kind = _peaks()
+    sites = float(sum((b - a + 1) * lat.S3 // 2 for a, b in doms))  # system sites per parity
+
+    def group(kernels):
+        per, tot_b, tot_t, traffic, have_traffic = {}, 0.0, 0.0, 0.0, True
+        for k, (name, n_launch) in kernels.items():
+            ms, by, fl = lat.stencil_bench(doms, fields, precision, k, reps)
+            t = _traffic(precision, k)
+            per[name] = {"ms": round(ms, 4), "alg_bytes": by, "GB/s": round(by / (ms * 1e-3) / 1e9, 1),
+                         "frac": round(by / (ms * 1e-3) / 1e9 / peak, 4), "launches_per_iteration": n_launch,
+                         "tflops": round(fl / (ms * 1e-3) / 1e12, 3),
+                         "dram_bytes": None if t is None else round(t * sites)}
+            tot_b += n_launch * by
+            tot_t += n_launch * ms
+            if t is None:
+                have_traffic = False
+            else:
+                traffic += n_launch * t * sites
+        achieved = tot_b / (tot_t * 1e-3) / 1e9
+        return per, achieved, tot_b, tot_t, (traffic if have_traffic else None)
+
+    hop, hop_gbs, hop_b, hop_t, hop_traffic = group(HOP_KERNELS)
+    blas, blas_gbs, blas_b, blas_t, _ = group(BLAS_KERNELS)
+    n_hop = sum(n for _, n in HOP_KERNELS.values())
+    roofline = {"bound": "hbm", "achieved": round(hop_gbs, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(hop_gbs / peak, 4),
+                "traffic": None if hop_traffic is None else round(hop_traffic / n_hop),
+                "peak_kind": peak_kind,
+                "kernel": f"FP{precision} stencil as the solver launches it: 2 x k_hop_clinv + 2 x k_hop_lin (fused "
+                          f"reductions) per BiCGStab iteration, time-weighted, on {len(doms)} systems of the "
+                          f"solver's batch; achieved and traffic per launch (mean of the 4)",
+                "alg_bytes_per_launch": round(hop_b / n_hop), "ms_per_launch": round(hop_t / n_hop, 4),
+                "per_kernel": hop}
+    blas_out = {"GB/s": round(blas_gbs, 1), "frac": round(blas_gbs / peak, 4), "ms_per_iteration": round(blas_t, 4),
+                "alg_bytes_per_iteration": blas_b, "per_kernel": blas,
+                "iteration_share_of_time": round(blas_t / (blas_t + hop_t), 3)}
+    return roofline, blas_out
+
+
+def _factorized_16x32(args, dist, world, rank, K, W, with_fp64):
+    """The 16^3x32 factorized propagator + correction (kappa 0.13, c_sw 1, Gamma 0..13, DeltaGamma
+    14..17, Gamma* 14..31, source (2,0,0,0)): a step loads the field and runs the propagator."""
+    import torch
+
+    from paper_1612_06424_gb300 import inputs, lqcd
+
+    wl = WL16
+    U = inputs.random_su3_field(wl["dims"], wl["eps"], _rank_seed(rank))
+    U_dev = torch.from_numpy(U).cuda()
+    lat = lqcd.Lattice(wl["dims"], "open")
+    fact = torch.empty((1, 12, lat.V, 4, 3), dtype=torch.complex128, device="cuda")
+    corr = torch.empty_like(fact)
+
+    def step(prec, U_src=None):
+        lat.set_gauge(U_dev if U_src is None else U_src, wl["kappa"], wl["csw"])
+        _, _, st = lat.factorized_propagators(wl["gamma"], wl["gamma_star"], wl["x_src"], [0], delta=wl["delta"],
+                                              corr=True, params=lqcd.SolverParams(tol=wl["tol"], precision=prec),
+                                              out=(fact, corr))
+        return st[0]
+
+    out = {"workload": wl["name"]}
+    with Clocks() as clk:
+        ms, launches, st = _timed(step, args.precision, K, W, dist)
+    out.update({"value": ms / 1e3 / (K * world), "unit": UNIT, "steps": K, "warmup": W, "dtype": DTYPE[args.precision],
+                "iters": {k: v["iters"] for k, v in st.items()}, "cycles": {k: v["cycles"] for k, v in st.items()},
+                "true_residual": max(v["true_residual"] for v in st.values()), "gpu_launches": int(launches),
+                "clocks": clk.summary()})
+    if with_fp64 and args.precision != 64:
+        ms64, _, st64 = _timed(step, 64, 2, 1, dist)
+        out["fp64_form"] = {"value": ms64 / 1e3 / (2 * world), "unit": UNIT, "dtype": "f64",
+                            "iters": {k: v["iters"] for k, v in st64.items()},
+                            "true_residual": max(v["true_residual"] for v in st64.values())}
+    doms = [(0, wl["delta"][1])] * 12 + [wl["gamma"]] * 12
+    lat.set_gauge(U_dev, wl["kappa"], wl["csw"])
+    out["roofline"], out["blas"] = _iteration_roofline(lat, doms, [0] * 24, args.precision, reps=30)
+    out["_U"] = U
+    out["_lat"], out["_fact"], out["_corr"], out["_step"] = lat, fact, corr, step
+    return out
+
+
+def run_factorized_16x32(args):
+    """--workload factorized_16x32: the 16^3x32 figures as their own JSON line."""
+    import torch
+
+    from paper_1612_06424_gb300 import build
+
+    world, rank, _, dist = _dist_setup()
+    build.build()
+    r = _factorized_16x32(args, dist, world, rank, args.steps, args.warmup, not args.no_fp64_form)
+    lat = r.pop("_lat")
+    for k in ("_U", "_fact", "_corr", "_step"):
+        r.pop(k)
+    if rank == 0:
+        line = {"metric": METRIC, "n_gpus": world, "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": None, "data": "synthetic",
+                "ms_per_step": r["value"] * 1e3 * world,
+                "config": {"workload": WL16["name"], "dims": list(WL16["dims"]), "kappa": WL16["kappa"],
+                           "c_sw": WL16["csw"], "residual": WL16["tol"], "l2": "working set > L2 (no flush)"}}
+        line.update(r)
+        line.pop("workload")
+        print(json.dumps(line))
+    lat.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    del torch
+
+
+def run_headline(args):
+    """The default workload (module docstring): 48^3x96, 12 sources x 8 inner-level fields, one
+    field per step, plus the full-lattice correction, residual 1e-10."""
     import torch
 
     from paper_1612_06424_gb300 import build, inputs, lqcd
 
+    world, rank, _, dist = _dist_setup()
     build.build()
-    dims = (96, 48, 48, 48)
-    G, DL, GS = (0, 43), (44, 51), (44, 95)
+    wl = WL
+    dims = wl["dims"]
+    T = dims[0]
+    G, DL, GS = wl["gamma"], wl["delta"], wl["gamma_star"]
+    nf = args.fields
+    want_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
+    ora = OracleIterations() if want_cpu else None  # host thread; overlaps the GPU work
+    t0 = time.time()
+    seed = _rank_seed(rank)
+    U0 = inputs.random_su3_field_device(dims, wl["eps"], 6 + seed, device="cuda")
+    Uf = inputs.inner_level_fields_device(U0, dims, [G, (DL[1] + 1, T - 1)], nf, wl["eps"], 7 + seed, frozen=DL)
+    del U0
+    torch.cuda.empty_cache()
+    t_gen = time.time() - t0
     lat = lqcd.Lattice(dims, "open")
     V = lat.V
-    fact = torch.empty((12, V, 4, 3), dtype=torch.complex128, device="cuda")
+    fact = torch.empty((1, 12, V, 4, 3), dtype=torch.complex128, device="cuda")
     corr = torch.empty_like(fact)
-    params = lqcd.SolverParams(tol=1e-10, precision=args.precision)
-    t_fields, t_solve, stats = 0.0, 0.0, []
-    U0 = inputs.random_su3_field_device(dims, 0.4, 7, device="cuda")
+    counter = [0]
+
+    def step(prec, U_src=None):
+        j = counter[0] % nf
+        counter[0] += 1
+        lat.set_gauge(Uf[j] if U_src is None else U_src, wl["kappa"], wl["csw"])
+        _, _, st = lat.factorized_propagators(G, GS, wl["x_src"], [0], delta=DL, corr=True,
+                                              params=lqcd.SolverParams(tol=wl["tol"], precision=prec),
+                                              out=(fact, corr))
+        return st[0]
+
     with Clocks() as clk:
-        for j in range(args.fields):
-            t0 = time.time()
-            Uj = inputs.inner_level_fields_device(U0, dims, [G, (52, 95)], args.fields, 0.4, 8, frozen=DL,
-                                                  field_ids=[j])
-            lat.set_gauge(Uj, 0.135, 1.0)
-            del Uj
-            torch.cuda.synchronize()
-            t1 = time.time()
-            _, _, st = lat.factorized_propagator(G, GS, (2, 0, 0, 0), delta=DL, corr=True, params=params,
-                                                 out=(fact, corr))
-            torch.cuda.synchronize()
-            t_fields += t1 - t0
-            t_solve += time.time() - t1
-            stats.append(st)
-    print(json.dumps({
-        "metric": "s per 12-source factorized propagator + correction @ res 1e-10 (48^3x96)",
-        "value": t_solve / args.fields, "unit": "s/propagator", "n_gpus": 1, "steps": args.fields, "warmup": 0,
-        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": {64: "f64", 32: "f32+f64", 16: "f16+f32+f64"}[args.precision], "data": "synthetic",
-        "config": {"workload": "48^3x96 factorized propagator, inner-level fields", "dims": list(dims), "kappa": 0.135,
-                   "c_sw": 1.0, "gamma": list(G), "delta": list(DL), "gamma_star": list(GS), "fields": args.fields},
-        "field_setup_s_per_field": t_fields / args.fields,
-        "iters": [{k: v["iters"] for k, v in st.items()} for st in stats],
-        "true_residual_max": max(v["true_residual"] for st in stats for v in st.values()),
-        "clocks": clk.summary()}))
+        ms, launches, stats = _timed(step, args.precision, args.steps, args.warmup, dist)
+    clocks = clk.summary()
+    value = ms / 1e3 / (args.steps * world)
+    gpu_iters = {k: v["iters"] for k, v in stats.items()}
+
+    # plain FP64 form on the same box and workload (one field)
+    fp64_form = None
+    if not args.no_fp64_form and args.precision != 64:
+        ms64, _, st64 = _timed(step, 64, 1, 0, dist)
+        fp64_form = {"value": ms64 / 1e3 / world, "unit": UNIT, "dtype": "f64", "fields": 1,
+                     "iters": {k: v["iters"] for k, v in st64.items()},
+                     "true_residual": max(v["true_residual"] for v in st64.values())}
+
+    # end to end through the public API: the step's field from pinned host memory in, both
+    # propagators out to host memory (pinned when the host can lock that much)
+    U_h = Uf[0].cpu()
+    try:
+        U_h = U_h.pin_memory()
+        fact_h = torch.empty(fact.shape, dtype=fact.dtype, pin_memory=True)
+        corr_h = torch.empty(corr.shape, dtype=corr.dtype, pin_memory=True)
+        pinned = True
+    except RuntimeError:
+        fact_h = torch.empty(fact.shape, dtype=fact.dtype)
+        corr_h = torch.empty(corr.shape, dtype=corr.dtype)
+        pinned = False
+    Ke = max(1, min(args.steps, 2))
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(Ke):
+        step(args.precision, U_src=U_h.numpy())
+        fact_h.copy_(fact, non_blocking=pinned)
+        corr_h.copy_(corr, non_blocking=pinned)
+    e1.record()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    e2e_ms = _max_over_ranks(e0.elapsed_time(e1), dist)
+    e2e = {"value": e2e_ms / 1e3 / (Ke * world), "unit": UNIT, "h2d_bytes_per_step": int(U_h.numel() * 16),
+           "d2h_bytes_per_step": int(fact.numel() * 16 * 2), "steps": Ke, "pinned_host": pinned}
+    del fact_h, corr_h
+
+    # roofline of the stencil as the solver launches it, on the Gamma* batch of a step
+    lat.set_gauge(Uf[0], wl["kappa"], wl["csw"])
+    roofline, blas = _iteration_roofline(lat, [GS] * 12, [0] * 12, args.precision)
+    fp64_peak = lqcd.fma_peak(64)
+    m64, _, f64 = lat.stencil_bench([GS] * 12, [0] * 12, 64, 0, 3)
+    dslash64 = {"TFLOP/s": round(f64 / (m64 * 1e-3) / 1e12, 3), "ms": round(m64, 3), "bound": "alu",
+                "fp64_fma_peak_tflops_measured": round(fp64_peak, 3),
+                "alu_frac": round(f64 / (m64 * 1e-3) / 1e12 / fp64_peak, 3)}
+    s3 = dims[1] * dims[2] * dims[3]
+    U_sample = Uf[0][:SAMPLE_SLICES * s3].cpu().numpy() if want_cpu else None
     lat.close()
+    del fact, corr
+    torch.cuda.empty_cache()
+
+    extra = None
+    if rank == 0 and world == 1 and not args.no_extra:
+        del Uf
+        torch.cuda.empty_cache()
+        r = _factorized_16x32(args, None, 1, 0, 5, 3, True)
+        r.pop("_lat").close()
+        for k in ("_U", "_fact", "_corr", "_step"):
+            r.pop(k)
+        extra = r
+
+    cpu = None
+    if want_cpu:
+        ora_its = ora.get()
+        gpu16 = (extra or {}).get("fp64_form", {}).get("iters", {}).get("gamma") or (extra or {}).get("iters", {}).get(
+            "gamma")
+        ratio = ora_its / gpu16 if gpu16 else 1.0
+        cpu = _cpu_baseline(U_sample, wl, gpu_iters, ratio, ora_its, ora.seconds or 0.0, gpu16)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
+            "config": {"workload": wl["name"], "dims": list(dims), "kappa": wl["kappa"], "c_sw": wl["csw"],
+                       "eps": wl["eps"], "gamma": list(G), "delta": list(DL), "gamma_star": list(GS),
+                       "x_src": list(wl["x_src"]), "sources": 12, "inner_level_fields": nf,
+                       "fields_per_step": 1,
+                       "precision": {64: "fp64", 32: "fp32 inner BiCGStab + fp64 defect correction",
+                                     16: "fp16 vectors/links (fp32 norm) inner + fp64 defect correction"}[
+                           args.precision],
+                       "residual": wl["tol"], "l2": "inputs larger than L2 (no flush)",
+                       "parallelism": f"replicas x{world} (independent propagators)"},
+            "true_residual": max(v["true_residual"] for v in stats.values()),
+            "iters": gpu_iters, "cycles": {k: v["cycles"] for k, v in stats.items()},
+            "fp64_form": fp64_form, "e2e": e2e, "roofline": roofline, "blas": blas,
+            "dslash_fp64": dslash64, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": int(launches),
+            "setup_s": round(t_gen, 1), "factorized_16x32": extra,
+        }
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
 
 
 def _oracle_disconnected_sample(U, dims, kappa, doms, iters, sample_seconds=12.0):
@@ -441,7 +812,7 @@ def _oracle_disconnected_sample(U, dims, kappa, doms, iters, sample_seconds=12.0
 
 def run_disconnected(args):
     """64x24^3 Wilson (c_sw = 0), kappa 0.1360, open time boundaries: the stochastic
-    disconnected traces of Sec. 4.1 with `--sources` Gaussian sources (100 in the paper) on
+    disconnected traces of Sec. 5 with `--sources` Gaussian sources (100 in the paper) on
     Gamma = t 0..32 and Gamma* = 33..63 (Dirichlet blocks) and on the full lattice, all
     solved together; eight (kappa D_hop) hops and per-slice contractions on the GPU."""
     import numpy as np
@@ -503,7 +874,7 @@ def run_disconnected(args):
 
 def run_projection(args):
     """64x24^3 Wilson (c_sw = 0), kappa 0.1360, open time boundaries: the quark-line cut of
-    Sec. 3.3 with the Sec. 5 setup for Delta = 8: Gammabar = t 0..31 (Gamma = 0..23,
+    Sec. 3.3 with the Sec. 6 setup for Delta = 8: Gammabar = t 0..31 (Gamma = 0..23,
     DeltaGamma = 24..31), Gamma* = 24..63; N_m = `--modes` (120 in the paper) projection
     vectors from 10 inverse iterations on t 16..31, cut on slice 23; the factors xi, eta
     (2 N_m solves) and the projected case-II propagator for 12 point sources at (4,0,0,0).
@@ -588,157 +959,10 @@ def main():
     args = _args()
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload == "batched_32x64":
-        return run_batched(args)
-    if args.workload == "force_24x48":
-        return run_force(args)
-    if args.workload == "disconnected_64x24":
-        return run_disconnected(args)
-    if args.workload == "projection_64x24":
-        return run_projection(args)
-    if args.workload == "factorized_48x96":
-        return run_factorized_48(args)
-    import numpy as np
-    import torch
-
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    from paper_1612_06424_gb300 import build, inputs, lqcd
-
-    build.build()
-    dims = WL["dims"]
-    U = inputs.random_su3_field(dims, WL["eps"], _rank_seed(rank))
-    U_dev = torch.from_numpy(U).cuda()
-    lat = lqcd.Lattice(dims, "open")
-    V = lat.V
-    fact = torch.empty((12, V, 4, 3), dtype=torch.complex128, device="cuda")
-    corr = torch.empty_like(fact)
-
-    def step(prec, U_src=None):
-        lat.set_gauge(U_dev if U_src is None else U_src, WL["kappa"], WL["csw"])
-        _, _, st = lat.factorized_propagator(WL["gamma"], WL["gamma_star"], WL["x_src"], delta=WL["delta"],
-                                             corr=True, params=lqcd.SolverParams(tol=WL["tol"], precision=prec),
-                                             out=(fact, corr))
-        return st
-
-    def timed(prec, K, W):
-        for _ in range(W):
-            step(prec)
-        torch.cuda.synchronize()
-        barrier()
-        l0 = lqcd.kernel_launches()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        stats = None
-        for _ in range(K):
-            stats = step(prec)
-        e1.record()
-        torch.cuda.synchronize()
-        barrier()
-        ms = _max_over_ranks(e0.elapsed_time(e1), dist)
-        launches = lqcd.kernel_launches() - l0
-        return ms, launches, stats
-
-    # headline: the requested precision
-    with Clocks() as clk:
-        ms, launches, stats = timed(args.precision, args.steps, args.warmup)
-    clocks = clk.summary()
-    value = ms / 1e3 / (args.steps * world)
-    worst_res = max(s["true_residual"] for s in stats.values())
-
-    # plain FP64 form on the same box (context for the mixed-precision speed-up)
-    fp64_form = None
-    if not args.no_fp64_form and args.precision != 64:
-        ms64, _, st64 = timed(64, max(1, min(args.steps, 2)), 1)
-        fp64_form = {"value": ms64 / 1e3 / (max(1, min(args.steps, 2)) * world), "unit": UNIT, "dtype": "f64",
-                     "iters": {k: v["iters"] for k, v in st64.items()},
-                     "true_residual": max(s["true_residual"] for s in st64.values())}
-
-    # end to end through the public API: host field in, host propagators out
-    U_pin = torch.from_numpy(U).pin_memory()
-    fact_h = torch.empty(fact.shape, dtype=fact.dtype, pin_memory=True)
-    corr_h = torch.empty(corr.shape, dtype=corr.dtype, pin_memory=True)
-    Ke = max(1, min(args.steps, 3))
-    torch.cuda.synchronize()
-    barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(Ke):
-        step(args.precision, U_src=U_pin.numpy())
-        fact_h.copy_(fact, non_blocking=True)
-        corr_h.copy_(corr, non_blocking=True)
-    e1.record()
-    torch.cuda.synchronize()
-    barrier()
-    e2e_ms = _max_over_ranks(e0.elapsed_time(e1), dist)
-    e2e = {"value": e2e_ms / 1e3 / (Ke * world), "unit": UNIT, "h2d_bytes_per_step": int(U.nbytes),
-           "d2h_bytes_per_step": int(fact.numel() * 16 * 2)}
-
-    # roofline of the dominant kernel: the hop kernel of the inner solves,
-    # on the stage-A batch (12 x Gammabar + 12 x Gamma systems) it runs on
-    doms = [(0, WL["delta"][1])] * 12 + [WL["gamma"]] * 12
-    lat.set_gauge(U_dev, WL["kappa"], WL["csw"])
-    d_ms, d_bytes, d_flops = lat.dslash_bench(doms, [0] * 24, args.precision, 50)
-    peak, peak_kind = _peaks()
-    achieved = d_bytes / (d_ms * 1e-3) / 1e9
-    traffic = _traffic(args.precision)
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
-                "kernel": f"k_hop_lin<{args.precision}> (Wilson-clover hop + clover + axpy, even-odd)",
-                "ms_per_launch": round(d_ms, 5), "alg_bytes_per_launch": d_bytes,
-                "tflops": round(d_flops / (d_ms * 1e-3) / 1e12, 3)}
-    dslash_other = {}
-    fp64_peak = lqcd.fma_peak(64)
-    for p in (64, 32, 16):
-        if p == args.precision:
-            continue
-        m, b, f = lat.dslash_bench(doms, [0] * 24, p, 20)
-        dslash_other[str(p)] = {"GB/s": round(b / (m * 1e-3) / 1e9, 1), "TFLOP/s": round(f / (m * 1e-3) / 1e12, 3),
-                                "ms": round(m, 5)}
-        if p == 64:  # FP64 is bound by the FP64 FMA rate on this GPU, not by HBM
-            dslash_other["64"].update({"bound": "alu", "fp64_fma_peak_tflops_measured": round(fp64_peak, 3),
-                                       "alu_frac": round(f / (m * 1e-3) / 1e12 / fp64_peak, 3)})
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = _cpu_baseline(U)
-
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None,
-            "dtype": {64: "f64", 32: "f32+f64", 16: "f16+f32+f64"}[args.precision], "data": "synthetic",
-            "config": {"workload": WL["name"], "dims": list(dims), "kappa": WL["kappa"], "c_sw": WL["csw"],
-                       "eps": WL["eps"], "gamma": list(WL["gamma"]), "delta": list(WL["delta"]),
-                       "gamma_star": list(WL["gamma_star"]), "x_src": list(WL["x_src"]), "sources": 12,
-                       "precision": {64: "fp64", 32: "fp32 inner BiCGStab + fp64 defect correction",
-                                     16: "fp16 vectors/links (fp32 norm) inner + fp64 defect correction"}[args.precision],
-                       "residual": WL["tol"], "l2": "working set > L2 (no flush)",
-                       "parallelism": f"replicas x{world} (independent propagators)"},
-            "true_residual": worst_res,
-            "iters": {k: v["iters"] for k, v in stats.items()},
-            "cycles": {k: v["cycles"] for k, v in stats.items()},
-            "fp64_form": fp64_form,
-            "e2e": e2e, "roofline": roofline, "dslash_other_precisions": dslash_other,
-            "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": int(launches),
-        }
-        print(json.dumps(line))
-    lat.close()
-    if dist is not None:
-        dist.destroy_process_group()
+    runs = {"batched_32x64": run_batched, "force_24x48": run_force, "disconnected_64x24": run_disconnected,
+            "projection_64x24": run_projection, "factorized_16x32": run_factorized_16x32,
+            "factorized_48x96": run_headline}
+    return runs[args.workload](args)
 
 
 if __name__ == "__main__":

@@ -10,7 +10,7 @@
  *   - its domain (block) operators D_L on time slabs with Dirichlet boundaries,
  *     the exact sub-blocks of D of eq. block_inverse (Sec. 3) and Sec. 5;
  *   - solves of D_L psi = eta and D psi = eta (Sec. 5: "solutions of the
- *     Dirac equation"; Sec. 4.1: cost counted in Dirac-operator inversions);
+ *     Dirac equation", and its cost counted in Dirac-operator inversions);
  *   - the factorized propagator of Sec. 3 (eqs. quark_prop_I, quark_prop_II)
  *     and its correction, corr = D^{-1} - fact (eq. observable_factorization);
  *   - the link force of S = phi^dag (D_L^dag D_L)^{-1} phi, the domain-local
@@ -177,6 +177,23 @@ int lqcd_factorized_propagator(lqcd_lattice *lat, const lqcd_split *split, const
                                double *fact, double *corr, const lqcd_solver_params *params,
                                lqcd_solver_stats *stats, void *stream);
 
+/* lqcd_factorized_propagator for n_fields gauge fields at once (the level-1
+ * fields of Sec. 2.2 eq. multilevel_estimator, whose factors the two-level
+ * average needs field by field): field_ids[j] < loaded fields, j < n_fields.
+ * fact: device [n_fields][12][V][4][3] complex128; corr: the same shape or
+ * NULL; stats: host array of 4 n_fields entries, stats[4 j + k] as in
+ * lqcd_factorized_propagator for field j, or NULL.  The 12 n_fields systems
+ * of each kind are solved in one batch (consecutive waves when they exceed
+ * free device memory), in four stages: Gamma; Gammabar started from the
+ * Gamma solution (zero on DeltaGamma); Gamma* from the boundary source; the
+ * full lattice started from fact.  A starting iterate changes iteration
+ * counts only: every system stops at ||eta - D psi|| <= tol ||eta|| in FP64.
+ * Errors: LQCD_EBADARG, LQCD_ENOFIELD, LQCD_ENOMEM, LQCD_ENOTCONVERGED,
+ * LQCD_ECUDA. */
+int lqcd_factorized_propagators(lqcd_lattice *lat, const lqcd_split *split, const int x_src[4], int n_fields,
+                                const int *field_ids, double *fact, double *corr, const lqcd_solver_params *params,
+                                lqcd_solver_stats *stats, void *stream);
+
 /* Link force of S = phi^dag (D_L^dag D_L)^{-1} phi for the slab dom on field
  * `field`: force[i][mu][a] = dS/domega for U_mu(x_i) -> exp(i omega T_a)
  * U_mu(x_i), T_a = lambda_a / 2 (Gell-Mann), i.e.
@@ -191,7 +208,7 @@ int lqcd_factorized_propagator(lqcd_lattice *lat, const lqcd_split *split, const
 int lqcd_link_force(lqcd_lattice *lat, const lqcd_slab *dom, int field, const double *phi, double *force,
                     double *action, const lqcd_solver_params *params, lqcd_solver_stats *stats, void *stream);
 
-/* Projection vectors of the quark-line cut (Sec. 5: N_m orthonormal vectors
+/* Projection vectors of the quark-line cut (Sec. 6: N_m orthonormal vectors
  * from inverse iterations of the Dirac operator on a slab around the
  * boundary).  Starting from v0 (device, n_modes slab vectors on dom back to
  * back), each of the n_iter iterations solves D_L w_i = v_i (L = dom, all
@@ -234,7 +251,7 @@ int lqcd_projected_factors(lqcd_lattice *lat, const lqcd_split *split, int field
 int lqcd_projected_propagator(lqcd_lattice *lat, const lqcd_split *split, int n_modes, const double *xi,
                               const double *eta, const int x_src[4], double *fact, void *stream);
 
-/* Nucleon blocks of the factorized nucleon propagator (Sec. 3.3 eq.
+/* Nucleon blocks of the factorized nucleon propagator (Sec. 4.2 eq.
  * nucleon_prop_factorized) for n fields s_i (device [n] slab vectors on
  * `slab`, complex128; conj = 1 uses conj(s_i), e.g. the xi of
  * lqcd_projected_factors, whose conjugate is the paper's row xi_i^T), for the
@@ -269,7 +286,7 @@ int lqcd_nucleon_contract(int n, int n_x, const double *B_xi, int n_y, const dou
 int lqcd_level_mean(long long size, int count, const double *in, double *out, void *stream);
 
 /* Stochastic estimator of the disconnected traces of Sec. 4.1 (eq.
- * stochastic_estimator) on each slab L_d = doms[d], d < n_doms, of field
+ * stochastic_estimator of Sec. 5) on each slab L_d = doms[d], d < n_doms, of field
  * `field` (Dirichlet blocks of Sec. 3, or the whole lattice for doms[d] =
  * 0..T-1), all sources and slabs solved together:
  *   trace[i][d][x0] = sum_{xvec} eta_i^dag(x) [(kappa D_hop)^8 D_L^{-1} g5 eta_i](x)
@@ -307,6 +324,27 @@ int lqcd_dslash_bench(lqcd_lattice *lat, int n_sys, const lqcd_slab *doms, const
                       int reps, double *ms_per_launch, double *bytes_per_launch, double *flops_per_launch,
                       void *stream);
 
+/* Timing hook of one kernel of the solver's BiCGStab iteration (no
+ * counterpart in the paper: a measurement aid), on the batch of systems
+ * (slab doms[k] on field field_ids[k]) with synthetic vectors, in the
+ * solver's launch shape, timed like lqcd_dslash_bench.  kernel:
+ *   0  out_o = A_oo y_o - 1/4 D_hop x_e            (3 spinor passes)
+ *   1  out_e = A_ee^{-1} D_hop x_o                 (2 passes; first half of D^)
+ *   2  kernel 0 with the reduction <r0, out>       (4 passes)
+ *   3  kernel 0 with <out, y> and |out|^2          (3 passes)
+ *   4  s = r - alpha v                             (3 passes)
+ *   5  x += alpha p + omega s, r = s - omega t, <r0, r>, |r|^2   (7 passes)
+ *   6  p = r + beta (p - omega v)                  (4 passes)
+ * bytes_per_launch: algorithmic bytes = passes x spinor bytes per system
+ * site, plus (8 links + 1 clover block) per distinct field site of the
+ * slabs for kernels 0-3.  flops_per_launch: per system site, hop 1320 +
+ * site-diagonal block (504 with clover, else 24) + epilogue / reductions
+ * (kernels 0-3), or the vector arithmetic (kernels 4-6).  Errors:
+ * LQCD_EBADARG, LQCD_ENOFIELD, LQCD_ENOMEM, LQCD_ECUDA. */
+int lqcd_stencil_bench(lqcd_lattice *lat, int n_sys, const lqcd_slab *doms, const int *field_ids, int precision,
+                       int kernel, int reps, double *ms_per_launch, double *bytes_per_launch,
+                       double *flops_per_launch, void *stream);
+
 /* Measured FMA throughput of the current GPU in TFLOP/s (bits = 64 or 32;
  * no counterpart in the paper: the ALU roofline of the FP64 kernels).  One
  * launch of 8 independent FMA chains per thread on 8 blocks per SM, timed
@@ -328,8 +366,11 @@ int lqcd_fma_peak(int bits, double *tflops, void *stream);
  * pointer table) lives in one file-scope device array of
  * LQCD_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
  * the process exits.  The caller still owns and passes in / out (device).
- * Limit: the slab may hold at most (LQCD_NOALLOC_SCRATCH_BYTES - 512) / 384
- * sites (43 688, e.g. a 16^3 x 10 slab); larger slabs return LQCD_EBADARG.
+ * Limit: the scratch needs 512 + 768 n bytes for a slab of n sites per
+ * parity, so the slab may hold at most 2 floor((LQCD_NOALLOC_SCRATCH_BYTES -
+ * 512) / 768) = 43 688 sites (e.g. a 16^3 x 10 slab); larger slabs return
+ * LQCD_EBADARG.  The descriptor and the in / out pointers reach the scratch
+ * array as kernel arguments of a one-thread set-up kernel.
  * The first call on a device looks up the array's device address (with that
  * device current) and caches it; make that first call before any stream
  * capture.  All calls share the one array and it keeps the last call's

@@ -239,7 +239,7 @@ def link_force(op: Operator, phi: np.ndarray, t0: int, t1: int, tol: float = 1e-
 
 def disconnected_contract(op: Operator, etas: np.ndarray, psis: np.ndarray, t0: int, t1: int,
                           hops: int = 8) -> np.ndarray:
-    """The contraction half of eq. stochastic_estimator (Sec. 4.1), given the solutions
+    """The contraction half of eq. stochastic_estimator (Sec. 5), given the solutions
     psi_i = D_L^{-1} gamma_5 eta_i on the slab L = t0..t1 (plain Wilson operator):
         t(x0) = (1/n_src) sum_i sum_{x in slice x0} eta_i^dag(x) [(kappa D_hop)^hops psi_i](x),
     kappa D_hop psi = psi - 2 kappa D_L psi (since 2 kappa D = 1 - kappa D_hop).
@@ -262,7 +262,7 @@ def disconnected_contract(op: Operator, etas: np.ndarray, psis: np.ndarray, t0: 
 def disconnected_trace(op: Operator, etas: np.ndarray, t0: int, t1: int, tol: float = 1e-13,
                        hops: int = 8) -> np.ndarray:
     """Stochastic estimate of sum_x tr{gamma_5 D_L^{-1}(x,x)} per time slice x0 of the
-    slab L = t0..t1 (Sec. 4.1, eq. stochastic_estimator), plain Wilson operator:
+    slab L = t0..t1 (Sec. 5, eq. stochastic_estimator), plain Wilson operator:
         t(x0) = (1/n_src) sum_i sum_{x in slice x0} eta_i^dag(x) [(kappa D_hop)^8 D_L^{-1} gamma_5 eta_i](x).
     etas: (n_src, V, 4, 3) sources (only their slab part is used).  Returns complex (T,) with
     zeros outside the slab."""
@@ -278,7 +278,7 @@ def disconnected_trace(op: Operator, etas: np.ndarray, t0: int, t1: int, tol: fl
 
 
 # --------------------------------------------------------------------------
-# Quark-line projection (Sec. 3.3 eqs. projection, quark_prop_II_proj; Sec. 5)
+# Quark-line projection (Sec. 3.3 eqs. projection, quark_prop_II_proj; Sec. 6)
 
 def orthonormalize(W: np.ndarray) -> np.ndarray:
     """The orthonormal factor Q of W = Q R (columns of W (n, N) linearly independent), with R
@@ -299,7 +299,7 @@ def spin_project_plus(v: np.ndarray) -> np.ndarray:
 def boundary_modes(op: Operator, v0: np.ndarray, t0: int, t1: int, g1: int, n_iter: int,
                    tol: float = 1e-13) -> np.ndarray:
     """N_m orthonormal projection vectors on the time slice g1 (the external boundary of Gamma*),
-    from n_iter inverse iterations of D on the slab L = t0..t1 (Sec. 5): starting from the slab
+    from n_iter inverse iterations of D on the slab L = t0..t1 (Sec. 6): starting from the slab
     part of v0 (N_m, V, 4, 3), each iteration solves W_i = D_L^{-1} V_i for every column and
     orthonormalises, V = orthonormalize(W); the result is phi = orthonormalize(P_+ V|_{g1})
     (reading: the vectors live in the 6 L^3-dimensional space that D_dGamma* reads, Sec. 3.3).
@@ -364,7 +364,7 @@ def projected_propagator(op: Operator, split: Split, xi: np.ndarray, eta: np.nda
 
 
 # --------------------------------------------------------------------------
-# Nucleon blocks on projected quark lines (Sec. 3.3 eq. nucleon_prop_factorized)
+# Nucleon blocks on projected quark lines (Sec. 4.2 eq. nucleon_prop_factorized)
 
 def charge_conjugation() -> np.ndarray:
     """C = gamma_0 gamma_2 (real, antisymmetric, unitary, C gamma_mu C^{-1} = -gamma_mu^T in this basis)."""

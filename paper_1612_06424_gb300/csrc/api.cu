@@ -159,19 +159,6 @@ struct BatchStore {
     CK(cudaMemcpyAsync(sc.p, h_sc.data(), sizeof(lq::SolverScal) * b.nsys, cudaMemcpyHostToDevice, st));
     return 0;
   }
-  // A view of systems [k0, k0+n) (same pools, offsets from the descriptors).
-  Batch view(int k0, int n) const {
-    Batch v = b;
-    v.nsys = n;
-    v.sys = b.sys + k0;
-    v.active = b.active + k0;
-    v.sc = b.sc + k0;
-    long long maxn = 0;
-    for (int k = k0; k < k0 + n; k++) maxn = std::max(maxn, (long long)h_sys[k].n);
-    v.max_n = maxn;
-    v.partial = b.partial + (size_t)k0 * b.pstride * 4;  // layout [sys][pstride][4]
-    return v;
-  }
 };
 
 // FP64 pool of `count` vectors of a batch (each total*12 double2).
@@ -219,9 +206,11 @@ struct SolveOut {
 };
 
 // Solve D_L x = b (dag: D_L^dag x = b) for every system of the batch.
-// b_e, b_o, x_e, x_o: FP64 even / odd pools of the batch.
+// b_e, b_o, x_e, x_o: FP64 even / odd pools of the batch.  With guess, x_o
+// holds a starting iterate of the odd half on entry (the even half is always
+// reconstructed from it at the end); else the solve starts from x = 0.
 int solve_core(lqcd_lattice* L, BatchStore& B, bool dag, const lqcd_solver_params& prm, double2* b_e, double2* b_o,
-               double2* x_e, double2* x_o, SolveOut& out, cudaStream_t st) {
+               double2* x_e, double2* x_o, SolveOut& out, cudaStream_t st, bool guess = false) {
   Batch& b = B.b;
   const int n = b.nsys;
   const int P = prm.precision == 16 ? 16 : prm.precision == 32 ? 32 : 64;
@@ -279,7 +268,7 @@ int solve_core(lqcd_lattice* L, BatchStore& B, bool dag, const lqcd_solver_param
   // prepare: bh_o = b_o + 1/2 H_oe A_ee^{-1} b_e
   RC(lq_hop_clinv(64, dag, clov, L, b, none, v64(b_e), v64(t64), 0.0, 1.0, st));
   RC(lq_hop_lin(64, dag, clov, lq::RED_NONE, L, b, 1, v64(t64), none, v64(b_o), none, v64(bh_o), 0.5, 0.0, 1.0, st));
-  CK(cudaMemsetAsync(x_o, 0, sizeof(double2) * (size_t)b.total * 12, st));
+  if (!guess) CK(cudaMemsetAsync(x_o, 0, sizeof(double2) * (size_t)b.total * 12, st));
 
   std::vector<int> outer(n, 1);
   for (int k = 0; k < n; k++)
@@ -289,10 +278,10 @@ int solve_core(lqcd_lattice* L, BatchStore& B, bool dag, const lqcd_solver_param
   std::vector<int> stall(n, 0);
   for (int cycle = 0;; cycle++) {
     // true residual of the preconditioned system: r64 = bh_o - Dhat x_o (FP64);
-    // at the first cycle x_o = 0 and r64 = bh_o needs no operator
+    // at the first cycle without a guess x_o = 0 and r64 = bh_o needs no operator
     B.h_active = outer;
     RC(B.push_active(st));
-    if (cycle == 0) {
+    if (cycle == 0 && !guess) {
       CK(cudaMemcpyAsync(r64, bh_o, sizeof(double2) * (size_t)b.total * 12, cudaMemcpyDeviceToDevice, st));
       RC(lq_norm2_64(b, r64, st));
       RC(lq_finalize(lq::FIN_NORM, b, 0, 0, 12, st));
@@ -476,10 +465,14 @@ struct SysSpec {
   int role;   // caller-defined (which source / which output)
   int col;    // spin-colour column 3*s + c of a point source
   int4 xsrc;  // point-source position
+  int out = 0;  // caller-defined output slot (e.g. field index * 12 + column)
 };
 
 using FillFn = std::function<int(BatchStore& B, int k0, double2* b_e, double2* b_o)>;
 using SinkFn = std::function<int(BatchStore& B, int k0, const double2* x_e, const double2* x_o)>;
+// Writes a starting iterate of the wave's systems into their even / odd pools
+// (only the odd half enters the solve).
+using GuessFn = std::function<int(BatchStore& B, int k0, double2* x_e, double2* x_o)>;
 
 // device bytes per system site (one parity) held during a solve in precision P:
 // 4 caller-side FP64 vectors + 3 solver FP64 vectors + 8 Krylov vectors
@@ -502,24 +495,12 @@ size_t free_device_bytes() {
   return fr;
 }
 
-// Runs of equal role inside [0, n) of a wave starting at k0: f(a, b, role) on [a, b).
-template <typename F>
-int for_role_runs(const std::vector<SysSpec>& sp, int k0, int n, F f) {
-  int a = 0;
-  while (a < n) {
-    int b = a + 1;
-    while (b < n && sp[k0 + b].role == sp[k0 + a].role) b++;
-    RC(f(a, b, sp[k0 + a].role));
-    a = b;
-  }
-  return 0;
-}
-
 // Solve every system of `sp` (D_L x = b, or D_L^dag x = b), in consecutive
 // waves that fit in free device memory (at most prm.max_wave systems each).
 // For each wave: fill its sources, solve, hand the solutions to sink.
 int solve_waves(lqcd_lattice* L, const std::vector<SysSpec>& sp, bool dag, const lqcd_solver_params& prm,
-                const FillFn& fill, const SinkFn& sink, SolveOut& out, cudaStream_t st) {
+                const FillFn& fill, const SinkFn& sink, SolveOut& out, cudaStream_t st,
+                const GuessFn& guess = GuessFn()) {
   const int N = (int)sp.size();
   out.iters.assign(N, 0);
   out.cycles.assign(N, 0);
@@ -551,8 +532,9 @@ int solve_waves(lqcd_lattice* L, const std::vector<SysSpec>& sp, bool dag, const
     Pool64 e;
     RC(e.alloc(B.b, 4, st));
     RC(fill(B, k, e.v(0), e.v(1)));
+    if (guess) RC(guess(B, k, e.v(2), e.v(3)));
     SolveOut o;
-    RC(solve_core(L, B, dag, prm, e.v(0), e.v(1), e.v(2), e.v(3), o, st));
+    RC(solve_core(L, B, dag, prm, e.v(0), e.v(1), e.v(2), e.v(3), o, st, (bool)guess));
     RC(sink(B, k, e.v(2), e.v(3)));
     for (int q = 0; q < w; q++) {
       out.iters[k + q] = o.iters[q];
@@ -566,19 +548,23 @@ int solve_waves(lqcd_lattice* L, const std::vector<SysSpec>& sp, bool dag, const
   return 0;
 }
 
-// Device copies of the per-system point-source columns / positions of [k0, k0+n).
+// Device copies of the per-system point-source columns / positions and
+// output slots of [k0, k0+n).
 struct SrcArrays {
-  DBuf cols, xsrc;
+  DBuf cols, xsrc, outs;
   int upload(const std::vector<SysSpec>& sp, int k0, int n, cudaStream_t st) {
-    std::vector<int> c(n);
+    std::vector<int> c(n), o(n);
     std::vector<int4> x(n);
     for (int q = 0; q < n; q++) {
       c[q] = sp[k0 + q].col;
+      o[q] = sp[k0 + q].out;
       x[q] = sp[k0 + q].xsrc;
     }
     RC(cols.alloc(sizeof(int) * n, st));
+    RC(outs.alloc(sizeof(int) * n, st));
     RC(xsrc.alloc(sizeof(int4) * n, st));
     CK(cudaMemcpyAsync(cols.p, c.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(outs.p, o.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(xsrc.p, x.data(), sizeof(int4) * n, cudaMemcpyHostToDevice, st));
     return 0;
   }
@@ -865,12 +851,28 @@ extern "C" int lqcd_solve_full(lqcd_lattice* L, int n_sys, const int* field_ids,
   return solve_api(L, n_sys, d.data(), field_ids, src, sol, params, stats, stream);
 }
 
-extern "C" int lqcd_factorized_propagator(lqcd_lattice* L, const lqcd_split* split, const int x_src[4], int field,
-                                          double* fact, double* corr, const lqcd_solver_params* params,
-                                          lqcd_solver_stats* stats, void* stream) {
+// Sec. 3 for the fields field_ids[0..n_f): per field and point-source column,
+//   fact = D_Gamma^{-1} eta on Gamma                                  (eq. quark_prop_I)
+//   fact = -D_Gamma*^{-1} D_dGamma* (D_Gammabar^{-1} eta)|_Gamma on Gamma*  (eq. quark_prop_II)
+//   corr = D^{-1} eta - fact                                          (eq. observable_factorization)
+// in four batched stages, each holding the 12 n_f systems of one kind:
+//   A1  Gamma from the point sources (fact on Gamma);
+//   A2  Gammabar from the point sources, started from the Gamma solution
+//       (zero on DeltaGamma): its residual lives on the first slice of
+//       DeltaGamma only; its boundary slice gives chi = D_dGamma* psi|_Gamma;
+//   B   Gamma* from chi (fact on Gamma*);
+//   C   the full lattice from the point sources, started from fact: the
+//       residual eta - D fact vanishes off the two slices next to the cut,
+//       where it is as small as the propagator across the cut.
+// The starting iterates change the iteration counts, not the solutions:
+// every system stops at the same true FP64 residual ||eta - D psi|| <= tol ||eta||.
+extern "C" int lqcd_factorized_propagators(lqcd_lattice* L, const lqcd_split* split, const int x_src[4], int n_f,
+                                           const int* field_ids, double* fact, double* corr,
+                                           const lqcd_solver_params* params, lqcd_solver_stats* stats,
+                                           void* stream) {
   RC(check_lat(L));
-  if (!split || !x_src || !fact) {
-    lq_set_error("factorized_propagator: null argument");
+  if (!split || !x_src || !fact || n_f < 1 || !field_ids) {
+    lq_set_error("factorized_propagators: null argument or n_fields < 1");
     return LQCD_EBADARG;
   }
   const int T = L->dims[0];
@@ -890,104 +892,138 @@ extern "C" int lqcd_factorized_propagator(lqcd_lattice* L, const lqcd_split* spl
       lq_set_error("factorized_propagator: source outside the lattice");
       return LQCD_EBADARG;
     }
-  if (field < 0 || field >= (int)L->fields.size()) {
-    lq_set_error("factorized_propagator: field index not loaded");
-    return LQCD_ENOFIELD;
-  }
+  for (int j = 0; j < n_f; j++)
+    if (field_ids[j] < 0 || field_ids[j] >= (int)L->fields.size()) {
+      lq_set_error("factorized_propagator: field index not loaded");
+      return LQCD_ENOFIELD;
+    }
   const double t_start = now_s();
   cudaStream_t st = (cudaStream_t)stream;
   lqcd_solver_params prm = default_params(params);
   const lqcd_slab Gb = {0, has_delta ? Dl.t1 : G.t1};
+  const lqcd_slab Full = {0, T - 1};
   const bool want_corr = corr != nullptr;
   const int4 xs = make_int4(x_src[0], x_src[1], x_src[2], x_src[3]);
   const long long V = L->V, S3 = L->S3;
-  enum { R_GBAR = 0, R_GAMMA = 1, R_GSTAR = 2, R_FULL = 3 };
+  const size_t col_words = (size_t)V * 12;  // one propagator column (complex128 words)
+  const int NS = 12 * n_f;                  // systems per stage; output slot = field index * 12 + column
 
-  CK(cudaMemsetAsync(fact, 0, sizeof(double2) * 12 * (size_t)V * 12, st));
-  // compact boundary source chi[col][slot][slice site][12] (two time slices)
+  CK(cudaMemsetAsync(fact, 0, sizeof(double2) * (size_t)NS * col_words, st));
+  // compact boundary source chi[slot][2][slice site][12] (two time slices per system)
   DBuf chi;
-  RC(chi.alloc(sizeof(double2) * 12 * 2 * (size_t)S3 * 12, st));
-
-  // stage A: Gammabar (and Gamma) from the 12 point sources (eqs. quark_prop_I, quark_prop_II)
-  std::vector<SysSpec> sa;
-  for (int c = 0; c < 12; c++) sa.push_back(SysSpec{Gb, field, R_GBAR, c, xs});
-  if (has_delta)
-    for (int c = 0; c < 12; c++) sa.push_back(SysSpec{G, field, R_GAMMA, c, xs});
-  FillFn fill_a = [&](BatchStore& B, int k0, double2* be, double2* bo) -> int {
-    SrcArrays s;
-    RC(s.upload(sa, k0, B.b.nsys, st));
-    return lq_point_source(L, B.b, s.cols.as<int>(), s.xsrc.as<int4>(), be, bo, st);
+  RC(chi.alloc(sizeof(double2) * (size_t)NS * 2 * (size_t)S3 * 12, st));
+  auto stage = [&](lqcd_slab dom) {
+    std::vector<SysSpec> sp;
+    for (int j = 0; j < n_f; j++)
+      for (int c = 0; c < 12; c++) {
+        SysSpec q{dom, field_ids[j], 0, c, xs};
+        q.out = 12 * j + c;
+        sp.push_back(q);
+      }
+    return sp;
   };
-  auto write_gamma = [&](BatchStore& B, int k0, int a, int b, const double2* xe, const double2* xo) -> int {
-    std::vector<void*> p;
-    for (int q = a; q < b; q++) p.push_back((double2*)fact + (size_t)sa[k0 + q].col * V * 12 + (size_t)G.t0 * S3 * 12);
+  // natural-order device pointers of slab `dom` inside the columns of `base` for the wave's systems
+  auto col_ptrs = [&](const std::vector<SysSpec>& sp, int k0, int n, double* base, lqcd_slab dom, DBuf& d) -> int {
+    std::vector<void*> p(n);
+    for (int q = 0; q < n; q++) p[q] = (double2*)base + (size_t)sp[k0 + q].out * col_words + (size_t)dom.t0 * S3 * 12;
+    return upload_ptrs(d, p, st);
+  };
+  auto point_fill = [&](const std::vector<SysSpec>& sp) -> FillFn {
+    return [&, sp_ptr = &sp](BatchStore& B, int k0, double2* be, double2* bo) -> int {
+      SrcArrays s;
+      RC(s.upload(*sp_ptr, k0, B.b.nsys, st));
+      return lq_point_source(L, B.b, s.cols.as<int>(), s.xsrc.as<int4>(), be, bo, st);
+    };
+  };
+  // starting iterate read from fact (natural order) on the stage's slab
+  auto fact_guess = [&](const std::vector<SysSpec>& sp, lqcd_slab dom) -> GuessFn {
+    return [&, sp_ptr = &sp, dom](BatchStore& B, int k0, double2* xe, double2* xo) -> int {
+      DBuf d;
+      RC(col_ptrs(*sp_ptr, k0, B.b.nsys, fact, dom, d));
+      return lq_nat_to_eo(L, B.b, d.as<const double2*>(), xe, xo, st);
+    };
+  };
+  auto chi_sink = [&](const std::vector<SysSpec>& sp) {
+    return [&, sp_ptr = &sp](BatchStore& B, int k0, const double2* xe, const double2* xo) -> int {
+      SrcArrays s;
+      RC(s.upload(*sp_ptr, k0, B.b.nsys, st));
+      return lq_boundary_chi(L, B.b, s.outs.as<int>(), G.t1, xe, xo, chi.as<double2>(), st);
+    };
+  };
+
+  // A1: Gamma (eq. quark_prop_I); without an overlap it is also Gammabar
+  const std::vector<SysSpec> sa1 = stage(G);
+  SinkFn sink_a1 = [&](BatchStore& B, int k0, const double2* xe, const double2* xo) -> int {
     DBuf d;
-    RC(upload_ptrs(d, p, st));
-    return lq_eo_to_nat(L, B.view(a, b - a), xe, xo, d.as<double2* const>(), 1.0, st);
+    RC(col_ptrs(sa1, k0, B.b.nsys, fact, G, d));
+    RC(lq_eo_to_nat(L, B.b, xe, xo, d.as<double2* const>(), 1.0, st));
+    if (!has_delta) RC(chi_sink(sa1)(B, k0, xe, xo));
+    return 0;
   };
-  SinkFn sink_a = [&](BatchStore& B, int k0, const double2* xe, const double2* xo) -> int {
-    return for_role_runs(sa, k0, B.b.nsys, [&](int a, int b, int role) -> int {
-      if (role == R_GAMMA) return write_gamma(B, k0, a, b, xe, xo);
-      // Gammabar: chi = D_dGamma* (D_Gammabar^{-1} eta)|_Gamma, and fact on Gamma when DeltaGamma is empty
-      SrcArrays s;
-      RC(s.upload(sa, k0 + a, b - a, st));
-      RC(lq_boundary_chi(L, B.view(a, b - a), s.cols.as<int>(), G.t1, xe, xo, chi.as<double2>(), st));
-      if (!has_delta) RC(write_gamma(B, k0, a, b, xe, xo));
-      return 0;
-    });
-  };
-  SolveOut oa;
+  SolveOut o_g, o_gb, o_gs, o_full;
   const double t_a0 = now_s();
-  RC(solve_waves(L, sa, false, prm, fill_a, sink_a, oa, st));
+  RC(solve_waves(L, sa1, false, prm, point_fill(sa1), sink_a1, o_g, st));
+  // A2: Gammabar, started from the Gamma solution (eq. quark_prop_II)
+  const std::vector<SysSpec> sa2 = stage(Gb);
+  if (has_delta) {
+    SinkFn sink_a2 = chi_sink(sa2);
+    RC(solve_waves(L, sa2, false, prm, point_fill(sa2), sink_a2, o_gb, st, fact_guess(sa2, Gb)));
+  } else {
+    o_gb = o_g;
+  }
   const double t_a1 = now_s();
-
-  // stage B: Gamma* from chi (eq. quark_prop_II), and the full lattice from the point sources
-  std::vector<SysSpec> sb;
-  for (int c = 0; c < 12; c++) sb.push_back(SysSpec{Gs, field, R_GSTAR, c, xs});
-  if (want_corr)
-    for (int c = 0; c < 12; c++) sb.push_back(SysSpec{lqcd_slab{0, T - 1}, field, R_FULL, c, xs});
+  // B: Gamma* from chi; fact on Gamma* is -zeta (eq. quark_prop_II)
+  const std::vector<SysSpec> sb = stage(Gs);
   FillFn fill_b = [&](BatchStore& B, int k0, double2* be, double2* bo) -> int {
-    return for_role_runs(sb, k0, B.b.nsys, [&](int a, int b, int role) -> int {
-      SrcArrays s;
-      RC(s.upload(sb, k0 + a, b - a, st));
-      if (role == R_GSTAR) return lq_chi_to_eo(L, B.view(a, b - a), s.cols.as<int>(), G.t1, chi.as<double2>(), be, bo, st);
-      return lq_point_source(L, B.view(a, b - a), s.cols.as<int>(), s.xsrc.as<int4>(), be, bo, st);
-    });
+    SrcArrays s;
+    RC(s.upload(sb, k0, B.b.nsys, st));
+    return lq_chi_to_eo(L, B.b, s.outs.as<int>(), G.t1, chi.as<double2>(), be, bo, st);
   };
   SinkFn sink_b = [&](BatchStore& B, int k0, const double2* xe, const double2* xo) -> int {
-    return for_role_runs(sb, k0, B.b.nsys, [&](int a, int b, int role) -> int {
-      std::vector<void*> p;
-      for (int q = a; q < b; q++) {
-        if (role == R_GSTAR) p.push_back((double2*)fact + (size_t)sb[k0 + q].col * V * 12 + (size_t)Gs.t0 * S3 * 12);
-        else p.push_back((double2*)corr + (size_t)sb[k0 + q].col * V * 12);
-      }
-      DBuf d;
-      RC(upload_ptrs(d, p, st));
-      // fact on Gamma* is -zeta; corr first receives the full propagator
-      return lq_eo_to_nat(L, B.view(a, b - a), xe, xo, d.as<double2* const>(), role == R_GSTAR ? -1.0 : 1.0, st);
-    });
+    DBuf d;
+    RC(col_ptrs(sb, k0, B.b.nsys, fact, Gs, d));
+    return lq_eo_to_nat(L, B.b, xe, xo, d.as<double2* const>(), -1.0, st);
   };
-  SolveOut ob;
-  const double t_b0 = now_s();
-  RC(solve_waves(L, sb, false, prm, fill_b, sink_b, ob, st));
+  RC(solve_waves(L, sb, false, prm, fill_b, sink_b, o_gs, st));
   const double t_b1 = now_s();
-  if (want_corr) RC(lq_sub_inplace((double2*)corr, (const double2*)fact, 12 * V * 12, st));  // corr = full - fact
+  // C: the full lattice, started from fact; corr first receives D^{-1} eta
+  const std::vector<SysSpec> sc = stage(Full);
+  if (want_corr) {
+    SinkFn sink_c = [&](BatchStore& B, int k0, const double2* xe, const double2* xo) -> int {
+      DBuf d;
+      RC(col_ptrs(sc, k0, B.b.nsys, corr, Full, d));
+      return lq_eo_to_nat(L, B.b, xe, xo, d.as<double2* const>(), 1.0, st);
+    };
+    RC(solve_waves(L, sc, false, prm, point_fill(sc), sink_c, o_full, st, fact_guess(sc, Full)));
+    RC(lq_sub_inplace((double2*)corr, (const double2*)fact, (long long)NS * V * 12, st));  // corr = full - fact
+  }
   CK(cudaStreamSynchronize(st));
   const double secs = now_s() - t_start;
   if (verbose())
-    fprintf(stderr, "[lqcd] factorized: setup %.1f ms, stage A %.1f ms, stage B %.1f ms, assembly %.1f ms\n",
-            1e3 * (t_a0 - t_start), 1e3 * (t_a1 - t_a0), 1e3 * (t_b1 - t_b0), 1e3 * (now_s() - t_b1));
-  if (stats) {
-    fill_stats(oa, has_delta ? 12 : 0, 12, secs, &stats[0]);  // Gamma
-    fill_stats(oa, 0, 12, secs, &stats[1]);                   // Gammabar
-    fill_stats(ob, 0, 12, secs, &stats[2]);                   // Gamma*
-    if (want_corr) fill_stats(ob, 12, 12, secs, &stats[3]);
-    else memset(&stats[3], 0, sizeof(lqcd_solver_stats));
-  }
-  int w = worst_status(oa);
-  if (!w) w = worst_status(ob);
+    fprintf(stderr, "[lqcd] factorized (%d fields): setup %.1f ms, Gamma + Gammabar %.1f ms, Gamma* %.1f ms, "
+            "full %.1f ms\n", n_f, 1e3 * (t_a0 - t_start), 1e3 * (t_a1 - t_a0), 1e3 * (t_b1 - t_a1),
+            1e3 * (now_s() - t_b1));
+  if (stats)
+    for (int j = 0; j < n_f; j++) {
+      lqcd_solver_stats* sj = stats + 4 * j;
+      fill_stats(o_g, 12 * j, 12, secs, &sj[0]);   // Gamma
+      fill_stats(o_gb, 12 * j, 12, secs, &sj[1]);  // Gammabar
+      fill_stats(o_gs, 12 * j, 12, secs, &sj[2]);  // Gamma*
+      if (want_corr) fill_stats(o_full, 12 * j, 12, secs, &sj[3]);
+      else memset(&sj[3], 0, sizeof(lqcd_solver_stats));
+    }
+  int w = worst_status(o_g);
+  if (!w) w = worst_status(o_gb);
+  if (!w) w = worst_status(o_gs);
+  if (!w && want_corr) w = worst_status(o_full);
   if (w) lq_set_error("factorized_propagator: some solves did not reach the tolerance");
   return w;
+}
+
+extern "C" int lqcd_factorized_propagator(lqcd_lattice* L, const lqcd_split* split, const int x_src[4], int field,
+                                          double* fact, double* corr, const lqcd_solver_params* params,
+                                          lqcd_solver_stats* stats, void* stream) {
+  return lqcd_factorized_propagators(L, split, x_src, 1, &field, fact, corr, params, stats, stream);
 }
 
 extern "C" int lqcd_point_propagators(lqcd_lattice* L, int n_sys, const lqcd_slab* doms, const int* field_ids,
@@ -1111,7 +1147,7 @@ extern "C" int lqcd_link_force(lqcd_lattice* L, const lqcd_slab* dom, int field,
   return w;
 }
 
-// Sec. 4.1 eq. stochastic_estimator: per source i and slab d, solve
+// Sec. 5 eq. stochastic_estimator: per source i and slab d, solve
 // D_L psi = g5 eta_i, apply (kappa D_hop)^8 on the slab and contract with
 // eta_i per time slice.  Systems are ordered source-major (k = i * n_doms + d).
 extern "C" int lqcd_disconnected_trace(lqcd_lattice* L, int n_doms, const lqcd_slab* doms, int field, int n_src,
@@ -1241,7 +1277,7 @@ void merge_stats(const SolveOut& o, double secs, lqcd_solver_stats* acc, bool fi
 
 }  // namespace
 
-// Sec. 5: projection vectors on the time slice g1 from n_iter inverse
+// Sec. 6: projection vectors on the time slice g1 from n_iter inverse
 // iterations of D_L, L = dom, each followed by an orthonormalisation; then
 // phi = orthonormalise(P_+ V|_{g1}).
 extern "C" int lqcd_boundary_modes(lqcd_lattice* L, const lqcd_slab* dom, int g1, int field, int n_modes, int n_iter,
@@ -1452,12 +1488,14 @@ extern "C" int lqcd_projected_propagator(lqcd_lattice* L, const lqcd_split* spli
   return 0;
 }
 
-extern "C" int lqcd_dslash_bench(lqcd_lattice* L, int n_sys, const lqcd_slab* doms, const int* field_ids,
-                                 int precision, int reps, double* ms_per_launch, double* bytes_per_launch,
-                                 double* flops_per_launch, void* stream) {
+// Timing hook: one kernel of the solver's BiCGStab iteration on a batch.
+extern "C" int lqcd_stencil_bench(lqcd_lattice* L, int n_sys, const lqcd_slab* doms, const int* field_ids,
+                                  int precision, int kernel, int reps, double* ms_per_launch,
+                                  double* bytes_per_launch, double* flops_per_launch, void* stream) {
   RC(check_lat(L));
-  if (n_sys < 1 || !doms || !field_ids || reps < 1 || (precision != 64 && precision != 32 && precision != 16)) {
-    lq_set_error("dslash_bench: bad arguments");
+  if (n_sys < 1 || !doms || !field_ids || reps < 1 || (precision != 64 && precision != 32 && precision != 16) ||
+      kernel < 0 || kernel > 6) {
+    lq_set_error("stencil_bench: bad arguments");
     return LQCD_EBADARG;
   }
   cudaStream_t st = (cudaStream_t)stream;
@@ -1469,45 +1507,83 @@ extern "C" int lqcd_dslash_bench(lqcd_lattice* L, int n_sys, const lqcd_slab* do
   RC(lq_fill64(tmp.v(0), b.total * 12, 12345u, st));
   RC(lq_fill64(tmp.v(1), b.total * 12, 67890u, st));
   PoolP q;
-  RC(q.alloc(b, precision, 3, st));
+  RC(q.alloc(b, precision, kernel >= 4 ? 6 : 4, st));
   RC(lq_convert(64, precision, b, v64(tmp.v(0)), q.v(0), st));
   RC(lq_convert(64, precision, b, v64(tmp.v(1)), q.v(1), st));
+  RC(lq_convert(64, precision, b, v64(tmp.v(1)), q.v(3), st));
+  if (kernel >= 4) {
+    RC(lq_convert(64, precision, b, v64(tmp.v(0)), q.v(4), st));
+    RC(lq_convert(64, precision, b, v64(tmp.v(1)), q.v(5), st));
+  }
   const bool clov = L->csw != 0.0;
   VecP none;
   B.b.hop_variant = lq_tune_hop(L, B.b, precision, clov, q.v(0), q.v(1), q.v(2), st);
-  for (int w = 0; w < 3; w++)
-    RC(lq_hop_lin(precision, false, clov, lq::RED_NONE, L, b, 1, q.v(0), q.v(1), none, none, q.v(2), -0.25, 1.0, 0.0,
-                  st));
+  // the iteration's kernels on the pools q0..q5 (x, y, out, w, and two more for the BLAS passes)
+  auto launch = [&]() -> int {
+    switch (kernel) {
+      case 0:  // out_o = A_oo y_o - 1/4 D_hop x_e
+        return lq_hop_lin(precision, false, clov, lq::RED_NONE, L, b, 1, q.v(0), q.v(1), none, none, q.v(2), -0.25,
+                          1.0, 0.0, st);
+      case 1:  // out_e = A_ee^{-1} D_hop x_o
+        return lq_hop_clinv(precision, false, clov, L, b, q.v(0), none, q.v(2), 1.0, 0.0, st);
+      case 2:  // v = A_oo p - 1/4 D_hop te, with <r0, v>
+        return lq_hop_lin(precision, false, clov, lq::RED_DOT_W, L, b, 1, q.v(0), q.v(1), none, q.v(3), q.v(2),
+                          -0.25, 1.0, 0.0, st);
+      case 3:  // t = A_oo s - 1/4 D_hop te, with <t, s> and |t|^2
+        return lq_hop_lin(precision, false, clov, lq::RED_TS, L, b, 1, q.v(0), q.v(1), none, none, q.v(2), -0.25,
+                          1.0, 0.0, st);
+      case 4:  // s = r - alpha v
+        return lq_bicg_s(precision, b, q.v(0), q.v(1), q.v(2), st);
+      case 5:  // x += alpha p + omega s, r = s - omega t, <r0, r>, |r|^2
+        return lq_bicg_xr(precision, b, q.v(2), q.v(0), q.v(1), q.v(4), q.v(5), q.v(3), st);
+      default:  // p = r + beta (p - omega v)
+        return lq_bicg_p(precision, b, q.v(2), q.v(0), q.v(1), st);
+    }
+  };
+  for (int w = 0; w < 3; w++) RC(launch());
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   CK(cudaEventRecord(e0, st));
-  for (int r = 0; r < reps; r++)
-    RC(lq_hop_lin(precision, false, clov, lq::RED_NONE, L, b, 1, q.v(0), q.v(1), none, none, q.v(2), -0.25, 1.0, 0.0,
-                  st));
+  for (int r = 0; r < reps; r++) RC(launch());
   CK(cudaEventRecord(e1, st));
   CK(cudaEventSynchronize(e1));
   float ms = 0.f;
   CK(cudaEventElapsedTime(&ms, e0, e1));
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  // algorithmic bytes: 3 spinors per system site (x, y read once, out written),
-  // 8 links + the clover block per distinct site of each field's slabs
+  // algorithmic bytes: the spinor passes per system site (each vector read or
+  // written once), plus 8 links + the clover block per distinct site of each
+  // field's slabs for the hop kernels
   const double S = precision == 64 ? 192.0 : precision == 32 ? 96.0 : 52.0;
   const double Lk = precision == 64 ? 144.0 : precision == 32 ? 48.0 : 24.0;
   const double C = clov ? (precision == 64 ? 576.0 : 288.0) : 0.0;
+  static const double passes[7] = {3, 2, 4, 3, 3, 7, 4};
   double bytes = 0.0, sites = 0.0;
   std::vector<std::vector<char>> used(L->fields.size(), std::vector<char>(L->dims[0], 0));
   for (int k = 0; k < n_sys; k++) {
-    bytes += 3.0 * S * (double)B.h_sys[k].n;
+    bytes += passes[kernel] * S * (double)B.h_sys[k].n;
     sites += (double)B.h_sys[k].n;
     for (int t = doms[k].t0; t <= doms[k].t1; t++) used[field_ids[k]][t] = 1;
   }
-  for (auto& u : used)
-    for (char c : u)
-      if (c) bytes += (8.0 * Lk + C) * (double)L->S3h;
+  if (kernel <= 3)
+    for (auto& u : used)
+      for (char c : u)
+        if (c) bytes += (8.0 * Lk + C) * (double)L->S3h;
+  // flop per system site: hop 1320, site-diagonal block 504 (clover) or 24, epilogue and reductions
+  const double diag = clov ? 504.0 : 24.0;
+  const double flop[7] = {1320.0 + diag + 72.0, 1320.0 + diag + 24.0, 1320.0 + diag + 72.0 + 96.0,
+                          1320.0 + diag + 72.0 + 144.0, 96.0, 432.0, 192.0};
+  const double fl = sites * flop[kernel];
   if (ms_per_launch) *ms_per_launch = ms / reps;
   if (bytes_per_launch) *bytes_per_launch = bytes;
-  if (flops_per_launch) *flops_per_launch = sites * (1320.0 + (clov ? 504.0 : 24.0) + 72.0);
+  if (flops_per_launch) *flops_per_launch = fl;
   return 0;
+}
+
+extern "C" int lqcd_dslash_bench(lqcd_lattice* L, int n_sys, const lqcd_slab* doms, const int* field_ids,
+                                 int precision, int reps, double* ms_per_launch, double* bytes_per_launch,
+                                 double* flops_per_launch, void* stream) {
+  return lqcd_stencil_bench(L, n_sys, doms, field_ids, precision, 0, reps, ms_per_launch, bytes_per_launch,
+                            flops_per_launch, stream);
 }

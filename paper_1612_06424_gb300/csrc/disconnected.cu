@@ -1,4 +1,4 @@
-// Contraction of the stochastic disconnected-trace estimator, Sec. 4.1 eq.
+// Contraction of the stochastic disconnected-trace estimator, Sec. 5 eq.
 // stochastic_estimator: per source, slab and time slice,
 //   t(x0) = sum_{xvec} eta^dag(x) y(x),   y = (kappa D_hop)^8 D_L^{-1} g5 eta,
 // and the mean over the sources.

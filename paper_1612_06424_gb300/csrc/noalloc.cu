@@ -48,6 +48,17 @@ int scratch_address(void** out) {
   return 0;
 }
 
+// Writes the system descriptor and the in / out pointer table into the
+// scratch array.  They arrive as by-value kernel arguments, which the launch
+// copies, so no host buffer has to outlive the call.
+__global__ void k_noalloc_setup(lq::SysDesc s, const void* in, void* out, lq::SysDesc* d_sys, void** d_ptr) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    *d_sys = s;
+    d_ptr[0] = const_cast<void*>(in);
+    d_ptr[1] = out;
+  }
+}
+
 }  // namespace
 
 extern "C" int lqcd_dslash_noalloc(lqcd_lattice* L, int field, const lqcd_slab* dom, int dagger, const double* in,
@@ -99,9 +110,9 @@ extern "C" int lqcd_dslash_noalloc(lqcd_lattice* L, int field, const lqcd_slab* 
   s.n = (int)n;
   s.cb0 = (int)(d.t0 * L->S3h);
   s.off = 0;
-  const void* ptrs[2] = {in, out};
-  cudaError_t e = cudaMemcpyAsync(d_sys, &s, sizeof s, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_ptr, ptrs, sizeof ptrs, cudaMemcpyHostToDevice, st);
+  k_noalloc_setup<<<1, 32, 0, st>>>(s, in, out, d_sys, d_ptr);
+  lq_count_launch();
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     lq_set_error(std::string("dslash_noalloc: ") + cudaGetErrorString(e));
     return LQCD_ECUDA;

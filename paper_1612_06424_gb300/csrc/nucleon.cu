@@ -1,4 +1,4 @@
-// Nucleon blocks on projected quark lines (Sec. 3.3 eq. nucleon_prop_factorized):
+// Nucleon blocks on projected quark lines (Sec. 4.2 eq. nucleon_prop_factorized):
 //   B[i][j][k][alpha](t) = sum_{x in slice t} eps^{abc} {[s_i^T]^a(x) C g5 [s_j]^b(x)} [s_k]^c_alpha(x)
 // as a contraction over (x, c) of the diquark D[(i,j)][(x,c)] with
 // S[(x,c)][(k,alpha)] = s_k(x)[alpha][c]: a dense O(N^3 L^3) product, run on

@@ -1,5 +1,5 @@
 // Quark-line projection (Sec. 3.3 eqs. projection, quark_prop_II_proj) and
-// the inverse-iteration projection vectors of Sec. 5:
+// the inverse-iteration projection vectors of Sec. 6:
 //   * orthonormalisation of N FP64 complex columns by Cholesky QR, twice
 //     (Gram matrix G = V^dag V, G = L L^dag, W = V L^{-dag}; the second pass
 //     restores orthogonality lost to cond(V)^2 in the first);

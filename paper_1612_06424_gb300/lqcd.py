@@ -87,11 +87,14 @@ def lib() -> ctypes.CDLL:
     L.lqcd_solve_full.argtypes = [vp, c, ip, vp, vp, ctypes.POINTER(ParamsC), ctypes.POINTER(StatsC), vp]
     L.lqcd_factorized_propagator.argtypes = [vp, ctypes.POINTER(SplitC), ip, c, vp, vp, ctypes.POINTER(ParamsC),
                                              ctypes.POINTER(StatsC), vp]
+    L.lqcd_factorized_propagators.argtypes = [vp, ctypes.POINTER(SplitC), ip, c, ip, vp, vp,
+                                              ctypes.POINTER(ParamsC), ctypes.POINTER(StatsC), vp]
     L.lqcd_link_force.argtypes = [vp, ctypes.POINTER(Slab), c, vp, vp, dp, ctypes.POINTER(ParamsC),
                                   ctypes.POINTER(StatsC), vp]
     L.lqcd_point_propagators.argtypes = [vp, c, ctypes.POINTER(Slab), ip, ip, ip, vp, ctypes.POINTER(ParamsC),
                                          ctypes.POINTER(StatsC), vp]
     L.lqcd_dslash_bench.argtypes = [vp, c, ctypes.POINTER(Slab), ip, c, c, dp, dp, dp, vp]
+    L.lqcd_stencil_bench.argtypes = [vp, c, ctypes.POINTER(Slab), ip, c, c, c, dp, dp, dp, vp]
     L.lqcd_boundary_modes.argtypes = [vp, ctypes.POINTER(Slab), c, c, c, c, vp, vp, ctypes.POINTER(ParamsC),
                                       ctypes.POINTER(StatsC), vp]
     L.lqcd_projected_factors.argtypes = [vp, ctypes.POINTER(SplitC), c, c, vp, vp, vp, ctypes.POINTER(ParamsC),
@@ -248,6 +251,28 @@ class Lattice:
         names = ["gamma", "gamma_bar", "gamma_star", "full"]
         return fact, cor, {k: s.as_dict() for k, s in zip(names, st)}
 
+    def factorized_propagators(self, gamma, gamma_star, x_src, fields, delta=None, corr: bool = True,
+                               params: SolverParams | None = None, stream=None, out=None):
+        """Sec. 3 for several gauge fields in one batched call: (fact, corr, stats) with fact/corr
+        [n_fields, 12, V, 4, 3] and stats[j] the four stage statistics of field fields[j]."""
+        n = len(fields)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if out is None:
+            fact = torch.empty((n, 12, self.V, 4, 3), dtype=torch.complex128, device=dev)
+            cor = torch.empty_like(fact) if corr else None
+        else:
+            fact, cor = out
+        sp = self._split(gamma, gamma_star, delta)
+        st = (StatsC * (4 * n))()
+        p = (params or SolverParams()).c()
+        _check(lib().lqcd_factorized_propagators(self._h, ctypes.byref(sp), (ctypes.c_int * 4)(*x_src), n,
+                                                 (ctypes.c_int * n)(*fields), _dev(fact, "fact"),
+                                                 _dev(cor, "corr") if cor is not None else None, ctypes.byref(p),
+                                                 st, _stream(stream)))
+        names = ["gamma", "gamma_bar", "gamma_star", "full"]
+        stats = [{k: st[4 * j + i].as_dict() for i, k in enumerate(names)} for j in range(n)]
+        return fact, cor, stats
+
     def dslash_bench(self, doms, field_ids, precision: int = 32, reps: int = 20, stream=None):
         """(ms per launch, algorithmic bytes per launch, flops per launch) of the solver's hop kernel."""
         n = len(doms)
@@ -256,6 +281,17 @@ class Lattice:
         ms, by, fl = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
         _check(lib().lqcd_dslash_bench(self._h, n, sl, fi, precision, reps, ctypes.byref(ms), ctypes.byref(by),
                                        ctypes.byref(fl), _stream(stream)))
+        return ms.value, by.value, fl.value
+
+    def stencil_bench(self, doms, field_ids, precision: int = 32, kernel: int = 0, reps: int = 20, stream=None):
+        """(ms per launch, algorithmic bytes, flops) of one kernel of the solver's iteration
+        (0-3: hop kernels, 4-6: vector updates; see lqcd_stencil_bench in include/lqcd.h)."""
+        n = len(doms)
+        sl = (Slab * n)(*[Slab(*d) for d in doms])
+        fi = (ctypes.c_int * n)(*field_ids)
+        ms, by, fl = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(lib().lqcd_stencil_bench(self._h, n, sl, fi, precision, kernel, reps, ctypes.byref(ms),
+                                        ctypes.byref(by), ctypes.byref(fl), _stream(stream)))
         return ms.value, by.value, fl.value
 
     def link_force(self, phi: torch.Tensor, dom, field: int = 0, params: SolverParams | None = None,
@@ -273,7 +309,7 @@ class Lattice:
 
     def disconnected_trace(self, eta: torch.Tensor, doms, field: int = 0, params: SolverParams | None = None,
                            stream=None):
-        """Sec. 4.1 eq. stochastic_estimator on each slab of `doms` (Wilson operator, c_sw = 0).
+        """Sec. 5 eq. stochastic_estimator on each slab of `doms` (Wilson operator, c_sw = 0).
 
         eta: device complex128 [n_src, V, 4, 3] sources.  Returns (trace, mean, stats):
         trace [n_src, n_doms, T] per source and time slice, mean [n_doms, T] over the
@@ -292,7 +328,7 @@ class Lattice:
 
     def boundary_modes(self, v0: torch.Tensor, dom, g1: int, field: int = 0, n_iter: int = 10,
                        params: SolverParams | None = None, stream=None):
-        """Sec. 5 projection vectors: n_iter inverse iterations of D on the slab `dom` from the
+        """Sec. 6 projection vectors: n_iter inverse iterations of D on the slab `dom` from the
         starting vectors v0 (complex128 [n_modes, slab sites, 4, 3]), each followed by an
         orthonormalisation; phi = orthonormalised (1 + g0)/2 V on slice g1.
         Returns (phi [n_modes, L1 L2 L3, 4, 3], stats)."""
@@ -365,7 +401,7 @@ def level_mean(t: torch.Tensor, stream=None) -> torch.Tensor:
 
 
 def multilevel_nucleon(B_xi_levels: torch.Tensor, B_eta_levels: torch.Tensor, stream=None) -> torch.Tensor:
-    """Level-1 part of eq. multilevel_estimator for the factorized nucleon (Sec. 2.2, Sec. 3.3): the
+    """Level-1 part of eq. multilevel_estimator for the factorized nucleon (Sec. 2.2, Sec. 4.2): the
     blocks of each region averaged over their n1 level-1 fields (B_xi_levels [n1, n_x, n, n, n, 4],
     B_eta_levels [n1, n_y, n, n, n, 4]), then contracted: W [n_x, n_y, 2] (W1, W2).  The contraction
     is bilinear, so this equals the mean of the n1^2 contractions of level-1 pairs."""

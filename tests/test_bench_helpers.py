@@ -39,14 +39,26 @@ def test_kernel_hash_ignores_comments_only(fake_root):
 
 
 def test_traffic_record_used_only_for_matching_source(fake_root):
-    rec = {"32": {"kernel_hash": bench._kernel_hash(), "dram_bytes_per_launch": 123456}}
+    rec = {"32:1": {"kernel_hash": bench._kernel_hash(), "dram_bytes_per_launch": 123456, "system_sites": 1000}}
     path = fake_root / "profiles" / "dslash_traffic.json"
     path.write_text(json.dumps(rec))
-    assert bench._traffic(32) == 123456.0
-    assert bench._traffic(16) is None
-    rec["32"]["kernel_hash"] = "0" * 16
+    assert bench._traffic(32, 1) == pytest.approx(123.456)
+    assert bench._traffic(32, 2) is None
+    assert bench._traffic(16, 1) is None
+    rec["32:1"]["kernel_hash"] = "0" * 16
     path.write_text(json.dumps(rec))
-    assert bench._traffic(32) is None
+    assert bench._traffic(32, 1) is None
+
+
+def test_cpu_cost_counts_site_applications():
+    """The extrapolated oracle time: every solve's sites x (2 per iteration + 2), scaled by the
+    measured seconds per round over the sample's sites."""
+    wl = dict(bench.WL16)
+    s3 = 16 ** 3
+    iters = {"gamma": 10, "gamma_bar": 20, "gamma_star": 30, "full": 40}
+    sites = {"gamma": 14 * s3, "gamma_bar": 18 * s3, "gamma_star": 18 * s3, "full": 32 * s3}
+    want = sum(sites[k] * (2 * iters[k] + 2) for k in iters) * 2.0 / s3
+    assert bench._cpu_cost(2.0, s3, wl, iters) == pytest.approx(want)
 
 
 def test_clock_summary_flags_throttle_reasons():

@@ -1,4 +1,4 @@
-"""Parity of the disconnected-trace estimator (Sec. 4.1, eq. stochastic_estimator) on the
+"""Parity of the disconnected-trace estimator (Sec. 5, eq. stochastic_estimator) on the
 GPU with the FP64 oracle, through the C ABI.
 
 Tolerance: the GPU solves D_L psi = g5 eta to relative residual 1e-12 (FP32 inner

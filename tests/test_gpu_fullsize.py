@@ -1,5 +1,4 @@
-"""Parity at the full size of the 16^3x32 workload (the launch configuration
-bench.py times), checked on sampled columns with the oracle's own operator.
+"""Parity at the full sizes of the workloads, checked with the oracle's own operator.
 
 Oracle solves at this size take hours, so every GPU result is checked through
 properties the exact answer has, each evaluated with the oracle's independent
@@ -24,7 +23,7 @@ KAPPA, CSW = 0.13, 1.0
 G, DL, GS = (0, 13), (14, 17), (14, 31)
 GB = (0, 17)
 X_SRC = (2, 0, 0, 0)
-COLS = (0, 7)
+COLS = tuple(range(12))  # every column of the propagator
 
 
 @pytest.fixture(scope="module")
@@ -74,16 +73,48 @@ def test_factorized_propagator_16x32_properties(field, prec):
     lat.close()
 
 
+def _sample_sites(dims, slab, x_src, n_random, rng):
+    """Natural indices of a fixed site sample of a slab: the source, four sites on each of
+    the slab's two boundary slices and n_random sites inside."""
+    s3 = dims[1] * dims[2] * dims[3]
+    a, b = slab
+    src = ((x_src[0] * dims[1] + x_src[1]) * dims[2] + x_src[2]) * dims[3] + x_src[3]
+    out = [src] + [a * s3 + int(v) for v in rng.integers(s3, size=4)] + [b * s3 + int(v) for v in rng.integers(s3, size=4)]
+    out += [int(v) for v in rng.integers(a * s3, (b + 1) * s3, size=n_random)]
+    return np.array(out, dtype=np.int64)
+
+
+def _neighbours(dims, sites):
+    """The sites themselves and their 8 nearest neighbours (periodic wrap; the slab
+    operator ignores the ones outside its slab)."""
+    T, L1, L2, L3 = dims
+    x3 = sites % L3
+    x2 = (sites // L3) % L2
+    x1 = (sites // (L3 * L2)) % L1
+    x0 = sites // (L3 * L2 * L1)
+    out = [sites]
+    for d, (x, L) in enumerate(((x0, T), (x1, L1), (x2, L2), (x3, L3))):
+        for step in (1, -1):
+            c = [x0, x1, x2, x3]
+            c[d] = (x + step) % L
+            out.append(((c[0] * L1 + c[1]) * L2 + c[2]) * L3 + c[3])
+    return np.unique(np.concatenate(out))
+
+
 def test_batched_32x64_domain_propagators_sampled():
     """The 32^3x64 batched workload (8 slabs x 12 sources x 16 inner-level fields,
-    1536 systems, FP16 inner solves + FP64 correction): every system reports a
-    true residual <= 1e-10, and sampled systems are checked with the oracle's D."""
+    1536 systems, FP16 inner solves + FP64 correction).  Every system reports a true
+    residual <= 1e-10, and every system's residual eta - D_L psi is evaluated by the
+    oracle (one site at a time, clover from the links) on a fixed 24-site sample of
+    its slab: the source, both boundary slices and random sites.  On field 0, one
+    column of each slab is checked in full with the oracle's operator."""
     from paper_1612_06424_gb300 import build, lqcd
 
     build.build()
     dims = (64, 32, 32, 32)
     slabs = [(8 * d, 8 * d + 7) for d in range(8)]
     nf = 16
+    s3 = 32 ** 3
     U0 = inputs.random_su3_field_device(dims, 0.4, 3, device="cuda")
     Uf = inputs.inner_level_fields_device(U0, dims, slabs, nf, 0.4, 4)
     del U0
@@ -97,13 +128,30 @@ def test_batched_32x64_domain_propagators_sampled():
     sol, st = lat.point_propagators(doms, fields, xs, cols, lqcd.SolverParams(tol=1e-10, precision=16))
     assert all(x["status"] == 0 and x["true_residual"] <= 1e-10 for x in st)
     n_slab = lat.slab_len(0, 7)
-    for k in (5, 1000):  # (field 0, slab 0, col 5) and (field 10, slab 3, col 4)
-        j, (a, b) = fields[k], doms[k]
+    rng = np.random.default_rng(12)
+    V = lat.V
+    buf = np.zeros((V, 4, 3), complex)  # full-lattice input of the oracle, filled only where read
+    for j in range(nf):
         U = Uf[j].cpu().numpy()
-        op = oracle.Operator(dims, U, 0.134, 1.0)
+        for k in [q for q in range(len(doms)) if fields[q] == j]:
+            a, b = doms[k]
+            smp = _sample_sites(dims, (a, b), xs[k], 15, rng)
+            need = _neighbours(dims, smp)
+            need = need[(need >= a * s3) & (need < (b + 1) * s3)]
+            idx = torch.from_numpy(k * n_slab + need - a * s3).cuda()
+            buf[need] = sol.index_select(0, idx).cpu().numpy()
+            eta = np.zeros((len(smp), 4, 3), complex)
+            s0, c0 = divmod(cols[k], 3)
+            eta[smp == smp[0], s0, c0] = 1.0  # the first sample is the source site
+            r = eta - oracle.dirac_at_sites(dims, U, 0.134, 1.0, oracle.BC_OPEN, (a, b), smp, buf)
+            buf[need] = 0
+            assert np.abs(r).max() <= 1e-10, (k, np.abs(r).max())
+    # field 0 in full, one column per slab
+    op = oracle.Operator(dims, Uf[0].cpu().numpy(), 0.134, 1.0)
+    for d, (a, b) in enumerate(slabs):
+        k = 12 * d + (5 * d) % 12
         x = np.zeros((op.V, 4, 3), complex)
-        sl = inputs.slab_sites(dims, a, b)
-        x[sl] = sol[k * n_slab:(k + 1) * n_slab].cpu().numpy()
+        x[inputs.slab_sites(dims, a, b)] = sol[k * n_slab:(k + 1) * n_slab].cpu().numpy()
         eta = np.zeros((op.V, 4, 3), complex)
         s0, c0 = divmod(cols[k], 3)
         eta[((xs[k][0] * 32 + xs[k][1]) * 32 + xs[k][2]) * 32 + xs[k][3], s0, c0] = 1.0
@@ -168,6 +216,49 @@ def test_link_force_24x48_finite_differences():
         err = abs(F[site, mu, a] - fd)
         assert err <= 1e-6 * abs(fd) + 1e-9 * np.abs(F).max(), (site, mu, a, F[site, mu, a], fd)
         worst = max(worst, err)
+    lat.close()
+
+
+def test_link_force_24x48_against_oracle_formula():
+    """The GPU force kernels at 24^3x48 (domain t 12..23, kappa 0.132, c_sw 1) against the
+    oracle's force formula F = -2 Re <Y, dD_L X> evaluated on the GPU's own X and Y.  X and Y
+    come from separate FP64 GPU solves (Y = D_L^{-dag} phi via g5 D_L^{-1} g5, X = D_L^{-1} Y,
+    residual 1e-12), and the oracle's D first confirms D_L^dag Y = phi and D_L X = Y to
+    1.05e-12.  lat.link_force solves for its own X and Y to 1e-12, so the two forces differ
+    by cond(D_L) x 1e-12 relative; 1e-9 of max |F| is allowed, element by element on every
+    link of the lattice."""
+    from paper_1612_06424_gb300 import build, lqcd
+
+    build.build()
+    dims = (48, 24, 24, 24)
+    dom = (12, 23)
+    U = inputs.random_su3_field(dims, 0.4, 5)
+    lat = lqcd.Lattice(dims, "open")
+    lat.set_gauge(torch.from_numpy(U).cuda(), 0.132, 1.0)
+    sl = inputs.slab_sites(dims, *dom)
+    phi_h = inputs.gaussian_spinor(dims, 52)[0]
+    phi = torch.from_numpy(np.ascontiguousarray(phi_h[sl])).cuda()
+    params = lqcd.SolverParams(tol=1e-12, precision=64)
+    F, S, st = lat.link_force(phi, dom, 0, params)
+    assert all(x["status"] == 0 for x in st), st
+    g5 = torch.tensor([1, 1, -1, -1], dtype=torch.complex128, device="cuda").view(1, 4, 1)
+    y, _ = lat.solve_block((g5 * phi).contiguous(), [dom], [0], params)
+    y = (g5 * y).contiguous()
+    x, _ = lat.solve_block(y, [dom], [0], params)
+    op = oracle.Operator(dims, U, 0.132, 1.0)
+    X = np.zeros((op.V, 4, 3), complex)
+    Y = np.zeros((op.V, 4, 3), complex)
+    X[sl] = x.cpu().numpy()
+    Y[sl] = y.cpu().numpy()
+    phi_m = op.masked(phi_h, *dom)
+    assert np.linalg.norm(phi_m - op.apply(Y, *dom, dagger=True)) <= 1.05e-12 * np.linalg.norm(phi_m)
+    assert np.linalg.norm(Y - op.apply(X, *dom)) <= 1.05e-12 * np.linalg.norm(Y)
+    F_ref = op.force(X, Y, *dom)
+    F = F.cpu().numpy()
+    scale = np.abs(F_ref).max()
+    assert scale > 0
+    assert np.abs(F - F_ref).max() <= 1e-9 * scale
+    assert abs(S - np.linalg.norm(Y) ** 2) <= 1e-9 * S
     lat.close()
 
 

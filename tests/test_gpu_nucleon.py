@@ -1,4 +1,4 @@
-"""Parity of the nucleon blocks and contractions on the GPU (Sec. 3.3 eq. nucleon_prop_factorized)
+"""Parity of the nucleon blocks and contractions on the GPU (Sec. 4.2 eq. nucleon_prop_factorized)
 with the FP64 oracle, through the C ABI.
 
 Tolerance of the blocks: the GPU forms the diquark and the (x, c) sum in FP32 (inputs rounded from

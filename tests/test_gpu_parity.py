@@ -151,6 +151,42 @@ def test_factorized_propagator_with_overlap_clover(bc):
         assert st[k]["status"] == 0 and st[k]["true_residual"] <= 1e-12
 
 
+@pytest.mark.parametrize("prec", [64, 32])
+def test_factorized_propagators_batched_over_fields(prec):
+    """Two gauge fields (the level-0 field and an inner-level field with Gamma's and
+    Gamma*'s own links redrawn) in one batched call, fields passed in reverse order:
+    each field's fact and corr match its single-field call and the oracle's
+    factorization and full propagator (eqs. quark_prop_I/II, observable_factorization)."""
+    lqcd = _lq()
+    dims = (8, 4, 4, 6)
+    kappa, csw = 0.13, 1.0
+    U0 = inputs.random_su3_field(dims, 0.4, 91)
+    U1 = inputs.inner_level_fields(U0, dims, [(0, 3), (6, 7)], 2, 0.4, 92, frozen=(4, 5))[1]
+    Us = np.stack([U0, U1])
+    lat = lqcd.Lattice(dims, "open")
+    lat.set_gauge(Us, kappa, csw)
+    x_src = (1, 2, 0, 3)
+    tol = 1e-12 if prec == 64 else 1e-10
+    params = lqcd.SolverParams(tol=tol, precision=prec)
+    fact, corr, st = lat.factorized_propagators((0, 3), (4, 7), x_src, [1, 0], delta=(4, 5), params=params)
+    eta = inputs.point_sources(dims, x_src)
+    split = oracle.Split((0, 3), (4, 7), delta=(4, 5))
+    bound = 1e-9 if prec == 64 else 2e-9
+    for j, fid in enumerate([1, 0]):
+        for k in ("gamma", "gamma_bar", "gamma_star", "full"):
+            assert st[j][k]["status"] == 0 and st[j][k]["true_residual"] <= tol, (j, k, st[j][k])
+        f1, c1, _ = lat.factorized_propagator((0, 3), (4, 7), x_src, fid, delta=(4, 5), params=params)
+        op = oracle.Operator(dims, Us[fid], kappa, csw)
+        f_ref = oracle.factorized_propagator(op, split, eta)
+        full = oracle.full_propagator(op, eta)
+        scale = np.abs(full).max()
+        assert np.abs(fact[j].cpu().numpy() - f_ref).max() <= bound * scale, j
+        assert np.abs(corr[j].cpu().numpy() - (full - f_ref)).max() <= bound * scale, j
+        assert (fact[j] - f1).abs().max().item() <= bound * scale
+        assert (corr[j] - c1).abs().max().item() <= bound * scale
+    lat.close()
+
+
 @pytest.mark.parametrize("csw,dom", [(0.0, (0, 3)), (1.0, (1, 2)), (1.0, (0, 3))])
 def test_link_force_matches_oracle(csw, dom):
     lqcd = _lq()

@@ -1,5 +1,5 @@
 """Parity of the quark-line projection on the GPU (Sec. 3.3 eqs. projection, quark_prop_II_proj;
-Sec. 5 inverse-iteration vectors) with the FP64 oracle, through the C ABI.
+Sec. 6 inverse-iteration vectors) with the FP64 oracle, through the C ABI.
 
 Tolerances: the GPU solves to relative residual 1e-12 (FP32 inner solves, FP64 defect
 correction), the oracle to 1e-13.

@@ -1,4 +1,4 @@
-"""Pins of the oracle's disconnected-trace estimator (Sec. 4.1, eq. stochastic_estimator).
+"""Pins of the oracle's disconnected-trace estimator (Sec. 5, eq. stochastic_estimator).
 
 - exact identity per site, checked by dense LU: with K = kappa D_hop,
   D^{-1} = 2 kappa sum_{n<8} K^n + K^8 D^{-1} and tr{gamma_5 K^n(x,x)} = 0 for n < 8

@@ -1,4 +1,4 @@
-"""Pins of the oracle's factorized nucleon contraction (Sec. 3.3 eq. nucleon_prop_factorized).
+"""Pins of the oracle's factorized nucleon contraction (Sec. 4.2 eq. nucleon_prop_factorized).
 
 - C = gamma_0 gamma_2 is a charge-conjugation matrix of this basis: C gamma_mu C^{-1} = -gamma_mu^T;
 - the block B is the eps/C-gamma_5 contraction written out site by site and index by index in plain

@@ -1,5 +1,5 @@
 """Pins of the oracle's quark-line projection (Sec. 3.3 eqs. projection, quark_prop_II_proj) and
-of its inverse-iteration projection vectors (Sec. 5).
+of its inverse-iteration projection vectors (Sec. 6).
 
 - orthonormalize: Q^dag Q = 1 and R = Q^dag W upper triangular with a positive real diagonal;
 - P_+ is the half of a spinor the boundary block reads: D_dGamma* (1 - P_+) = 0, checked with the

@@ -4,9 +4,11 @@ The allocation-free entry point serves callers that cannot allocate device
 memory while they run (an application whose allocator owns the GPU's memory,
 or a latency-critical path); its scratch is a fixed device array inside the
 library.  Two calls in a row on different inputs (the second must not see the
-first's leftovers), both parities of a slab and the whole lattice, plus the
-size limit.  Tolerance: the FP64 operator tolerance of the parity tests
-(1e-13 relative to the largest element).
+first's leftovers), both parities of a slab and the whole lattice, the whole
+lattice with periodic and antiperiodic time boundaries (the hop across
+x0 = T-1 -> 0 and its sign), plus the size limit.  Tolerance: the FP64
+operator tolerance of the parity tests (1e-13 relative to the largest
+element).
 """
 import ctypes
 
@@ -48,6 +50,26 @@ def test_noalloc_dslash_matches_dslash_twice():
         scale = ref.abs().max().item()
         assert torch.isfinite(out).all()
         assert (out - ref).abs().max().item() <= 1e-13 * scale, call
+    lat.close()
+
+
+@pytest.mark.parametrize("bc", ["periodic", "antiperiodic"])
+def test_noalloc_dslash_wrapped_time_boundary(bc):
+    lqcd, L = _lib()
+    dims = (8, 6, 6, 4)
+    lat = lqcd.Lattice(dims, bc)
+    lat.set_gauge(inputs.random_su3_field(dims, 0.4, 86), 0.13, 1.0)
+    stream = torch.cuda.current_stream()
+    for dag, seed in ((0, 87), (1, 88)):
+        psi = torch.from_numpy(inputs.gaussian_spinor(dims, seed)[0]).cuda()
+        ref = lat.dslash(psi, 0, None, bool(dag), 64)
+        out = torch.full_like(psi, float("nan"))
+        rc = L.lqcd_dslash_noalloc(lat._h, 0, None, dag, ctypes.c_void_p(psi.data_ptr()),
+                                   ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
+        assert rc == 0, L.lqcd_last_error()
+        torch.cuda.synchronize()
+        assert torch.isfinite(out).all()
+        assert (out - ref).abs().max().item() <= 1e-13 * ref.abs().max().item(), (bc, dag)
     lat.close()
 
 
