@@ -194,6 +194,28 @@ int lqcd_factorized_propagators(lqcd_lattice *lat, const lqcd_split *split, cons
                                 const int *field_ids, double *fact, double *corr, const lqcd_solver_params *params,
                                 lqcd_solver_stats *stats, void *stream);
 
+/* The boundary source of eq. quark_prop_II on its own (Sec. 3 eq.
+ * block_inverse: D_dGamma* is the block of D from Gamma to Gamma*):
+ *   chi_k = P_Gamma* D P_Gamma psi_k,  k < n,
+ * for psi_k a device slab vector on Gammabar (e.g. D_Gammabar^{-1} eta from
+ * lqcd_point_propagators), on field field_ids[k].  chi: device [n][2][L1 L2
+ * L3][4][3] complex128, overwritten: slot 0 the first slice of Gamma* (the
+ * backward time hop from the last slice of Gamma), slot 1 the last slice
+ * x0 = T-1 (the wrapping hop to x0 = 0; zero for the open time boundary).
+ * With lqcd_schur_solve it splits a factorized propagator between processes
+ * that exchange chi alone (L1 L2 L3 x 12 complex per source and slot).
+ * Synchronises.  Errors: LQCD_EBADARG, LQCD_ENOFIELD, LQCD_ECUDA. */
+int lqcd_schur_boundary(lqcd_lattice *lat, const lqcd_split *split, int n, const int *field_ids, const double *psi,
+                        double *chi, void *stream);
+
+/* The Gamma* half of eq. quark_prop_II: fact_k = -D_Gamma*^{-1} chi_k on
+ * field field_ids[k], k < n, with chi in the layout of lqcd_schur_boundary.
+ * fact_gs: device [n] slab vectors on Gamma* back to back, overwritten.
+ * stats: host array of n entries or NULL.  Errors: LQCD_EBADARG,
+ * LQCD_ENOFIELD, LQCD_ENOMEM, LQCD_ENOTCONVERGED, LQCD_ECUDA. */
+int lqcd_schur_solve(lqcd_lattice *lat, const lqcd_split *split, int n, const int *field_ids, const double *chi,
+                     double *fact_gs, const lqcd_solver_params *params, lqcd_solver_stats *stats, void *stream);
+
 /* Link force of S = phi^dag (D_L^dag D_L)^{-1} phi for the slab dom on field
  * `field`: force[i][mu][a] = dS/domega for U_mu(x_i) -> exp(i omega T_a)
  * U_mu(x_i), T_a = lambda_a / 2 (Gell-Mann), i.e.

@@ -579,6 +579,11 @@ int upload_ptrs(DBuf& d, const std::vector<void*>& p, cudaStream_t st) {
 
 }  // namespace
 
+namespace {
+int check_split(const lqcd_lattice* L, const lqcd_split* split, const char* who);
+lqcd_slab gamma_bar_of(const lqcd_split* split);
+}  // namespace
+
 // ===================================================================== API
 extern "C" int lqcd_create_lattice(const int dims[4], int bc_t, lqcd_lattice** out) {
   if (!dims || !out) {
@@ -1024,6 +1029,93 @@ extern "C" int lqcd_factorized_propagator(lqcd_lattice* L, const lqcd_split* spl
                                           double* fact, double* corr, const lqcd_solver_params* params,
                                           lqcd_solver_stats* stats, void* stream) {
   return lqcd_factorized_propagators(L, split, x_src, 1, &field, fact, corr, params, stats, stream);
+}
+
+// The two halves of eq. quark_prop_II on their own, so that the systems of a
+// factorized propagator can be split between processes that exchange only chi.
+extern "C" int lqcd_schur_boundary(lqcd_lattice* L, const lqcd_split* split, int n, const int* field_ids,
+                                   const double* psi, double* chi, void* stream) {
+  RC(check_lat(L));
+  if (!split || n < 1 || !field_ids || !psi || !chi) {
+    lq_set_error("schur_boundary: bad arguments");
+    return LQCD_EBADARG;
+  }
+  RC(check_split(L, split, "schur_boundary"));
+  for (int k = 0; k < n; k++)
+    if (field_ids[k] < 0 || field_ids[k] >= (int)L->fields.size()) {
+      lq_set_error("schur_boundary: field index not loaded");
+      return LQCD_ENOFIELD;
+    }
+  cudaStream_t st = (cudaStream_t)stream;
+  const lqcd_slab Gb = gamma_bar_of(split);
+  std::vector<lqcd_slab> doms(n, Gb);
+  BatchStore B;
+  RC(B.build(L, n, doms.data(), field_ids, st));
+  Pool64 e;
+  RC(e.alloc(B.b, 2, st));
+  const long long len = (long long)(Gb.t1 - Gb.t0 + 1) * L->S3 * 12;
+  std::vector<void*> p(n);
+  std::vector<int> ids(n);
+  for (int k = 0; k < n; k++) {
+    p[k] = (void*)((const double2*)psi + k * len);
+    ids[k] = k;
+  }
+  DBuf d, di;
+  RC(upload_ptrs(d, p, st));
+  RC(di.alloc(sizeof(int) * n, st));
+  CK(cudaMemcpyAsync(di.p, ids.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+  RC(lq_nat_to_eo(L, B.b, d.as<const double2*>(), e.v(0), e.v(1), st));
+  RC(lq_boundary_chi(L, B.b, di.as<int>(), split->gamma.t1, e.v(0), e.v(1), (double2*)chi, st));
+  CK(cudaStreamSynchronize(st));
+  return 0;
+}
+
+extern "C" int lqcd_schur_solve(lqcd_lattice* L, const lqcd_split* split, int n, const int* field_ids,
+                                const double* chi, double* fact_gs, const lqcd_solver_params* params,
+                                lqcd_solver_stats* stats, void* stream) {
+  RC(check_lat(L));
+  if (!split || n < 1 || !field_ids || !chi || !fact_gs) {
+    lq_set_error("schur_solve: bad arguments");
+    return LQCD_EBADARG;
+  }
+  RC(check_split(L, split, "schur_solve"));
+  for (int k = 0; k < n; k++)
+    if (field_ids[k] < 0 || field_ids[k] >= (int)L->fields.size()) {
+      lq_set_error("schur_solve: field index not loaded");
+      return LQCD_ENOFIELD;
+    }
+  const double t_start = now_s();
+  cudaStream_t st = (cudaStream_t)stream;
+  lqcd_solver_params prm = default_params(params);
+  const lqcd_slab Gs = split->gamma_star;
+  const int g1 = split->gamma.t1;
+  const long long len = (long long)(Gs.t1 - Gs.t0 + 1) * L->S3 * 12;
+  std::vector<SysSpec> sp(n);
+  for (int k = 0; k < n; k++) {
+    sp[k] = SysSpec{Gs, field_ids[k], 0, 0, make_int4(0, 0, 0, 0)};
+    sp[k].out = k;
+  }
+  FillFn fill = [&](BatchStore& B, int k0, double2* be, double2* bo) -> int {
+    SrcArrays s;
+    RC(s.upload(sp, k0, B.b.nsys, st));
+    return lq_chi_to_eo(L, B.b, s.outs.as<int>(), g1, (const double2*)chi, be, bo, st);
+  };
+  SinkFn sink = [&](BatchStore& B, int k0, const double2* xe, const double2* xo) -> int {
+    std::vector<void*> p(B.b.nsys);
+    for (int q = 0; q < B.b.nsys; q++) p[q] = (void*)((double2*)fact_gs + (k0 + q) * len);
+    DBuf d;
+    RC(upload_ptrs(d, p, st));
+    return lq_eo_to_nat(L, B.b, xe, xo, d.as<double2* const>(), -1.0, st);
+  };
+  SolveOut o;
+  RC(solve_waves(L, sp, false, prm, fill, sink, o, st));
+  CK(cudaStreamSynchronize(st));
+  const double secs = now_s() - t_start;
+  if (stats)
+    for (int k = 0; k < n; k++) fill_stats(o, k, 1, secs, &stats[k]);
+  int w = worst_status(o);
+  if (w) lq_set_error("schur_solve: some systems did not reach the tolerance");
+  return w;
 }
 
 extern "C" int lqcd_point_propagators(lqcd_lattice* L, int n_sys, const lqcd_slab* doms, const int* field_ids,

@@ -89,6 +89,9 @@ def lib() -> ctypes.CDLL:
                                              ctypes.POINTER(StatsC), vp]
     L.lqcd_factorized_propagators.argtypes = [vp, ctypes.POINTER(SplitC), ip, c, ip, vp, vp,
                                               ctypes.POINTER(ParamsC), ctypes.POINTER(StatsC), vp]
+    L.lqcd_schur_boundary.argtypes = [vp, ctypes.POINTER(SplitC), c, ip, vp, vp, vp]
+    L.lqcd_schur_solve.argtypes = [vp, ctypes.POINTER(SplitC), c, ip, vp, vp, ctypes.POINTER(ParamsC),
+                                   ctypes.POINTER(StatsC), vp]
     L.lqcd_link_force.argtypes = [vp, ctypes.POINTER(Slab), c, vp, vp, dp, ctypes.POINTER(ParamsC),
                                   ctypes.POINTER(StatsC), vp]
     L.lqcd_point_propagators.argtypes = [vp, c, ctypes.POINTER(Slab), ip, ip, ip, vp, ctypes.POINTER(ParamsC),
@@ -272,6 +275,30 @@ class Lattice:
         names = ["gamma", "gamma_bar", "gamma_star", "full"]
         stats = [{k: st[4 * j + i].as_dict() for i, k in enumerate(names)} for j in range(n)]
         return fact, cor, stats
+
+    def schur_boundary(self, psi_gbar: torch.Tensor, gamma, gamma_star, field_ids, delta=None, stream=None):
+        """chi_k = D_dGamma* psi_k (eq. quark_prop_II) for slab vectors psi [n, Gammabar sites, 4, 3] on the
+        fields field_ids; chi [n, 2, L1 L2 L3, 4, 3] (slot 0: first slice of Gamma*, slot 1: last slice)."""
+        n = len(field_ids)
+        chi = torch.empty((n, 2, self.S3, 4, 3), dtype=torch.complex128, device=psi_gbar.device)
+        sp = self._split(gamma, gamma_star, delta)
+        _check(lib().lqcd_schur_boundary(self._h, ctypes.byref(sp), n, (ctypes.c_int * n)(*field_ids),
+                                         _dev(psi_gbar, "psi"), _dev(chi, "chi"), _stream(stream)))
+        return chi
+
+    def schur_solve(self, chi: torch.Tensor, gamma, gamma_star, field_ids, delta=None,
+                    params: SolverParams | None = None, stream=None):
+        """fact_k = -D_Gamma*^{-1} chi_k on Gamma* (eq. quark_prop_II); returns (fact [n, Gamma* sites, 4, 3],
+        stats)."""
+        n = len(field_ids)
+        out = torch.empty((n, self.slab_len(*gamma_star), 4, 3), dtype=torch.complex128, device=chi.device)
+        sp = self._split(gamma, gamma_star, delta)
+        st = (StatsC * n)()
+        p = (params or SolverParams()).c()
+        _check(lib().lqcd_schur_solve(self._h, ctypes.byref(sp), n, (ctypes.c_int * n)(*field_ids),
+                                      _dev(chi.contiguous(), "chi"), _dev(out, "fact"), ctypes.byref(p), st,
+                                      _stream(stream)))
+        return out, [s.as_dict() for s in st]
 
     def dslash_bench(self, doms, field_ids, precision: int = 32, reps: int = 20, stream=None):
         """(ms per launch, algorithmic bytes per launch, flops per launch) of the solver's hop kernel."""
