@@ -24,6 +24,7 @@ second field's, so the fields run one per step.
   python bench.py --workload factorized_16x32  # 16^3x32 factorized propagator + correction
   python bench.py --workload batched_32x64   # 8 slabs x 12 sources x 16 inner-level fields
   python bench.py --workload force_24x48     # domain pseudofermion link force, 4 domains
+  python bench.py --workload nucleon_hierarchy_64x24  # Sec. 6 Delta = 8/12/16 hierarchy
 
 Multi-GPU (torchrun): every rank computes its own propagators (its own
 gauge fields, independent problems); there is no collective on the data path.
@@ -92,7 +93,7 @@ def _args():
     ap.add_argument("--no-extra", action="store_true", help="skip the 16^3x32 figures of the default line")
     ap.add_argument("--workload", default="factorized_48x96",
                     choices=["factorized_48x96", "factorized_16x32", "batched_32x64", "force_24x48",
-                             "disconnected_64x24", "projection_64x24"])
+                             "disconnected_64x24", "projection_64x24", "nucleon_hierarchy_64x24"])
     ap.add_argument("--fields", type=int, default=8, help="inner-level fields of factorized_48x96")
     ap.add_argument("--sources", type=int, default=100, help="Gaussian sources of disconnected_64x24")
     ap.add_argument("--modes", type=int, default=120, help="projection vectors of projection_64x24")
@@ -955,13 +956,59 @@ def run_projection(args):
     lat.close()
 
 
+def run_hierarchy(args):
+    """64x24^3 Wilson-clover (kappa 0.1360, c_sw 1.0), open time boundary: the nucleon hierarchy of
+    Sec. 6 eq. nucleon_prop_hierarchical with the paper's split, Gamma = t 0..23, Gamma* = 24..63
+    and overlaps Delta = 8, 12, 16 (DeltaGamma = 24 .. 23+Delta), 12 point sources at (4,0,0,0): the
+    three factorized propagators and the full one in one batched set of solves, then the nucleon
+    point correlators.  A step is one hierarchy."""
+    import torch
+
+    from paper_1612_06424_gb300 import build, inputs, lqcd
+
+    build.build()
+    dims = (64, 24, 24, 24)
+    kappa, csw = 0.136, 1.0
+    G, GS, ends = (0, 23), (24, 63), [31, 35, 39]
+    U = inputs.random_su3_field_device(dims, 0.4, 41, device="cuda")
+    lat = lqcd.Lattice(dims, "open")
+    lat.set_gauge(U, kappa, csw)
+    del U
+    params = lqcd.SolverParams(tol=1e-10, precision=args.precision)
+    for _ in range(max(0, args.warmup)):
+        lat.nucleon_hierarchy(G, GS, ends, (4, 0, 0, 0), 0, params)
+    torch.cuda.synchronize()
+    n0 = lqcd.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks() as clk:
+        e0.record()
+        for _ in range(args.steps):
+            terms, full, st = lat.nucleon_hierarchy(G, GS, ends, (4, 0, 0, 0), 0, params)
+        e1.record()
+        torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3 / args.steps
+    ys = [30, 40, 50]
+    print(json.dumps({
+        "metric": "s per nucleon hierarchy (3 factorized propagators + full, 12 sources, contractions) @ res 1e-10",
+        "value": sec, "unit": "s/hierarchy", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": sec * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": DTYPE[args.precision], "data": "synthetic",
+        "config": {"workload": "64x24^3 nucleon hierarchy, Delta = 8/12/16", "dims": list(dims), "kappa": kappa,
+                   "c_sw": csw, "gamma": list(G), "gamma_star": list(GS), "delta_ends": ends, "x_src": [4, 0, 0, 0]},
+        "iters": {k: v["iters"] for k, v in st.items()},
+        "true_residual_max": max(v["true_residual"] for v in st.values()),
+        "terms_over_full": {str(y): [abs(terms[k][y]) / abs(full[y]) for k in range(len(ends) + 1)] for y in ys},
+        "gpu_launches": lqcd.kernel_launches() - n0, "clocks": clk.summary()}))
+    lat.close()
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         return run_reference(args)
     runs = {"batched_32x64": run_batched, "force_24x48": run_force, "disconnected_64x24": run_disconnected,
             "projection_64x24": run_projection, "factorized_16x32": run_factorized_16x32,
-            "factorized_48x96": run_headline}
+            "factorized_48x96": run_headline, "nucleon_hierarchy_64x24": run_hierarchy}
     return runs[args.workload](args)
 
 

@@ -216,6 +216,37 @@ int lqcd_schur_boundary(lqcd_lattice *lat, const lqcd_split *split, int n, const
 int lqcd_schur_solve(lqcd_lattice *lat, const lqcd_split *split, int n, const int *field_ids, const double *chi,
                      double *fact_gs, const lqcd_solver_params *params, lqcd_solver_stats *stats, void *stream);
 
+/* Nucleon correlators of point-source propagators (the two Wick
+ * contractions whose factorized form is Sec. 4.2 eq. nucleon_prop_factorized),
+ * summed over the sink sites y of each time slice t0 .. t0+n_t-1:
+ *   W[p][t][0] = W1 = sum_y eps^{abc} eps^{a'b'c'} (C g5)_{mu nu} (C g5)_{mu' nu'}
+ *                (g5 P_-)_{gam del} S^{ab'}_{mu nu'} S^{ba'}_{nu mu'} S^{cc'}_{del gam}
+ *   W[p][t][1] = W2 = the same with S^{ab'}_{mu nu'} S^{bc'}_{nu gam} S^{ca'}_{del mu'}
+ * with S = S_p(y, x)[(sink spin, colour), (source spin, colour)] =
+ * prop[p][3 s0 + c0][y][s][c], C = g0 g2, P_- = (1 - g0)/2; the correlator is
+ * W1 - W2.  prop: device [n_prop][12][V][4][3] complex128 (e.g. fact or
+ * fact + corr of lqcd_factorized_propagators); W: device [n_prop][n_t][2]
+ * complex128.  FP64, one warp per site, block sums in a fixed order.
+ * Stream-ordered.  Errors: LQCD_EBADARG, LQCD_ENOMEM, LQCD_ECUDA. */
+int lqcd_nucleon_point(lqcd_lattice *lat, int n_prop, const double *prop, int t0, int n_t, double *W, void *stream);
+
+/* The hierarchy of Sec. 6 eq. nucleon_prop_hierarchical for the 12 point
+ * sources at x_src on field `field`: C^(d) is the nucleon correlator
+ * (lqcd_nucleon_point, W1 - W2) of the factorized propagator with the overlap
+ * DeltaGamma_d = gamma.t1+1 .. delta_t1[d] (nested: gamma.t1 < delta_t1[0] <
+ * ... < delta_t1[n_d-1] < T-1; split->delta is ignored), C that of the full
+ * propagator.  All overlaps run in one batched set of solves (Gamma and the
+ * full lattice once, the n_d Gammabar and Gamma* stages together).
+ * C: host [n_d + 2][T] complex128, row k < n_d+1 the k-th term of
+ *   C = C^(0) + [C^(1) - C^(0)] + ... + [C^(n_d-1) - C^(n_d-2)] + [C - C^(n_d-1)],
+ * the last term C^(rest); row n_d+1 the full C.  stats: host array of 4
+ * entries (Gamma, Gammabar, Gamma*, full; each the worst over columns and
+ * overlaps) or NULL.  Synchronises.  Errors: LQCD_EBADARG, LQCD_ENOFIELD,
+ * LQCD_ENOMEM, LQCD_ENOTCONVERGED, LQCD_ECUDA. */
+int lqcd_nucleon_hierarchy(lqcd_lattice *lat, const lqcd_split *split, int n_d, const int *delta_t1,
+                           const int x_src[4], int field, double *C, const lqcd_solver_params *params,
+                           lqcd_solver_stats *stats, void *stream);
+
 /* Link force of S = phi^dag (D_L^dag D_L)^{-1} phi for the slab dom on field
  * `field`: force[i][mu][a] = dS/domega for U_mu(x_i) -> exp(i omega T_a)
  * U_mu(x_i), T_a = lambda_a / 2 (Gell-Mann), i.e.

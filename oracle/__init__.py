@@ -403,6 +403,54 @@ def nucleon_factorized(op: Operator, xi: np.ndarray, eta: np.ndarray, x0: int, y
     return w1, w2
 
 
+def nucleon_point_correlator(S: np.ndarray, T: int) -> np.ndarray:
+    """The two nucleon Wick contractions from a point source x to every sink y, summed over the
+    sites of each time slice (Sec. 4.2, the contractions whose factorized form is eq.
+    nucleon_prop_factorized), for the 12 propagator columns S[(3 nu + b), y, mu, a] = S(y, x)
+    [(mu, a), (nu, b)] (sink spin-colour mu, a; source spin-colour nu, b):
+        W1(t) = sum_{y in t} eps^{abc} eps^{a'b'c'} (Cg5)_{mu nu} (Cg5)_{mu' nu'} (g5 P_-)_{gam del}
+                    S^{a b'}_{mu nu'} S^{b a'}_{nu mu'} S^{c c'}_{del gam}
+        W2(t) = the same with S^{a b'}_{mu nu'} S^{b c'}_{nu gam} S^{c a'}_{del mu'}
+    with C = gamma_0 gamma_2, P_- = (1 - gamma_0)/2.  Returns W[T, 2] (W1, W2); the correlator
+    is W1 - W2.  Written as the definition, one einsum per slice."""
+    n_col, V = S.shape[0], S.shape[1]
+    assert n_col == 12
+    s3 = V // T
+    cg5 = charge_conjugation() @ gamma(4)
+    g5pm = gamma(4) @ (0.5 * (np.eye(4) - gamma(0)))
+    E = EPS3
+    # P[y, mu, a, nu, b] = S(y, x)[(mu, a), (nu, b)]
+    P = np.asarray(S).reshape(4, 3, V, 4, 3).transpose(2, 3, 4, 0, 1)
+    out = np.zeros((T, 2), dtype=np.complex128)
+    for t in range(T):
+        Pt = P[t * s3:(t + 1) * s3]
+        out[t, 0] = np.einsum("abc,ABC,mn,MN,gd,ymaNB,ynbMA,ydcgC->", E, E, cg5, cg5, g5pm, Pt, Pt, Pt,
+                              optimize="optimal")
+        out[t, 1] = np.einsum("abc,ABC,mn,MN,gd,ymaNB,ynbgC,ydcMA->", E, E, cg5, cg5, g5pm, Pt, Pt, Pt,
+                              optimize="optimal")
+    return out
+
+
+def nucleon_hierarchy(op: Operator, gamma_: tuple, gamma_star: tuple, delta_ends, eta: np.ndarray,
+                      tol: float = 1e-13):
+    """Eq. nucleon_prop_hierarchical (Sec. 6) for the point source of the 12 columns eta:
+    C^(i) is the nucleon correlator (W1 - W2 per time slice, nucleon_point_correlator) of the
+    factorized propagator with overlap DeltaGamma_i = gamma_[1]+1 .. delta_ends[i] (nested,
+    growing), C that of the full propagator, and the terms of the expansion are
+        C^(0), C^(1) - C^(0), ..., C^(n-1) - C^(n-2), C^(rest) = C - C^(n-1),
+    which sum to C.  Returns (terms [n+1, T] complex, C^(i) [n, T], C [T])."""
+    T = op.T
+    corr = []
+    for d1 in delta_ends:
+        split = Split(gamma_, gamma_star, delta=(gamma_[1] + 1, d1))
+        w = nucleon_point_correlator(factorized_propagator(op, split, eta, tol=tol), T)
+        corr.append(w[:, 0] - w[:, 1])
+    w = nucleon_point_correlator(full_propagator(op, eta, tol=tol), T)
+    c_full = w[:, 0] - w[:, 1]
+    terms = [corr[0]] + [corr[i] - corr[i - 1] for i in range(1, len(corr))] + [c_full - corr[-1]]
+    return np.array(terms), np.array(corr), c_full
+
+
 def multilevel_estimator(o_gamma, o_gamma_star, o_corr, product=np.multiply):
     """Eq. multilevel_estimator (Sec. 2.2): for level-0 fields i and their level-1 fields j, k, l,
         (1/n0) sum_i { [(1/n1) sum_j O_Gamma[i,j]] . [(1/n1) sum_k O_Gamma*[i,k]] + (1/n1) sum_l O_corr[i,l] },

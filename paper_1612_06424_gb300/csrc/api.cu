@@ -856,38 +856,202 @@ extern "C" int lqcd_solve_full(lqcd_lattice* L, int n_sys, const int* field_ids,
   return solve_api(L, n_sys, d.data(), field_ids, src, sol, params, stats, stream);
 }
 
-// Sec. 3 for the fields field_ids[0..n_f): per field and point-source column,
+namespace {
+
+// Sec. 3 for the fields field_ids[0..n_f) and n_d nested overlaps (DeltaGamma_d =
+// g1+1 .. d1s[d], empty when d1s[d] <= g1), per field and point-source column:
 //   fact = D_Gamma^{-1} eta on Gamma                                  (eq. quark_prop_I)
 //   fact = -D_Gamma*^{-1} D_dGamma* (D_Gammabar^{-1} eta)|_Gamma on Gamma*  (eq. quark_prop_II)
-//   corr = D^{-1} eta - fact                                          (eq. observable_factorization)
-// in four batched stages, each holding the 12 n_f systems of one kind:
-//   A1  Gamma from the point sources (fact on Gamma);
-//   A2  Gammabar from the point sources, started from the Gamma solution
-//       (zero on DeltaGamma): its residual lives on the first slice of
-//       DeltaGamma only; its boundary slice gives chi = D_dGamma* psi|_Gamma;
-//   B   Gamma* from chi (fact on Gamma*);
-//   C   the full lattice from the point sources, started from fact: the
-//       residual eta - D fact vanishes off the two slices next to the cut,
-//       where it is as small as the propagator across the cut.
-// The starting iterates change the iteration counts, not the solutions:
-// every system stops at the same true FP64 residual ||eta - D psi|| <= tol ||eta||.
-extern "C" int lqcd_factorized_propagators(lqcd_lattice* L, const lqcd_split* split, const int x_src[4], int n_f,
-                                           const int* field_ids, double* fact, double* corr,
-                                           const lqcd_solver_params* params, lqcd_solver_stats* stats,
-                                           void* stream) {
-  RC(check_lat(L));
-  if (!split || !x_src || !fact || n_f < 1 || !field_ids) {
-    lq_set_error("factorized_propagators: null argument or n_fields < 1");
-    return LQCD_EBADARG;
-  }
+//   full = D^{-1} eta                                                 (eq. observable_factorization)
+// in four batched stages, each holding the systems of one kind:
+//   A1  Gamma from the point sources, 12 n_f systems shared by every overlap;
+//   A2  Gammabar_d from the point sources, 12 n_f n_d systems, each started
+//       from the Gamma solution (zero on DeltaGamma_d): its residual lives on
+//       the first slice of DeltaGamma_d only; its boundary slice gives
+//       chi = D_dGamma* psi|_Gamma;
+//   B   Gamma* from chi, 12 n_f n_d systems;
+//   C   the full lattice from the point sources, 12 n_f systems, started from
+//       fact of the last overlap: the residual eta - D fact vanishes off the two
+//       slices next to the cut, where it is as small as the propagator across it.
+// The starting iterates change the iteration counts, not the solutions: every
+// system stops at the same true FP64 residual ||eta - D psi|| <= tol ||eta||.
+// fact: [n_d][n_f][12][V][4][3]; full: [n_f][12][V][4][3] or NULL (then stage C
+// is skipped); with sub_fact, full receives full - fact of the last overlap.
+// stats (host, 4 per field, or NULL): Gamma, Gammabar, Gamma*, full, each the
+// worst over the field's columns and overlaps.
+int factorized_run(lqcd_lattice* L, lqcd_slab G, lqcd_slab Gs, int n_d, const int* d1s, int4 xs, int n_f,
+                   const int* field_ids, double* fact, double* full, bool sub_fact, const lqcd_solver_params& prm,
+                   lqcd_solver_stats* stats, cudaStream_t st) {
   const int T = L->dims[0];
-  const lqcd_slab G = split->gamma, Gs = split->gamma_star, Dl = split->delta;
-  const bool has_delta = Dl.t1 >= Dl.t0;
-  if (G.t0 != 0 || G.t1 < 0 || Gs.t0 != G.t1 + 1 || Gs.t1 != T - 1 ||
-      (has_delta && (Dl.t0 != G.t1 + 1 || Dl.t1 >= T - 1))) {
-    lq_set_error("factorized_propagator: need Gamma = 0..g1, Gamma* = g1+1..T-1, DeltaGamma = g1+1..d1 (d1 < T-1)");
+  const long long V = L->V, S3 = L->S3;
+  const size_t col_words = (size_t)V * 12;  // one propagator column (complex128 words)
+  const int NF = 12 * n_f;                  // systems of one overlap
+  const int ND = NF * n_d;                  // output slot = (d * n_f + field index) * 12 + column
+  const lqcd_slab Full = {0, T - 1};
+  const double t_start = now_s();
+  std::vector<lqcd_slab> Gb(n_d);
+  std::vector<bool> has_delta(n_d);
+  for (int d = 0; d < n_d; d++) {
+    has_delta[d] = d1s[d] > G.t1;
+    Gb[d] = lqcd_slab{0, has_delta[d] ? d1s[d] : G.t1};
+  }
+
+  CK(cudaMemsetAsync(fact, 0, sizeof(double2) * (size_t)ND * col_words, st));
+  // compact boundary source chi[slot][2][slice site][12] (two time slices per system)
+  DBuf chi;
+  RC(chi.alloc(sizeof(double2) * (size_t)ND * 2 * (size_t)S3 * 12, st));
+  auto make = [&](lqcd_slab dom, int d) {
+    std::vector<SysSpec> sp;
+    for (int j = 0; j < n_f; j++)
+      for (int c = 0; c < 12; c++) {
+        SysSpec q{dom, field_ids[j], d, c, xs};
+        q.out = (d * n_f + j) * 12 + c;
+        sp.push_back(q);
+      }
+    return sp;
+  };
+  // natural-order device pointers of each system's slab inside the columns of `base`
+  auto col_ptrs = [&](const std::vector<SysSpec>& sp, int k0, int n, double* base, DBuf& d, int slot_of_d = -1) -> int {
+    std::vector<void*> p(n);
+    for (int q = 0; q < n; q++) {
+      const SysSpec& y = sp[k0 + q];
+      const int slot = slot_of_d < 0 ? y.out : (slot_of_d * n_f + (y.out / 12) % n_f) * 12 + y.col;
+      p[q] = (double2*)base + (size_t)slot * col_words + (size_t)y.dom.t0 * S3 * 12;
+    }
+    return upload_ptrs(d, p, st);
+  };
+  auto point_fill = [&](const std::vector<SysSpec>& sp) -> FillFn {
+    return [&, sp_ptr = &sp](BatchStore& B, int k0, double2* be, double2* bo) -> int {
+      SrcArrays s;
+      RC(s.upload(*sp_ptr, k0, B.b.nsys, st));
+      return lq_point_source(L, B.b, s.cols.as<int>(), s.xsrc.as<int4>(), be, bo, st);
+    };
+  };
+  // starting iterate read from fact (natural order) on each system's slab
+  auto fact_guess = [&](const std::vector<SysSpec>& sp, int slot_of_d) -> GuessFn {
+    return [&, sp_ptr = &sp, slot_of_d](BatchStore& B, int k0, double2* xe, double2* xo) -> int {
+      DBuf d;
+      RC(col_ptrs(*sp_ptr, k0, B.b.nsys, fact, d, slot_of_d));
+      return lq_nat_to_eo(L, B.b, d.as<const double2*>(), xe, xo, st);
+    };
+  };
+  auto chi_sink = [&](const std::vector<SysSpec>& sp, BatchStore& B, int k0, const double2* xe,
+                      const double2* xo) -> int {
+    SrcArrays s;
+    RC(s.upload(sp, k0, B.b.nsys, st));
+    return lq_boundary_chi(L, B.b, s.outs.as<int>(), G.t1, xe, xo, chi.as<double2>(), st);
+  };
+
+  // A1: Gamma (eq. quark_prop_I), written into fact of every overlap; an
+  // overlap that is empty takes its chi from this solve
+  const std::vector<SysSpec> sa1 = make(G, 0);
+  SinkFn sink_a1 = [&](BatchStore& B, int k0, const double2* xe, const double2* xo) -> int {
+    for (int d = 0; d < n_d; d++) {
+      DBuf dp;
+      RC(col_ptrs(sa1, k0, B.b.nsys, fact, dp, d));
+      RC(lq_eo_to_nat(L, B.b, xe, xo, dp.as<double2* const>(), 1.0, st));
+      if (!has_delta[d]) {
+        std::vector<SysSpec> sd(sa1.begin() + k0, sa1.begin() + k0 + B.b.nsys);
+        for (auto& y : sd) y.out += d * NF;
+        RC(chi_sink(sd, B, 0, xe, xo));
+      }
+    }
+    return 0;
+  };
+  SolveOut o_g, o_gb, o_gs, o_full;
+  RC(solve_waves(L, sa1, false, prm, point_fill(sa1), sink_a1, o_g, st));
+  // A2: Gammabar_d, started from the Gamma solution (eq. quark_prop_II)
+  std::vector<SysSpec> sa2;
+  for (int d = 0; d < n_d; d++)
+    if (has_delta[d]) {
+      auto v = make(Gb[d], d);
+      sa2.insert(sa2.end(), v.begin(), v.end());
+    }
+  if (!sa2.empty()) {
+    SinkFn sink_a2 = [&](BatchStore& B, int k0, const double2* xe, const double2* xo) -> int {
+      return chi_sink(sa2, B, k0, xe, xo);
+    };
+    RC(solve_waves(L, sa2, false, prm, point_fill(sa2), sink_a2, o_gb, st, fact_guess(sa2, -1)));
+  }
+  // B: Gamma* from chi; fact on Gamma* is -zeta (eq. quark_prop_II)
+  std::vector<SysSpec> sb;
+  for (int d = 0; d < n_d; d++) {
+    auto v = make(Gs, d);
+    sb.insert(sb.end(), v.begin(), v.end());
+  }
+  FillFn fill_b = [&](BatchStore& B, int k0, double2* be, double2* bo) -> int {
+    SrcArrays s;
+    RC(s.upload(sb, k0, B.b.nsys, st));
+    return lq_chi_to_eo(L, B.b, s.outs.as<int>(), G.t1, chi.as<double2>(), be, bo, st);
+  };
+  SinkFn sink_b = [&](BatchStore& B, int k0, const double2* xe, const double2* xo) -> int {
+    DBuf d;
+    RC(col_ptrs(sb, k0, B.b.nsys, fact, d));
+    return lq_eo_to_nat(L, B.b, xe, xo, d.as<double2* const>(), -1.0, st);
+  };
+  RC(solve_waves(L, sb, false, prm, fill_b, sink_b, o_gs, st));
+  const double t_b1 = now_s();
+  // C: the full lattice, started from fact of the last overlap
+  if (full) {
+    const std::vector<SysSpec> sc = make(Full, 0);
+    SinkFn sink_c = [&](BatchStore& B, int k0, const double2* xe, const double2* xo) -> int {
+      DBuf d;
+      RC(col_ptrs(sc, k0, B.b.nsys, full, d));
+      return lq_eo_to_nat(L, B.b, xe, xo, d.as<double2* const>(), 1.0, st);
+    };
+    RC(solve_waves(L, sc, false, prm, point_fill(sc), sink_c, o_full, st, fact_guess(sc, n_d - 1)));
+    if (sub_fact)  // full - fact of the last overlap
+      RC(lq_sub_inplace((double2*)full, (const double2*)fact + (size_t)(n_d - 1) * NF * col_words,
+                        (long long)NF * V * 12, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  const double secs = now_s() - t_start;
+  if (verbose())
+    fprintf(stderr, "[lqcd] factorized (%d fields, %d overlaps): domains %.1f ms, full %.1f ms\n", n_f, n_d,
+            1e3 * (t_b1 - t_start), 1e3 * (now_s() - t_b1));
+  if (stats) {
+    // per field: the worst over its columns (and overlaps) of each stage
+    auto of_field = [&](const SolveOut& o, const std::vector<SysSpec>& sp, int j) {
+      SolveOut r;
+      for (size_t k = 0; k < sp.size() && k < o.iters.size(); k++)
+        if ((sp[k].out / 12) % n_f == j) {
+          r.iters.push_back(o.iters[k]);
+          r.cycles.push_back(o.cycles[k]);
+          r.status.push_back(o.status[k]);
+          r.res.push_back(o.res[k]);
+        }
+      return r;
+    };
+    for (int j = 0; j < n_f; j++) {
+      lqcd_solver_stats* sj = stats + 4 * j;
+      SolveOut og = of_field(o_g, sa1, j), ogb = sa2.empty() ? og : of_field(o_gb, sa2, j), ogs = of_field(o_gs, sb, j);
+      fill_stats(og, 0, (int)og.iters.size(), secs, &sj[0]);
+      fill_stats(ogb, 0, (int)ogb.iters.size(), secs, &sj[1]);
+      fill_stats(ogs, 0, (int)ogs.iters.size(), secs, &sj[2]);
+      if (full) {
+        SolveOut oc = of_field(o_full, make(Full, 0), j);
+        fill_stats(oc, 0, (int)oc.iters.size(), secs, &sj[3]);
+      } else {
+        memset(&sj[3], 0, sizeof(lqcd_solver_stats));
+      }
+    }
+  }
+  int w = worst_status(o_g);
+  if (!w) w = worst_status(o_gb);
+  if (!w) w = worst_status(o_gs);
+  if (!w && full) w = worst_status(o_full);
+  if (w) lq_set_error("factorized_propagator: some solves did not reach the tolerance");
+  return w;
+}
+
+int check_factorized_args(const lqcd_lattice* L, const lqcd_split* split, const int x_src[4], int n_f,
+                          const int* field_ids) {
+  if (!split || !x_src || n_f < 1 || !field_ids) {
+    lq_set_error("factorized_propagator: null argument or n_fields < 1");
     return LQCD_EBADARG;
   }
+  RC(check_split(L, split, "factorized_propagator"));
+  const lqcd_slab G = split->gamma;
   if (x_src[0] < G.t0 || x_src[0] > G.t1) {
     lq_set_error("factorized_propagator: the source must lie in Gamma");
     return LQCD_EBADARG;
@@ -902,127 +1066,80 @@ extern "C" int lqcd_factorized_propagators(lqcd_lattice* L, const lqcd_split* sp
       lq_set_error("factorized_propagator: field index not loaded");
       return LQCD_ENOFIELD;
     }
-  const double t_start = now_s();
-  cudaStream_t st = (cudaStream_t)stream;
-  lqcd_solver_params prm = default_params(params);
-  const lqcd_slab Gb = {0, has_delta ? Dl.t1 : G.t1};
-  const lqcd_slab Full = {0, T - 1};
-  const bool want_corr = corr != nullptr;
-  const int4 xs = make_int4(x_src[0], x_src[1], x_src[2], x_src[3]);
-  const long long V = L->V, S3 = L->S3;
-  const size_t col_words = (size_t)V * 12;  // one propagator column (complex128 words)
-  const int NS = 12 * n_f;                  // systems per stage; output slot = field index * 12 + column
+  return 0;
+}
 
-  CK(cudaMemsetAsync(fact, 0, sizeof(double2) * (size_t)NS * col_words, st));
-  // compact boundary source chi[slot][2][slice site][12] (two time slices per system)
-  DBuf chi;
-  RC(chi.alloc(sizeof(double2) * (size_t)NS * 2 * (size_t)S3 * 12, st));
-  auto stage = [&](lqcd_slab dom) {
-    std::vector<SysSpec> sp;
-    for (int j = 0; j < n_f; j++)
-      for (int c = 0; c < 12; c++) {
-        SysSpec q{dom, field_ids[j], 0, c, xs};
-        q.out = 12 * j + c;
-        sp.push_back(q);
-      }
-    return sp;
-  };
-  // natural-order device pointers of slab `dom` inside the columns of `base` for the wave's systems
-  auto col_ptrs = [&](const std::vector<SysSpec>& sp, int k0, int n, double* base, lqcd_slab dom, DBuf& d) -> int {
-    std::vector<void*> p(n);
-    for (int q = 0; q < n; q++) p[q] = (double2*)base + (size_t)sp[k0 + q].out * col_words + (size_t)dom.t0 * S3 * 12;
-    return upload_ptrs(d, p, st);
-  };
-  auto point_fill = [&](const std::vector<SysSpec>& sp) -> FillFn {
-    return [&, sp_ptr = &sp](BatchStore& B, int k0, double2* be, double2* bo) -> int {
-      SrcArrays s;
-      RC(s.upload(*sp_ptr, k0, B.b.nsys, st));
-      return lq_point_source(L, B.b, s.cols.as<int>(), s.xsrc.as<int4>(), be, bo, st);
-    };
-  };
-  // starting iterate read from fact (natural order) on the stage's slab
-  auto fact_guess = [&](const std::vector<SysSpec>& sp, lqcd_slab dom) -> GuessFn {
-    return [&, sp_ptr = &sp, dom](BatchStore& B, int k0, double2* xe, double2* xo) -> int {
-      DBuf d;
-      RC(col_ptrs(*sp_ptr, k0, B.b.nsys, fact, dom, d));
-      return lq_nat_to_eo(L, B.b, d.as<const double2*>(), xe, xo, st);
-    };
-  };
-  auto chi_sink = [&](const std::vector<SysSpec>& sp) {
-    return [&, sp_ptr = &sp](BatchStore& B, int k0, const double2* xe, const double2* xo) -> int {
-      SrcArrays s;
-      RC(s.upload(*sp_ptr, k0, B.b.nsys, st));
-      return lq_boundary_chi(L, B.b, s.outs.as<int>(), G.t1, xe, xo, chi.as<double2>(), st);
-    };
-  };
+}  // namespace
 
-  // A1: Gamma (eq. quark_prop_I); without an overlap it is also Gammabar
-  const std::vector<SysSpec> sa1 = stage(G);
-  SinkFn sink_a1 = [&](BatchStore& B, int k0, const double2* xe, const double2* xo) -> int {
-    DBuf d;
-    RC(col_ptrs(sa1, k0, B.b.nsys, fact, G, d));
-    RC(lq_eo_to_nat(L, B.b, xe, xo, d.as<double2* const>(), 1.0, st));
-    if (!has_delta) RC(chi_sink(sa1)(B, k0, xe, xo));
-    return 0;
-  };
-  SolveOut o_g, o_gb, o_gs, o_full;
-  const double t_a0 = now_s();
-  RC(solve_waves(L, sa1, false, prm, point_fill(sa1), sink_a1, o_g, st));
-  // A2: Gammabar, started from the Gamma solution (eq. quark_prop_II)
-  const std::vector<SysSpec> sa2 = stage(Gb);
-  if (has_delta) {
-    SinkFn sink_a2 = chi_sink(sa2);
-    RC(solve_waves(L, sa2, false, prm, point_fill(sa2), sink_a2, o_gb, st, fact_guess(sa2, Gb)));
-  } else {
-    o_gb = o_g;
+extern "C" int lqcd_factorized_propagators(lqcd_lattice* L, const lqcd_split* split, const int x_src[4], int n_f,
+                                           const int* field_ids, double* fact, double* corr,
+                                           const lqcd_solver_params* params, lqcd_solver_stats* stats,
+                                           void* stream) {
+  RC(check_lat(L));
+  if (!fact) {
+    lq_set_error("factorized_propagator: null fact");
+    return LQCD_EBADARG;
   }
-  const double t_a1 = now_s();
-  // B: Gamma* from chi; fact on Gamma* is -zeta (eq. quark_prop_II)
-  const std::vector<SysSpec> sb = stage(Gs);
-  FillFn fill_b = [&](BatchStore& B, int k0, double2* be, double2* bo) -> int {
-    SrcArrays s;
-    RC(s.upload(sb, k0, B.b.nsys, st));
-    return lq_chi_to_eo(L, B.b, s.outs.as<int>(), G.t1, chi.as<double2>(), be, bo, st);
-  };
-  SinkFn sink_b = [&](BatchStore& B, int k0, const double2* xe, const double2* xo) -> int {
-    DBuf d;
-    RC(col_ptrs(sb, k0, B.b.nsys, fact, Gs, d));
-    return lq_eo_to_nat(L, B.b, xe, xo, d.as<double2* const>(), -1.0, st);
-  };
-  RC(solve_waves(L, sb, false, prm, fill_b, sink_b, o_gs, st));
-  const double t_b1 = now_s();
-  // C: the full lattice, started from fact; corr first receives D^{-1} eta
-  const std::vector<SysSpec> sc = stage(Full);
-  if (want_corr) {
-    SinkFn sink_c = [&](BatchStore& B, int k0, const double2* xe, const double2* xo) -> int {
-      DBuf d;
-      RC(col_ptrs(sc, k0, B.b.nsys, corr, Full, d));
-      return lq_eo_to_nat(L, B.b, xe, xo, d.as<double2* const>(), 1.0, st);
-    };
-    RC(solve_waves(L, sc, false, prm, point_fill(sc), sink_c, o_full, st, fact_guess(sc, Full)));
-    RC(lq_sub_inplace((double2*)corr, (const double2*)fact, (long long)NS * V * 12, st));  // corr = full - fact
+  RC(check_factorized_args(L, split, x_src, n_f, field_ids));
+  const bool has_delta = split->delta.t1 >= split->delta.t0;
+  const int d1 = has_delta ? split->delta.t1 : split->gamma.t1;
+  return factorized_run(L, split->gamma, split->gamma_star, 1, &d1, make_int4(x_src[0], x_src[1], x_src[2], x_src[3]),
+                        n_f, field_ids, fact, corr, true, default_params(params), stats, (cudaStream_t)stream);
+}
+
+// Sec. 6 eq. nucleon_prop_hierarchical for one gauge field: the factorized
+// propagators of n_d nested overlaps in one batched run (Gamma and the full
+// lattice solved once), then the nucleon point correlators of each and of the
+// full propagator, and the terms of the expansion.
+extern "C" int lqcd_nucleon_hierarchy(lqcd_lattice* L, const lqcd_split* split, int n_d, const int* delta_t1,
+                                      const int x_src[4], int field, double* C, const lqcd_solver_params* params,
+                                      lqcd_solver_stats* stats, void* stream) {
+  RC(check_lat(L));
+  if (!C || n_d < 1 || n_d > 16 || !delta_t1) {
+    lq_set_error("nucleon_hierarchy: bad arguments (1 <= n_d <= 16)");
+    return LQCD_EBADARG;
   }
-  CK(cudaStreamSynchronize(st));
-  const double secs = now_s() - t_start;
-  if (verbose())
-    fprintf(stderr, "[lqcd] factorized (%d fields): setup %.1f ms, Gamma + Gammabar %.1f ms, Gamma* %.1f ms, "
-            "full %.1f ms\n", n_f, 1e3 * (t_a0 - t_start), 1e3 * (t_a1 - t_a0), 1e3 * (t_b1 - t_a1),
-            1e3 * (now_s() - t_b1));
-  if (stats)
-    for (int j = 0; j < n_f; j++) {
-      lqcd_solver_stats* sj = stats + 4 * j;
-      fill_stats(o_g, 12 * j, 12, secs, &sj[0]);   // Gamma
-      fill_stats(o_gb, 12 * j, 12, secs, &sj[1]);  // Gammabar
-      fill_stats(o_gs, 12 * j, 12, secs, &sj[2]);  // Gamma*
-      if (want_corr) fill_stats(o_full, 12 * j, 12, secs, &sj[3]);
-      else memset(&sj[3], 0, sizeof(lqcd_solver_stats));
+  RC(check_factorized_args(L, split, x_src, 1, &field));
+  const int T = L->dims[0];
+  const lqcd_slab G = split->gamma, Gs = split->gamma_star;
+  for (int d = 0; d < n_d; d++)
+    if (delta_t1[d] <= G.t1 || delta_t1[d] >= T - 1 || (d > 0 && delta_t1[d] <= delta_t1[d - 1])) {
+      lq_set_error("nucleon_hierarchy: need g1 < delta_t1[0] < delta_t1[1] < ... < T-1");
+      return LQCD_EBADARG;
     }
-  int w = worst_status(o_g);
-  if (!w) w = worst_status(o_gb);
-  if (!w) w = worst_status(o_gs);
-  if (!w && want_corr) w = worst_status(o_full);
-  if (w) lq_set_error("factorized_propagator: some solves did not reach the tolerance");
-  return w;
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long V = L->V;
+  const size_t prop_words = (size_t)12 * V * 12;
+  // fact of every overlap followed by the full propagator: n_d + 1 propagators back to back
+  DBuf props, partial, Wd;
+  RC(props.alloc(sizeof(double2) * prop_words * (n_d + 1), st));
+  double2* fact = props.as<double2>();
+  double2* full = fact + prop_words * n_d;
+  lqcd_solver_stats st4[4];
+  RC(factorized_run(L, G, Gs, n_d, delta_t1, make_int4(x_src[0], x_src[1], x_src[2], x_src[3]), 1, &field,
+                    (double*)fact, (double*)full, false, default_params(params), stats ? st4 : nullptr, st));
+  if (stats) memcpy(stats, st4, sizeof st4);
+  RC(partial.alloc(sizeof(double2) * (size_t)lq_nucleon_point_partial_words(L, n_d + 1, T), st));
+  RC(Wd.alloc(sizeof(double2) * (size_t)(n_d + 1) * T * 2, st));
+  RC(lq_nucleon_point(L, n_d + 1, fact, 0, T, partial.as<double2>(), Wd.as<double2>(), st));
+  std::vector<double2> W((size_t)(n_d + 1) * T * 2);
+  CK(cudaMemcpyAsync(W.data(), Wd.p, sizeof(double2) * W.size(), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  // C^(p)(t) = W1 - W2; terms C^(0), C^(d) - C^(d-1), C - C^(n_d - 1), then C
+  auto corr_of = [&](int p, int t) {
+    const double2 a = W[((size_t)p * T + t) * 2], b = W[((size_t)p * T + t) * 2 + 1];
+    return make_double2(a.x - b.x, a.y - b.y);
+  };
+  double2* out = (double2*)C;
+  for (int t = 0; t < T; t++) {
+    for (int k = 0; k <= n_d; k++) {
+      const double2 cur = corr_of(k, t);
+      const double2 prev = k == 0 ? make_double2(0.0, 0.0) : corr_of(k - 1, t);
+      out[(size_t)k * T + t] = make_double2(cur.x - prev.x, cur.y - prev.y);
+    }
+    out[(size_t)(n_d + 1) * T + t] = corr_of(n_d, t);
+  }
+  return 0;
 }
 
 extern "C" int lqcd_factorized_propagator(lqcd_lattice* L, const lqcd_split* split, const int x_src[4], int field,

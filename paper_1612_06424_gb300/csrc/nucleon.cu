@@ -22,6 +22,12 @@ constexpr int XS = 8;          // sites per shared-memory stage
 constexpr int FLUSH = 8;       // stages per first-level partial sum (64 sites)
 constexpr int TOT_BYTES = 16 * 256 * 8;  // dynamic shared memory of the second-level sums
 
+#define RC_LAUNCH()                     \
+  do {                                  \
+    const int r_ = launched_here();     \
+    if (r_ != 0) return r_;             \
+  } while (0)
+
 int launched_here() {
   lq_count_launch();
   const cudaError_t e = cudaGetLastError();
@@ -248,7 +254,167 @@ __global__ void k_level_mean(long long size, int count, const double2* in, doubl
   }
 }
 
+// The two nucleon Wick contractions from a point source to every sink y of a
+// time slice (the contractions behind eq. nucleon_prop_factorized), one warp
+// per site y, FP64.  S(y) = the 12 x 12 propagator matrix at y,
+// S_{(mu a),(nu b)} = prop[3 nu + b][y][mu][a], staged in shared memory; with
+// the non-zero entries of C g5 (mu -> nu(mu), sign) and of g5 P_- (M above):
+//   W1 = sum_{cc'} T^{cc'} U^{cc'},
+//     T^{cc'} = sum eps_{abc} eps_{a'b'c'} cg5(mu) cg5(mu') S_{mu a, nu(mu') b'} S_{nu(mu) b, mu' a'},
+//     U^{cc'} = sum_{gam del} M_{gam del} S_{del c, gam c'};
+//   W2 = sum eps_{abc} eps_{a'b'c'} cg5(mu) cg5(mu') M_{gam del}
+//            S_{mu a, nu(mu') b'} S_{nu(mu) b, gam c'} S_{del c, mu' a'}.
+// Each block sums its sites; partial[prop][slice][block] = (W1, W2).
+constexpr int NP_WARPS = 4;
+
+LQ_DI double2 cmul_d(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+
+__global__ void __launch_bounds__(32 * NP_WARPS) k_nucleon_point(int S3, long long V, const double2* prop,
+                                                                 long long prop_stride, int t0, double2* partial) {
+  __shared__ double2 sm[NP_WARPS][144];
+  __shared__ double2 red[NP_WARPS][2];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int site = blockIdx.x * NP_WARPS + w;  // site within the slice
+  const int slice = blockIdx.y;
+  const double2* P = prop + (long long)blockIdx.z * prop_stride;
+  const bool on = site < S3;
+  const long long y = (long long)(t0 + slice) * S3 + site;
+  if (on)
+    for (int q = lane; q < 144; q += 32) {
+      const int col = q / 12, e = q - col * 12;
+      sm[w][q] = P[((long long)col * V + y) * 12 + e];
+    }
+  __syncwarp();
+  // S_{(mu a),(nu b)} = sm[(3 nu + b) * 12 + 3 mu + a]
+  auto Sx = [&](int mu, int a, int nu, int b) { return sm[w][(3 * nu + b) * 12 + 3 * mu + a]; };
+  const int nu_of[4] = {1, 0, 3, 2};
+  const double cg[4] = {-1.0, 1.0, -1.0, 1.0};
+  // g5 P_-: row gam has entries at del = gam % 2 and gam % 2 + 2, value +1/2 (gam < 2) or -1/2
+  const int perm[6][3] = {{0, 1, 2}, {1, 2, 0}, {2, 0, 1}, {0, 2, 1}, {2, 1, 0}, {1, 0, 2}};
+  const double psg[6] = {1, 1, 1, -1, -1, -1};
+  double2 w1 = make_double2(0.0, 0.0), w2 = make_double2(0.0, 0.0);
+  if (on) {
+    // W1: 36 tasks (c, c', mu), each a 16-term part of T^{cc'} times U^{cc'}
+    for (int task = lane; task < 36; task += 32) {
+      const int c = task / 12, cp = (task / 4) % 3, mu = task % 4;
+      const int a0 = (c + 1) % 3, b0 = (c + 2) % 3, ap0 = (cp + 1) % 3, bp0 = (cp + 2) % 3;
+      double2 t = make_double2(0.0, 0.0);
+      for (int o = 0; o < 2; o++) {
+        const int a = o ? b0 : a0, b = o ? a0 : b0;
+        const double so = o ? -1.0 : 1.0;  // eps_{abc}
+        for (int op = 0; op < 2; op++) {
+          const int ap = op ? bp0 : ap0, bp = op ? ap0 : bp0;
+          const double sop = op ? -1.0 : 1.0;  // eps_{a'b'c'}
+          for (int mup = 0; mup < 4; mup++) {
+            const double f = so * sop * cg[mu] * cg[mup];
+            const double2 p = cmul_d(Sx(mu, a, nu_of[mup], bp), Sx(nu_of[mu], b, mup, ap));
+            t.x += f * p.x;
+            t.y += f * p.y;
+          }
+        }
+      }
+      double2 u = make_double2(0.0, 0.0);
+      for (int gam = 0; gam < 4; gam++) {
+        const double m = gam < 2 ? 0.5 : -0.5;
+        for (int k = 0; k < 2; k++) {
+          const double2 v = Sx(gam % 2 + 2 * k, c, gam, cp);
+          u.x += m * v.x;
+          u.y += m * v.y;
+        }
+      }
+      const double2 tu = cmul_d(t, u);
+      w1.x += tu.x;
+      w1.y += tu.y;
+    }
+    // W2: 36 colour pairs x 4 mu x 4 mu' x 8 (gam, del) = 4608 terms, 144 per lane
+    for (int e = lane; e < 4608; e += 32) {
+      const int pc = e / 128, r = e % 128;
+      const int mu = r / 32, mup = (r / 8) % 4, gd = r % 8;
+      const int gam = gd / 2, del = gam % 2 + 2 * (gd % 2);
+      const int* pa = perm[pc / 6];
+      const int* pb = perm[pc % 6];
+      const double f = psg[pc / 6] * psg[pc % 6] * cg[mu] * cg[mup] * (gam < 2 ? 0.5 : -0.5);
+      const double2 p = cmul_d(cmul_d(Sx(mu, pa[0], nu_of[mup], pb[1]), Sx(nu_of[mu], pa[1], gam, pb[2])),
+                               Sx(del, pa[2], mup, pb[0]));
+      w2.x += f * p.x;
+      w2.y += f * p.y;
+    }
+  }
+  double v[4] = {w1.x, w1.y, w2.x, w2.y};
+#pragma unroll
+  for (int q = 0; q < 4; q++)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+  if (lane == 0) {
+    red[w][0] = make_double2(v[0], v[1]);
+    red[w][1] = make_double2(v[2], v[3]);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double2 r1 = make_double2(0.0, 0.0), r2 = make_double2(0.0, 0.0);
+    for (int q = 0; q < NP_WARPS; q++) {
+      r1.x += red[q][0].x;
+      r1.y += red[q][0].y;
+      r2.x += red[q][1].x;
+      r2.y += red[q][1].y;
+    }
+    const long long o = (((long long)blockIdx.z * gridDim.y + slice) * gridDim.x + blockIdx.x) * 2;
+    partial[o] = r1;
+    partial[o + 1] = r2;
+  }
+}
+
+// W[p][t] = sum over the blocks of (prop p, slice t), in block order.
+__global__ void k_nucleon_point_sum(int nblk, int n_t, int n_prop, const double2* partial, double2* W) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_t * n_prop) return;
+  double2 r1 = make_double2(0.0, 0.0), r2 = make_double2(0.0, 0.0);
+  const double2* p = partial + (long long)i * nblk * 2;
+  for (int b = 0; b < nblk; b++) {
+    r1.x += p[2 * b].x;
+    r1.y += p[2 * b].y;
+    r2.x += p[2 * b + 1].x;
+    r2.y += p[2 * b + 1].y;
+  }
+  W[2 * i] = r1;
+  W[2 * i + 1] = r2;
+}
+
 }  // namespace
+
+int lq_nucleon_point(const lqcd_lattice* L, int n_prop, const double2* prop, int t0, int n_t, double2* partial,
+                     double2* W, cudaStream_t st) {
+  const int S3 = (int)L->S3;
+  const int nblk = (S3 + NP_WARPS - 1) / NP_WARPS;
+  k_nucleon_point<<<dim3((unsigned)nblk, (unsigned)n_t, (unsigned)n_prop), 32 * NP_WARPS, 0, st>>>(
+      S3, L->V, prop, (long long)12 * L->V * 12, t0, partial);
+  RC_LAUNCH();
+  k_nucleon_point_sum<<<(unsigned)((n_t * n_prop + 127) / 128), 128, 0, st>>>(nblk, n_t, n_prop, partial, W);
+  return launched_here();
+}
+
+long long lq_nucleon_point_partial_words(const lqcd_lattice* L, int n_prop, int n_t) {
+  return (long long)((L->S3 + NP_WARPS - 1) / NP_WARPS) * n_t * n_prop * 2;
+}
+
+extern "C" int lqcd_nucleon_point(lqcd_lattice* L, int n_prop, const double* prop, int t0, int n_t, double* W,
+                                  void* stream) {
+  if (!L || !prop || !W || n_prop < 1 || n_t < 1 || t0 < 0 || t0 + n_t > L->dims[0] || n_prop > 65535) {
+    lq_set_error("nucleon_point: bad arguments (1 <= n_prop, slices t0..t0+n_t-1 inside the lattice)");
+    return LQCD_EBADARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  void* partial = nullptr;
+  const size_t bytes = sizeof(double2) * (size_t)lq_nucleon_point_partial_words(L, n_prop, n_t);
+  if (cudaMallocAsync(&partial, bytes, st) != cudaSuccess) {
+    cudaGetLastError();
+    lq_set_error("nucleon_point: device allocation failed");
+    return LQCD_ENOMEM;
+  }
+  const int rc = lq_nucleon_point(L, n_prop, (const double2*)prop, t0, n_t, (double2*)partial, (double2*)W, st);
+  cudaFreeAsync(partial, st);
+  return rc;
+}
 
 extern "C" int lqcd_level_mean(long long size, int count, const double* in, double* out, void* stream) {
   if (!in || !out || size < 1 || count < 1) {

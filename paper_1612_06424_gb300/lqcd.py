@@ -92,6 +92,9 @@ def lib() -> ctypes.CDLL:
     L.lqcd_schur_boundary.argtypes = [vp, ctypes.POINTER(SplitC), c, ip, vp, vp, vp]
     L.lqcd_schur_solve.argtypes = [vp, ctypes.POINTER(SplitC), c, ip, vp, vp, ctypes.POINTER(ParamsC),
                                    ctypes.POINTER(StatsC), vp]
+    L.lqcd_nucleon_point.argtypes = [vp, c, vp, c, c, vp, vp]
+    L.lqcd_nucleon_hierarchy.argtypes = [vp, ctypes.POINTER(SplitC), c, ip, ip, c, vp, ctypes.POINTER(ParamsC),
+                                         ctypes.POINTER(StatsC), vp]
     L.lqcd_link_force.argtypes = [vp, ctypes.POINTER(Slab), c, vp, vp, dp, ctypes.POINTER(ParamsC),
                                   ctypes.POINTER(StatsC), vp]
     L.lqcd_point_propagators.argtypes = [vp, c, ctypes.POINTER(Slab), ip, ip, ip, vp, ctypes.POINTER(ParamsC),
@@ -299,6 +302,32 @@ class Lattice:
                                       _dev(chi.contiguous(), "chi"), _dev(out, "fact"), ctypes.byref(p), st,
                                       _stream(stream)))
         return out, [s.as_dict() for s in st]
+
+    def nucleon_point(self, props: torch.Tensor, t0: int = 0, n_t: int | None = None, stream=None):
+        """(W1, W2) per sink time slice of point-source propagators props [n, 12, V, 4, 3] (or [12, V, 4, 3]);
+        returns complex128 [n, n_t, 2] on the propagators' device.  The correlator is W1 - W2."""
+        p = props if props.dim() == 5 else props.unsqueeze(0)
+        n_t = self.T - t0 if n_t is None else n_t
+        W = torch.empty((p.shape[0], n_t, 2), dtype=torch.complex128, device=p.device)
+        _check(lib().lqcd_nucleon_point(self._h, p.shape[0], _dev(p.contiguous(), "props"), t0, n_t, _dev(W, "W"),
+                                        _stream(stream)))
+        return W
+
+    def nucleon_hierarchy(self, gamma, gamma_star, delta_ends, x_src, field: int = 0,
+                          params: SolverParams | None = None, stream=None):
+        """Eq. nucleon_prop_hierarchical (Sec. 6): the terms C^(0), C^(1) - C^(0), ..., C^(rest) [n_d + 1, T]
+        of the nucleon correlator from the point source x_src, for the nested overlaps DeltaGamma_d =
+        gamma[1]+1 .. delta_ends[d]; returns (terms, full C [T], stats) as numpy complex128."""
+        n = len(delta_ends)
+        C = np.zeros((n + 2, self.T), dtype=np.complex128)
+        sp = self._split(gamma, gamma_star, None)
+        st = (StatsC * 4)()
+        p = (params or SolverParams()).c()
+        _check(lib().lqcd_nucleon_hierarchy(self._h, ctypes.byref(sp), n, (ctypes.c_int * n)(*delta_ends),
+                                            (ctypes.c_int * 4)(*x_src), field, ctypes.c_void_p(C.ctypes.data),
+                                            ctypes.byref(p), st, _stream(stream)))
+        names = ["gamma", "gamma_bar", "gamma_star", "full"]
+        return C[:n + 1], C[n + 1], {k: s.as_dict() for k, s in zip(names, st)}
 
     def dslash_bench(self, doms, field_ids, precision: int = 32, reps: int = 20, stream=None):
         """(ms per launch, algorithmic bytes per launch, flops per launch) of the solver's hop kernel."""

@@ -136,7 +136,7 @@ class LatticeStages:
 
     def __init__(self, lat, gamma, gamma_star, x_src, field_ids, delta=None, params=None):
         self.lat = lat
-        self.gamma, self.gamma_star, self.delta = tuple(gamma), tuple(gamma_star), delta
+        self.G, self.GS, self.delta = tuple(gamma), tuple(gamma_star), delta
         self.gbar = (0, delta[1] if delta is not None and delta[1] >= delta[0] else gamma[1])
         self.x_src = tuple(x_src)
         self.field_ids = list(field_ids)
@@ -157,14 +157,13 @@ class LatticeStages:
         return sol.view(n, -1, 4, 3)
 
     def gamma_and_gbar(self, units):
-        return self._points(units, self.gamma), self._points(units, self.gbar)
+        return self._points(units, self.G), self._points(units, self.gbar)
 
     def boundary(self, psi_gbar, units):
-        return self.lat.schur_boundary(psi_gbar.contiguous(), self.gamma, self.gamma_star, self._fields(units),
-                                       self.delta)
+        return self.lat.schur_boundary(psi_gbar.contiguous(), self.G, self.GS, self._fields(units), self.delta)
 
     def gamma_star(self, chi, units):
-        out, _ = self.lat.schur_solve(chi, self.gamma, self.gamma_star, self._fields(units), self.delta, self.params)
+        out, _ = self.lat.schur_solve(chi, self.G, self.GS, self._fields(units), self.delta, self.params)
         return out
 
     def full(self, units):

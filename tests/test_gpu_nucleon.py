@@ -130,3 +130,58 @@ def test_multilevel_nucleon_matches_oracle_estimator():
             prod = lambda a, b: -np.einsum(pat + ",gd,ijkd->", a, g5pm, b)
             want = oracle.multilevel_estimator([bx[:, 0]], [by[:, iy]], [[0.0]], prod)
             assert abs(W[0, iy, q] - want) <= 1e-12 * abs(want)
+
+
+def test_nucleon_point_correlator_matches_oracle():
+    """lqcd_nucleon_point (FP64, one warp per site) on random 12-column propagators against the
+    oracle's two Wick contractions written as definitions, per sink time slice: 1e-12 of the
+    largest |W| (the same FP64 products summed in another order)."""
+    lqcd = _lq()
+    dims = (6, 4, 4, 6)  # 96 sites per slice: 24 blocks of four sites (every extent is even, so a
+    # slice always fills whole blocks)
+    lat = lqcd.Lattice(dims, "open")
+    rng = np.random.default_rng(31)
+    V = int(np.prod(dims))
+    props = (rng.standard_normal((2, 12, V, 4, 3)) + 1j * rng.standard_normal((2, 12, V, 4, 3))) / np.sqrt(2)
+    W = lat.nucleon_point(_cuda(props)).cpu().numpy()
+    for p in range(2):
+        ref = oracle.nucleon_point_correlator(props[p], dims[0])
+        assert np.abs(W[p] - ref).max() <= 1e-12 * np.abs(ref).max(), p
+    # a range of slices gives the same per-slice sums
+    W2 = lat.nucleon_point(_cuda(props), t0=2, n_t=3).cpu().numpy()
+    assert np.abs(W2 - W[:, 2:5]).max() == 0.0
+    lat.close()
+    dims = (4, 2, 2, 6)
+    lat = lqcd.Lattice(dims, "open")
+    V = int(np.prod(dims))
+    p1 = (rng.standard_normal((12, V, 4, 3)) + 1j * rng.standard_normal((12, V, 4, 3)))
+    W = lat.nucleon_point(_cuda(p1)).cpu().numpy()[0]
+    ref = oracle.nucleon_point_correlator(p1, dims[0])
+    assert np.abs(W - ref).max() <= 1e-12 * np.abs(ref).max()
+    lat.close()
+
+
+def test_nucleon_hierarchy_matches_oracle():
+    """Sec. 6 eq. nucleon_prop_hierarchical on 8 x 4^3 (Wilson-clover kappa 0.13): Gamma = t 0..2,
+    Gamma* = 3..7, nested overlaps ending at t = 3, 4, 5, source (1,1,0,2).  The GPU's terms and full
+    correlator against the oracle's (factorized propagators by oracle solves, contractions as
+    definitions); both solve to 1e-12, so the cubic correlators agree to ~1e-10 relative: 1e-8 of
+    max |C| allowed.  The terms telescope to C on the GPU as well."""
+    lqcd = _lq()
+    dims = (8, 4, 4, 4)
+    U = inputs.random_su3_field(dims, 0.4, 33)
+    lat = lqcd.Lattice(dims, "open")
+    lat.set_gauge(U, 0.13, 1.0)
+    x_src = (1, 1, 0, 2)
+    terms, full, st = lat.nucleon_hierarchy((0, 2), (3, 7), [3, 4, 5], x_src,
+                                            params=lqcd.SolverParams(tol=1e-12, precision=64))
+    for k in ("gamma", "gamma_bar", "gamma_star", "full"):
+        assert st[k]["status"] == 0 and st[k]["true_residual"] <= 1e-12, (k, st[k])
+    op = oracle.Operator(dims, U, 0.13, 1.0)
+    eta = inputs.point_sources(dims, x_src)
+    t_ref, _, full_ref = oracle.nucleon_hierarchy(op, (0, 2), (3, 7), [3, 4, 5], eta)
+    scale = np.abs(full_ref).max()
+    assert np.abs(full - full_ref).max() <= 1e-8 * scale
+    assert np.abs(terms - t_ref).max() <= 1e-8 * scale
+    assert np.abs(terms.sum(axis=0) - full).max() <= 1e-13 * scale
+    lat.close()

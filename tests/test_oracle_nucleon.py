@@ -76,6 +76,47 @@ def test_factorized_equals_propagator_form():
     assert abs(w1 - w2) > 1e-6 * abs(w1)        # the two contractions differ
 
 
+def test_point_correlator_equals_block_form_on_a_projected_propagator():
+    """With the projected propagator S(y,x) = -sum_i eta_i(y) xi_i^T(x) and one source site x, the
+    point correlator (the two contractions written as definitions) equals the block form of eq.
+    nucleon_prop_factorized with the source block taken at that single site."""
+    op = _op()
+    rng = np.random.default_rng(9)
+    n = 4
+    xi = rng.standard_normal((n, 32, 4, 3)) + 1j * rng.standard_normal((n, 32, 4, 3))
+    eta = rng.standard_normal((n, 32, 4, 3)) + 1j * rng.standard_normal((n, 32, 4, 3))
+    x = 1 * S3 + 5
+    # S columns: S[(3 nu + b), y, mu, a] = -sum_i eta_i(y)[mu, a] conj(xi_i(x)[nu, b])
+    S = -np.einsum("iyma,inb->nbyma", eta, np.conj(xi[:, x])).reshape(12, 32, 4, 3)
+    W = oracle.nucleon_point_correlator(S, DIMS[0])
+    xi_site = np.zeros_like(xi)  # xi at the source site only
+    xi_site[:, x] = xi[:, x]
+    for y0 in range(DIMS[0]):
+        # the block form sums the source block over slice 1; xi_site vanishes there except at x
+        w1, w2 = oracle.nucleon_factorized(op, xi_site, eta, 1, y0)
+        assert abs(W[y0, 0] - w1) <= 1e-12 * max(1.0, abs(w1))
+        assert abs(W[y0, 1] - w2) <= 1e-12 * max(1.0, abs(w2))
+    assert np.abs(W).max() > 1e-3
+
+
+def test_hierarchy_terms_telescope_and_shrink_with_the_overlap():
+    """The terms of eq. nucleon_prop_hierarchical are formed in the printed order and sum to the
+    full correlator; and on this field the factorized correlators on Gamma* approach the full
+    one as the overlap DeltaGamma grows (the suppression with Delta that Sec. 6 reports)."""
+    dims = (8, 2, 2, 2)
+    U = inputs.random_su3_field(dims, 0.3, 43)
+    op = oracle.Operator(dims, U, 0.12, 0.0)
+    eta = inputs.point_sources(dims, (1, 0, 0, 0))
+    terms, corr, full = oracle.nucleon_hierarchy(op, (0, 2), (3, 7), [4, 5, 6], eta)
+    assert terms.shape == (4, 8)
+    assert np.abs(terms.sum(axis=0) - full).max() <= 1e-13 * np.abs(full).max()
+    assert np.abs(terms[1] - (corr[1] - corr[0])).max() == 0.0
+    # the factorized correlators approach the full one as the overlap grows (Sec. 6 hierarchy)
+    far = slice(3, 8)
+    errs = [np.abs(c[far] - full[far]).max() for c in corr]
+    assert errs[0] > errs[1] > errs[2]
+
+
 def test_multilevel_estimator_special_cases():
     """n1 = 1 gives the plain estimator mean_i(O_G O_G* + O_corr); for a bilinear product the
     level-1 average equals the mean over all n1^2 (j, k) pairs (the exchange that makes the
