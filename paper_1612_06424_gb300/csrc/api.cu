@@ -54,6 +54,17 @@ struct DBuf {
     st = s;
     if (bytes == 0) bytes = 16;
     cudaError_t e = cudaMallocAsync(&p, bytes, s);
+    if (e == cudaErrorMemoryAllocation) {
+      // The pool keeps the blocks of earlier waves mapped; when they are too
+      // small for this request they only block it.  Wait for every pending
+      // free, hand the pool's unused memory back to the driver and retry.
+      cudaGetLastError();
+      int dev = 0;
+      cudaMemPool_t pool;
+      if (cudaDeviceSynchronize() == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess &&
+          cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess && cudaMemPoolTrimTo(pool, 0) == cudaSuccess)
+        e = cudaMallocAsync(&p, bytes, s);
+    }
     if (e != cudaSuccess) {
       p = nullptr;
       cudaGetLastError();
@@ -246,6 +257,8 @@ int solve_core(lqcd_lattice* L, BatchStore& B, bool dag, const lqcd_solver_param
 
   // stencil variant for this batch shape (autotuned once per shape)
   b.hop_variant = lq_tune_hop(L, b, P, clov, te, p, v, st);
+  if (verbose())
+    fprintf(stderr, "[lqcd] stencil variant %d for P=%d nsys=%d max_n=%lld\n", b.hop_variant, P, n, b.max_n);
   // |eta|^2 of each system (both parities)
   std::fill(B.h_active.begin(), B.h_active.end(), 1);
   RC(B.push_active(st));

@@ -525,10 +525,9 @@ LQ_DI void hop_pipe_step(HopRaw<P> (&buf)[D + 1], const Geom& g, const SysDesc& 
   if constexpr (K + 1 < 8) hop_pipe_step<P, DAG, K + 1, D>(buf, g, sd, f, pout, cb, j, x, in, inn, w0, w1, acc);
 }
 
-template <int P, bool DAG>
+template <int P, bool DAG, int D>
 LQ_DI void hop_sum_pipe(const Geom& g, const SysDesc& sd, const FieldPtrs& f, int pout, int cb, int j, const int x[4],
                         const void* in, const float* inn, cx<float> acc[12]) {
-  constexpr int D = HopDepth<P>::value;
   HopRaw<P> buf[D + 1];
   raw_fetch<P, 0>(buf[0], g, sd, f, pout, cb, j, x, in, inn);
   if constexpr (D > 1) raw_fetch<P, 1>(buf[1], g, sd, f, pout, cb, j, x, in, inn);
@@ -555,11 +554,11 @@ LQ_DI void hop_sum_pipe(const Geom& g, const SysDesc& sd, const FieldPtrs& f, in
   }
 }
 
-template <int P, bool DAG>
+template <int P, bool DAG, int D = HopDepth<P>::value>
 LQ_DI void hop_sum(const Geom& g, const SysDesc& sd, const FieldPtrs& f, int pout, int cb, int j, const int x[4],
                    const void* in, const float* inn, cx<typename Prec<P>::R> acc[12]) {
   if constexpr (P != 64 && LQ_HOP_PIPE)
-    hop_sum_pipe<P, DAG>(g, sd, f, pout, cb, j, x, in, inn, acc);
+    hop_sum_pipe<P, DAG, D>(g, sd, f, pout, cb, j, x, in, inn, acc);
   else
     hop_sum_f<P, DAG>(g, sd, f, pout, cb, x, GlobalFetch<P>{in, inn, sd.n}, acc);
 }
@@ -621,6 +620,40 @@ struct HopMinBlocks {
 #endif
 };
 
+// Launch configurations of the one-thread-per-site stencil that the autotuner
+// chooses from (lq_tune_hop): CFG 0 is the default above; CFG 1 and 2 trade
+// blocks per SM (the register cap) against the depth of the hop pipeline.
+// FP64 has the default only.
+template <int P, int CFG>
+struct HopCfg {
+  static constexpr int minb = HopMinBlocks<P>::value;
+  static constexpr int depth = HopDepth<P>::value;
+};
+template <>
+struct HopCfg<32, 1> {
+  static constexpr int minb = 3, depth = 3;
+};
+template <>
+struct HopCfg<32, 2> {
+  static constexpr int minb = 5, depth = 1;
+};
+template <>
+struct HopCfg<16, 1> {
+  static constexpr int minb = 4, depth = 3;
+};
+template <>
+struct HopCfg<16, 2> {
+  static constexpr int minb = 6, depth = 1;
+};
+constexpr int kHopCfgs = 3;
+
+struct HopArgs;
+// alternative configurations of the forward stencil (hop_tuned*.cu), cfg 1 or 2
+template <int P>
+int hop_lin_tuned(int cfg, bool clov, int red, int epi, dim3 gr, const HopArgs& a, cudaStream_t st);
+template <int P>
+int hop_clinv_tuned(int cfg, bool clov, int epi, dim3 gr, const HopArgs& a, cudaStream_t st);
+
 // Block reduction of NQ per-thread partial sums of type A (the kernel's own
 // precision: FP32 for the FP32 / FP16 solver, whose FP64 rate on this GPU is a
 // small fraction of its FP32 rate) through a warp-shuffle tree; the per-warp
@@ -666,8 +699,8 @@ LQ_DI float* nrm_ptr_w(float* pool, long long off) { return pool ? pool + off : 
 // fused per-system reduction over the stored values:
 //   RED_DOT_W: <w, out> (slots 0,1);  RED_TS: <out, y> (0,1) and |out|^2 (2);
 //   RED_NORM: |out|^2 (slot 2).
-template <int P, bool DAG, bool CLOV, int RED, int EPI>
-__global__ void __launch_bounds__(128, HopMinBlocks<P>::value) k_hop_lin(HopArgs a) {
+template <int P, bool DAG, bool CLOV, int RED, int EPI, int CFG = 0>
+__global__ void __launch_bounds__(128, (HopCfg<P, CFG>::minb)) k_hop_lin(HopArgs a) {
   typedef typename Prec<P>::R R;
   int s, by;
   grid_pos(a.nsys, s, by);
@@ -684,7 +717,8 @@ __global__ void __launch_bounds__(128, HopMinBlocks<P>::value) k_hop_lin(HopArgs
     if (EPI & EPI_X) {
       int x[4];
       eo_coords(a.g, cb, a.pout, x);
-      hop_sum<P, DAG>(a.g, sd, f, a.pout, cb, j, x, sys_ptr<P>(a.x, sd.off), nrm_ptr(a.xn, sd.off), res);
+      hop_sum<P, DAG, HopCfg<P, CFG>::depth>(a.g, sd, f, a.pout, cb, j, x, sys_ptr<P>(a.x, sd.off),
+                                             nrm_ptr(a.xn, sd.off), res);
       const R al = (R)a.alpha;
 #pragma unroll
       for (int k = 0; k < 12; k++) res[k] = al * res[k];
@@ -742,8 +776,8 @@ __global__ void __launch_bounds__(128, HopMinBlocks<P>::value) k_hop_lin(HopArgs
 
 // out = A^{-1} (alpha * D_hop x + beta * y) on even sites (pout = 0), terms
 // present per EPI (EPI_X, EPI_Y); A^{-1} = 1/diag without clover.
-template <int P, bool DAG, bool CLOV, int EPI>
-__global__ void __launch_bounds__(128, HopMinBlocks<P>::value) k_hop_clinv(HopArgs a) {
+template <int P, bool DAG, bool CLOV, int EPI, int CFG = 0>
+__global__ void __launch_bounds__(128, (HopCfg<P, CFG>::minb)) k_hop_clinv(HopArgs a) {
   typedef typename Prec<P>::R R;
   int s, by;
   grid_pos(a.nsys, s, by);
@@ -759,7 +793,8 @@ __global__ void __launch_bounds__(128, HopMinBlocks<P>::value) k_hop_clinv(HopAr
   if (EPI & EPI_X) {
     int x[4];
     eo_coords(a.g, cb, a.pout, x);
-    hop_sum<P, DAG>(a.g, sd, f, a.pout, cb, j, x, sys_ptr<P>(a.x, sd.off), nrm_ptr(a.xn, sd.off), res);
+    hop_sum<P, DAG, HopCfg<P, CFG>::depth>(a.g, sd, f, a.pout, cb, j, x, sys_ptr<P>(a.x, sd.off),
+                                           nrm_ptr(a.xn, sd.off), res);
     const R al = (R)a.alpha;
 #pragma unroll
     for (int k = 0; k < 12; k++) res[k] = al * res[k];

@@ -7,6 +7,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <vector>
 
 #include "blas.cuh"
 #include "internal.h"
@@ -53,22 +54,29 @@ static HopArgs hop_args(const lqcd_lattice* L, const Batch& b, int pout) {
   return a;
 }
 
-// FP32 stencil variant of a batch: 1 = one thread per site (k_hop_*), 2 = two
-// threads per site (k_hop2_*).  LQCD_HOP_SPLIT=1|2 forces one for every batch.
+// Stencil variant of a batch (FP32 / FP16; FP64 always 1):
+//   1 = one thread per site, default launch configuration (HopCfg 0),
+//   2 = two threads per site (k_hop2_*, FP32 only),
+//   3 / 4 = one thread per site in launch configuration HopCfg 1 / 2 (the
+//       forward operator; dagger launches keep configuration 0).
+// LQCD_HOP_VARIANT=1..4 (or the older LQCD_HOP_SPLIT=1|2) forces one for
+// every batch.
 static int forced_variant() {
   static int v = -1;
   if (v < 0) {
-    const char* e = getenv("LQCD_HOP_SPLIT");
-    v = (e && e[0] >= '1' && e[0] <= '2') ? e[0] - '0' : 0;
+    const char* e = getenv("LQCD_HOP_VARIANT");
+    if (!e) e = getenv("LQCD_HOP_SPLIT");
+    v = (e && e[0] >= '1' && e[0] <= '4') ? e[0] - '0' : 0;
   }
   return v;
 }
 
 static int variant_of(int P, const Batch& b) {
-  if (P != 32) return 1;
+  if (P == 64) return 1;
   const int f = forced_variant();
   const int v = f ? f : b.hop_variant;
-  return v == 2 ? 2 : 1;
+  if (v == 2) return P == 32 ? 2 : 1;
+  return (v == 3 || v == 4) ? v : 1;
 }
 
 int lq_hop_wps(int P, const Batch& b) { return variant_of(P, b) == 2 ? 2 : 1; }
@@ -139,9 +147,14 @@ int lq_hop_lin(int P, bool dag, bool clov, int red, const lqcd_lattice* L, const
     }
     return launched();
   }
-  int rc = P == 64 ? launch_lin_p<64>(dag, clov, red, epi, gr, a, st)
-         : P == 32 ? launch_lin_p<32>(dag, clov, red, epi, gr, a, st)
-                   : launch_lin_p<16>(dag, clov, red, epi, gr, a, st);
+  const int v = variant_of(P, b);
+  int rc;
+  if (!dag && v >= 3)
+    rc = P == 32 ? hop_lin_tuned<32>(v - 2, clov, red, epi, gr, a, st) : hop_lin_tuned<16>(v - 2, clov, red, epi, gr, a, st);
+  else
+    rc = P == 64 ? launch_lin_p<64>(dag, clov, red, epi, gr, a, st)
+       : P == 32 ? launch_lin_p<32>(dag, clov, red, epi, gr, a, st)
+                 : launch_lin_p<16>(dag, clov, red, epi, gr, a, st);
   if (rc) {
     lq_set_error("hop kernel: unsupported (reduction, epilogue) pair");
     return LQCD_EBADARG;
@@ -183,9 +196,14 @@ int lq_hop_clinv(int P, bool dag, bool clov, const lqcd_lattice* L, const Batch&
     }
     return launched();
   }
-  int rc = P == 64 ? launch_clinv_p<64>(dag, clov, epi, gr, a, st)
-         : P == 32 ? launch_clinv_p<32>(dag, clov, epi, gr, a, st)
-                   : launch_clinv_p<16>(dag, clov, epi, gr, a, st);
+  const int v = variant_of(P, b);
+  int rc;
+  if (!dag && v >= 3)
+    rc = P == 32 ? hop_clinv_tuned<32>(v - 2, clov, epi, gr, a, st) : hop_clinv_tuned<16>(v - 2, clov, epi, gr, a, st);
+  else
+    rc = P == 64 ? launch_clinv_p<64>(dag, clov, epi, gr, a, st)
+       : P == 32 ? launch_clinv_p<32>(dag, clov, epi, gr, a, st)
+                 : launch_clinv_p<16>(dag, clov, epi, gr, a, st);
   if (rc) {
     lq_set_error("clover-inverse hop kernel: unsupported epilogue");
     return LQCD_EBADARG;
@@ -552,7 +570,7 @@ void tune_store(int P, int n, long long m, int v) {
 }  // namespace
 
 int lq_tune_hop(const lqcd_lattice* L, const Batch& b, int P, bool clov, VecP x, VecP y, VecP out, cudaStream_t st) {
-  if (P != 32) return 1;
+  if (P == 64) return 1;
   if (forced_variant()) return forced_variant();
   const auto key = std::make_tuple(P, b.nsys, b.max_n);
   {
@@ -564,25 +582,38 @@ int lq_tune_hop(const lqcd_lattice* L, const Batch& b, int P, bool clov, VecP x,
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return 1;
   VecP none;
-  // both variants warmed, then timed in alternating rounds (5 launches each);
-  // the best round of each counts, and the two-thread variant must win by 5%
-  float best[3] = {1e30f, 1e30f, 1e30f};
+  // candidates: the default, the alternative launch configurations and (FP32)
+  // the two-thread kernel; each warmed, then timed in three alternating rounds
+  // of five launches of the solver's second half of D^ and of the clover-inverse
+  // first half; the best round of each counts, and a candidate must beat the
+  // default by 3% to be chosen
+  std::vector<int> cand = {1, 3, 4};
+  if (P == 32) cand.push_back(2);
+  std::vector<float> best(cand.size(), 1e30f);
   for (int round = -1; round < 3; round++)
-    for (int v = 1; v <= 2; v++) {
+    for (size_t c = 0; c < cand.size(); c++) {
       Batch t = b;
-      t.hop_variant = v;
+      t.hop_variant = cand[c];
       t.active = nullptr;  // time every system
       const int reps = round < 0 ? 1 : 5;
       cudaEventRecord(e0, st);
-      for (int r = 0; r < reps; r++)
+      for (int r = 0; r < reps; r++) {
+        lq_hop_clinv(P, false, clov, L, t, y, none, x, 1.0, 0.0, st);
         lq_hop_lin(P, false, clov, RED_NONE, L, t, 1, x, y, none, none, out, -0.25, 1.0, 0.0, st);
+      }
       cudaEventRecord(e1, st);
       cudaEventSynchronize(e1);
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
-      if (round >= 0 && ms < best[v]) best[v] = ms;
+      if (round >= 0 && ms < best[c]) best[c] = ms;
     }
-  const int pick = best[2] < 0.95f * best[1] ? 2 : 1;
+  int pick = 1;
+  float pick_ms = 0.97f * best[0];
+  for (size_t c = 1; c < cand.size(); c++)
+    if (best[c] < pick_ms) {
+      pick = cand[c];
+      pick_ms = best[c];
+    }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaGetLastError();

@@ -1,9 +1,13 @@
 """Every stencil variant the autotuner can pick, checked against the FP64 oracle.
 
-The variant is forced per process through LQCD_HOP_SPLIT (read once by the
+The variant is forced per process through LQCD_HOP_VARIANT (read once by the
 library), so each case runs in a child process:
-  1: one thread per site, 128 sites of one system per block;
-  2: two threads per site (FP32 only; FP16 falls back to 1).
+  1: one thread per site, 128 sites of one system per block, default launch
+     configuration (FP32: 4 blocks per SM, hop pipeline depth 2);
+  2: two threads per site (FP32 only; FP16 falls back to 1);
+  3, 4: one thread per site in the alternative launch configurations of the
+     forward operator (FP32: 3 blocks / depth 3 and 5 blocks / depth 1; FP16:
+     4 / 3 and 6 / 1); dagger launches keep the default.
 Each child applies the FP32 / FP16 operator on the whole lattice and on
 Dirichlet slabs (D and D^dag; tolerances of tests/test_gpu_parity.py) and
 solves a batch of five systems on mixed slabs in FP32 and FP16 to true
@@ -66,9 +70,55 @@ print("variant ok")
 """
 
 
-@pytest.mark.parametrize("variant", ["1", "2"])
+@pytest.mark.parametrize("variant", ["1", "2", "3", "4"])
 def test_stencil_variant_parity(variant):
-    env = dict(os.environ, LQCD_HOP_SPLIT=variant)
+    env = dict(os.environ, LQCD_HOP_VARIANT=variant)
+    env.pop("LQCD_HOP_SPLIT", None)
     r = subprocess.run([sys.executable, "-c", CHILD.replace("ROOT", repr(ROOT))], env=env, capture_output=True,
                        text=True, timeout=900)
     assert r.returncode == 0 and "variant ok" in r.stdout, r.stdout[-2000:] + r.stderr[-4000:]
+
+
+TUNE_CHILD = r"""
+import sys
+import numpy as np
+import torch
+sys.path.insert(0, ROOT)
+from paper_1612_06424_gb300 import build, inputs
+build.build()
+from paper_1612_06424_gb300 import lqcd
+
+dims = (8, 6, 6, 4)
+lat = lqcd.Lattice(dims, "open")
+lat.set_gauge(inputs.random_su3_field(dims, 0.4, 5), 0.13, 1.0)
+doms = [(0, 3), (2, 7), (0, 7)]
+srcs = inputs.gaussian_spinor(dims, 8, len(doms))
+packed = np.concatenate([srcs[k][inputs.slab_sites(dims, *d)] for k, d in enumerate(doms)])
+sol, st = lat.solve_block(torch.from_numpy(packed).cuda(), doms, [0] * 3, lqcd.SolverParams(tol=1e-10, precision=32))
+assert all(x["status"] == 0 for x in st)
+print("tune ok")
+"""
+
+
+def test_tuner_decisions_cached(tmp_path):
+    """The autotuner times every candidate on the solver's own batch shape, writes its decision to
+    LQCD_TUNE_CACHE ("P systems sites variant"), and a later process takes the decision from the
+    file instead of timing again (the decision it uses is the one written there)."""
+    cache = tmp_path / "tune.txt"
+    env = dict(os.environ, LQCD_TUNE_CACHE=str(cache), LQCD_VERBOSE="1")
+    env.pop("LQCD_HOP_SPLIT", None)
+    env.pop("LQCD_HOP_VARIANT", None)
+    code = TUNE_CHILD.replace("ROOT", repr(ROOT))
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0 and "tune ok" in r.stdout, r.stdout[-2000:] + r.stderr[-4000:]
+    lines = [l.split() for l in cache.read_text().splitlines() if l.strip()]
+    mine = [l for l in lines if l[0] == "32" and l[1] == "3"]
+    assert mine and all(int(l[3]) in (1, 2, 3, 4) for l in mine), lines
+    n_sites = mine[0][2]
+    # plant a different decision for that shape: the next process must use it
+    planted = 4 if int(mine[0][3]) != 4 else 3
+    cache.write_text(f"32 3 {n_sites} {planted}\n")
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0 and "tune ok" in r.stdout, r.stdout[-2000:] + r.stderr[-4000:]
+    assert f"stencil variant {planted} for P=32 nsys=3 max_n={n_sites}" in r.stderr, r.stderr[-3000:]
+    assert cache.read_text().strip() == f"32 3 {n_sites} {planted}"  # read, not re-timed
