@@ -225,6 +225,10 @@ int solve_core(lqcd_lattice* L, BatchStore& B, bool dag, const lqcd_solver_param
   Batch& b = B.b;
   const int n = b.nsys;
   const int P = prm.precision == 16 ? 16 : prm.precision == 32 ? 32 : 64;
+  // the FP64-accuracy operator of the defect correction (prepare, true residual,
+  // reconstruction): FP64 for the FP64 solver, double-float arithmetic on FP64
+  // data (about 48 significant bits, on the FP32 pipes) for the mixed ones
+  const int PD = P == 64 ? 64 : 65;
   const bool clov = L->csw != 0.0;
   const double tol = prm.tol > 0 ? prm.tol : 1e-10;
   const int max_iter = prm.max_iter > 0 ? prm.max_iter : 100000;
@@ -279,8 +283,8 @@ int solve_core(lqcd_lattice* L, BatchStore& B, bool dag, const lqcd_solver_param
   RC(B.push_sc(st));
 
   // prepare: bh_o = b_o + 1/2 H_oe A_ee^{-1} b_e
-  RC(lq_hop_clinv(64, dag, clov, L, b, none, v64(b_e), v64(t64), 0.0, 1.0, st));
-  RC(lq_hop_lin(64, dag, clov, lq::RED_NONE, L, b, 1, v64(t64), none, v64(b_o), none, v64(bh_o), 0.5, 0.0, 1.0, st));
+  RC(lq_hop_clinv(PD, dag, clov, L, b, none, v64(b_e), v64(t64), 0.0, 1.0, st));
+  RC(lq_hop_lin(PD, dag, clov, lq::RED_NONE, L, b, 1, v64(t64), none, v64(b_o), none, v64(bh_o), 0.5, 0.0, 1.0, st));
   if (!guess) CK(cudaMemsetAsync(x_o, 0, sizeof(double2) * (size_t)b.total * 12, st));
 
   std::vector<int> outer(n, 1);
@@ -299,8 +303,8 @@ int solve_core(lqcd_lattice* L, BatchStore& B, bool dag, const lqcd_solver_param
       RC(lq_norm2_64(b, r64, st));
       RC(lq_finalize(lq::FIN_NORM, b, 0, 0, 12, st));
     } else {
-      RC(lq_hop_clinv(64, dag, clov, L, b, v64(x_o), none, v64(t64), 1.0, 0.0, st));
-      RC(lq_hop_lin(64, dag, clov, lq::RED_NORM, L, b, 1, v64(t64), v64(x_o), v64(bh_o), none, v64(r64), 0.25, -1.0,
+      RC(lq_hop_clinv(PD, dag, clov, L, b, v64(x_o), none, v64(t64), 1.0, 0.0, st));
+      RC(lq_hop_lin(PD, dag, clov, lq::RED_NORM, L, b, 1, v64(t64), v64(x_o), v64(bh_o), none, v64(r64), 0.25, -1.0,
                     1.0, st));
       RC(lq_finalize(lq::FIN_NORM, b, 0, 0, 1, st));
     }
@@ -429,7 +433,7 @@ int solve_core(lqcd_lattice* L, BatchStore& B, bool dag, const lqcd_solver_param
   // the true FP64 residual is the one the last cycle recomputed from x_o.
   std::fill(B.h_active.begin(), B.h_active.end(), 1);
   RC(B.push_active(st));
-  RC(lq_hop_clinv(64, dag, clov, L, b, v64(x_o), v64(b_e), v64(x_e), 0.5, 1.0, st));
+  RC(lq_hop_clinv(PD, dag, clov, L, b, v64(x_o), v64(b_e), v64(x_e), 0.5, 1.0, st));
   for (int k = 0; k < n; k++) {
     out.res[k] = bb[k] > 0 ? std::sqrt(last_rr[k] / bb[k]) : 0.0;
     if (out.status[k] == 0 && !(out.res[k] <= tol)) out.status[k] = std::isfinite(out.res[k]) ? LQCD_ENOTCONVERGED : LQCD_ENAN;
@@ -767,7 +771,7 @@ extern "C" int lqcd_set_gauge(lqcd_lattice* L, int n_fields, const double* U, do
 extern "C" int lqcd_dslash(lqcd_lattice* L, int field, const lqcd_slab* dom, int dagger, int precision,
                            const double* in, double* out, void* stream) {
   RC(check_lat(L));
-  if (!in || !out || (precision != 64 && precision != 32 && precision != 16)) {
+  if (!in || !out || (precision != 64 && precision != 65 && precision != 32 && precision != 16)) {
     lq_set_error("dslash: bad arguments");
     return LQCD_EBADARG;
   }
@@ -785,11 +789,11 @@ extern "C" int lqcd_dslash(lqcd_lattice* L, int field, const lqcd_slab* dom, int
   RC(lq_nat_to_eo(L, b, ptr.as<const double2*>(), e.v(0), e.v(1), st));
   const bool clov = L->csw != 0.0;
   VecP none;
-  if (precision == 64) {
-    RC(lq_hop_lin(64, dagger, clov, lq::RED_NONE, L, b, 0, v64(e.v(1)), v64(e.v(0)), none, none, v64(e.v(2)), -0.5, 1.0,
-                  0.0, st));
-    RC(lq_hop_lin(64, dagger, clov, lq::RED_NONE, L, b, 1, v64(e.v(0)), v64(e.v(1)), none, none, v64(e.v(3)), -0.5, 1.0,
-                  0.0, st));
+  if (precision == 64 || precision == 65) {
+    RC(lq_hop_lin(precision, dagger, clov, lq::RED_NONE, L, b, 0, v64(e.v(1)), v64(e.v(0)), none, none, v64(e.v(2)),
+                  -0.5, 1.0, 0.0, st));
+    RC(lq_hop_lin(precision, dagger, clov, lq::RED_NONE, L, b, 1, v64(e.v(0)), v64(e.v(1)), none, none, v64(e.v(3)),
+                  -0.5, 1.0, 0.0, st));
   } else {
     PoolP q;
     RC(q.alloc(b, precision, 4, st));

@@ -72,7 +72,7 @@ static int forced_variant() {
 }
 
 static int variant_of(int P, const Batch& b) {
-  if (P == 64) return 1;
+  if (P == 64 || P == 65) return 1;
   const int f = forced_variant();
   const int v = f ? f : b.hop_variant;
   if (v == 2) return P == 32 ? 2 : 1;
@@ -149,7 +149,9 @@ int lq_hop_lin(int P, bool dag, bool clov, int red, const lqcd_lattice* L, const
   }
   const int v = variant_of(P, b);
   int rc;
-  if (!dag && v >= 3)
+  if (P == 65)
+    rc = hop_lin_df(dag, clov, red, epi, gr, a, st);
+  else if (!dag && v >= 3)
     rc = P == 32 ? hop_lin_tuned<32>(v - 2, clov, red, epi, gr, a, st) : hop_lin_tuned<16>(v - 2, clov, red, epi, gr, a, st);
   else
     rc = P == 64 ? launch_lin_p<64>(dag, clov, red, epi, gr, a, st)
@@ -198,7 +200,9 @@ int lq_hop_clinv(int P, bool dag, bool clov, const lqcd_lattice* L, const Batch&
   }
   const int v = variant_of(P, b);
   int rc;
-  if (!dag && v >= 3)
+  if (P == 65)
+    rc = hop_clinv_df(dag, clov, epi, gr, a, st);
+  else if (!dag && v >= 3)
     rc = P == 32 ? hop_clinv_tuned<32>(v - 2, clov, epi, gr, a, st) : hop_clinv_tuned<16>(v - 2, clov, epi, gr, a, st);
   else
     rc = P == 64 ? launch_clinv_p<64>(dag, clov, epi, gr, a, st)
@@ -570,7 +574,7 @@ void tune_store(int P, int n, long long m, int v) {
 }  // namespace
 
 int lq_tune_hop(const lqcd_lattice* L, const Batch& b, int P, bool clov, VecP x, VecP y, VecP out, cudaStream_t st) {
-  if (P == 64) return 1;
+  if (P == 64 || P == 65) return 1;
   if (forced_variant()) return forced_variant();
   const auto key = std::make_tuple(P, b.nsys, b.max_n);
   {
