@@ -663,8 +663,9 @@ def run_headline(args):
     ora = OracleIterations() if want_cpu else None  # host thread; overlaps the GPU work
     t0 = time.time()
     seed = _rank_seed(rank)
-    U0 = inputs.random_su3_field_device(dims, wl["eps"], 6 + seed, device="cuda")
-    Uf = inputs.inner_level_fields_device(U0, dims, [G, (DL[1] + 1, T - 1)], nf, wl["eps"], 7 + seed, frozen=DL)
+    U0 = inputs.random_su3_field_device(dims, wl["eps"], 6 + seed, device="cuda", rng="device")
+    Uf = inputs.inner_level_fields_device(U0, dims, [G, (DL[1] + 1, T - 1)], nf, wl["eps"], 7 + seed, frozen=DL,
+                                          rng="device")
     del U0
     torch.cuda.empty_cache()
     t_gen = time.time() - t0

@@ -94,13 +94,27 @@ def random_su3_field(dims, eps: float, seed: int, stream: int = 0,
     return out.reshape(V, 4, 3, 3)
 
 
+def _normals(n: int, seed: int, stream: int, device, rng: str):
+    """(n, 8) standard normals as a float64 tensor on `device`: numpy's Philox keyed by
+    (seed, stream) drawn on the host (rng="host", the draws of the numpy path), or torch's
+    generator on the device seeded from (seed, stream) (rng="device": the same law, other
+    draws, for large lattices where host draws dominate the set-up time)."""
+    import torch
+
+    if rng == "host":
+        return torch.from_numpy(_rng(seed, stream).standard_normal((n, 8))).to(device)
+    g = torch.Generator(device=device)
+    g.manual_seed((int(seed) * 0x9E3779B1 + int(stream) * 0x85EBCA77) & 0x7FFFFFFFFFFFFFFF)
+    return torch.randn((n, 8), dtype=torch.float64, device=device, generator=g)
+
+
 def _su3_torch(h, eps: float, torch_device):
-    """exp(i eps H) for H = sum_a h_a lambda_a / 2 (h: numpy (n, 8)), computed on a torch device,
-    then re-unitarised; returns a complex128 tensor (n, 3, 3) on that device."""
+    """exp(i eps H) for H = sum_a h_a lambda_a / 2 (h: numpy or torch (n, 8)), computed on a
+    torch device, then re-unitarised; returns a complex128 tensor (n, 3, 3) on that device."""
     import torch
 
     lam = torch.from_numpy(gell_mann() / 2).to(torch_device)
-    ht = torch.from_numpy(h).to(torch_device).to(torch.complex128)
+    ht = (h if isinstance(h, torch.Tensor) else torch.from_numpy(h)).to(torch_device).to(torch.complex128)
     H = torch.einsum("na,aij->nij", ht, lam)
     u = torch.linalg.matrix_exp(1j * eps * H)
     r0 = u[:, 0, :]
@@ -112,10 +126,11 @@ def _su3_torch(h, eps: float, torch_device):
     return torch.stack([r0, r1, r2], dim=-2)
 
 
-def random_su3_field_device(dims, eps: float, seed: int, device="cuda", stream: int = 0, chunk: int = 1 << 22):
-    """The field law of random_su3_field (same Philox draws) with the matrix
-    exponential done by torch on `device`; returns a complex128 tensor
-    [V, 4, 3, 3] there.  For large lattices, where the numpy path is slow."""
+def random_su3_field_device(dims, eps: float, seed: int, device="cuda", stream: int = 0, chunk: int = 1 << 22,
+                            rng: str = "host"):
+    """The field law of random_su3_field (rng="host": the same Philox draws) with the matrix
+    exponential done by torch on `device`; returns a complex128 tensor [V, 4, 3, 3] there.
+    For large lattices, where the numpy path is slow."""
     import torch
 
     V = int(np.prod(dims))
@@ -123,16 +138,15 @@ def random_su3_field_device(dims, eps: float, seed: int, device="cuda", stream: 
     out = torch.empty((n, 3, 3), dtype=torch.complex128, device=device)
     for k, lo in enumerate(range(0, n, chunk)):
         hi = min(n, lo + chunk)
-        h = _rng(seed, stream * 65536 + k).standard_normal((hi - lo, 8))
-        out[lo:hi] = _su3_torch(h, eps, out.device)
+        out[lo:hi] = _su3_torch(_normals(hi - lo, seed, stream * 65536 + k, out.device, rng), eps, out.device)
     return out.reshape(V, 4, 3, 3)
 
 
 def inner_level_fields_device(U0, dims, slabs, n_fields: int, eps: float, seed: int, frozen=None,
-                              chunk: int = 1 << 22, field_ids=None):
-    """inner_level_fields with the redrawn links exponentiated by torch on U0's device.
-    U0: complex128 tensor [V, 4, 3, 3]; returns [n, V, 4, 3, 3] on the same device for the
-    fields field_ids (default: all n_fields)."""
+                              chunk: int = 1 << 22, field_ids=None, rng: str = "host"):
+    """inner_level_fields with the redrawn links exponentiated by torch on U0's device (rng as in
+    random_su3_field_device).  U0: complex128 tensor [V, 4, 3, 3]; returns [n, V, 4, 3, 3] on the
+    same device for the fields field_ids (default: all n_fields)."""
     import torch
 
     T = dims[0]
@@ -156,10 +170,14 @@ def inner_level_fields_device(U0, dims, slabs, n_fields: int, eps: float, seed: 
         idx_t = torch.from_numpy(idx).to(U0.device)
         for q, j in enumerate(ids):
             flat = out[q].reshape(-1, 3, 3)
-            rng = _rng(seed, (d + 1) * 4096 + j)
-            for lo in range(0, idx.size, chunk):
+            if rng == "host":
+                gen = _rng(seed, (d + 1) * 4096 + j)
+            for k, lo in enumerate(range(0, idx.size, chunk)):
                 hi = min(idx.size, lo + chunk)
-                h = rng.standard_normal((hi - lo, 8))
+                if rng == "host":
+                    h = gen.standard_normal((hi - lo, 8))
+                else:
+                    h = _normals(hi - lo, seed, ((d + 1) * 4096 + j) * 65536 + k, U0.device, rng)
                 flat[idx_t[lo:hi]] = _su3_torch(h, eps, U0.device)
     return out
 
