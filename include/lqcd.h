@@ -87,11 +87,9 @@ typedef struct {
 typedef struct {
   double tol;            /* target relative true residual ||eta - D psi|| / ||eta||   */
   int max_iter;          /* bound on Krylov iterations per system (all cycles)        */
-  int precision;         /* 64: FP64 throughout; 32: FP32 inner solves with a defect
-                            correction on FP64 vectors whose operator runs in
-                            double-float arithmetic (LQCD_PREC_DFLOAT); 16: FP16
-                            vectors (per-site FP32 norm) and FP16 links in the inner
-                            solves, the same defect correction                       */
+  int precision;         /* 64: FP64 throughout; 32: FP32 inner solves with FP64
+                            defect correction; 16: FP16 vectors (per-site FP32 norm)
+                            and FP16 links in the inner solves, FP64 correction      */
   double inner_tol;      /* relative residual reduction per inner cycle (0: default) */
   int check_every;       /* iterations between host convergence checks (0: default) */
   int max_wave;          /* systems solved together at most (0: as many as fit in free
@@ -102,11 +100,9 @@ typedef struct {
   int iters;             /* inner Krylov iterations summed over cycles                */
   int cycles;            /* FP64 defect-correction cycles (true residual evaluations) */
   int status;            /* LQCD_OK, LQCD_ENOTCONVERGED, LQCD_EBREAKDOWN or LQCD_ENAN */
-  double true_residual;  /* ||eta - D psi||_2 / ||eta||_2 recomputed from the final
-                            iterate (even-odd: the odd half b^_o - D^ psi_o; the
-                            reconstructed even half is exact up to rounding): the
-                            operator in FP64 (precision 64) or double-float, the
-                            norms in FP64                                             */
+  double true_residual;  /* ||eta - D psi||_2 / ||eta||_2 recomputed in FP64 from the
+                            final iterate (even-odd: the odd half b^_o - D^ psi_o; the
+                            reconstructed even half is exact up to rounding)          */
   double seconds;        /* wall time of the call that produced this entry           */
 } lqcd_solver_stats;
 
@@ -133,18 +129,9 @@ int lqcd_destroy_lattice(lqcd_lattice *lat);
 int lqcd_set_gauge(lqcd_lattice *lat, int n_fields, const double *U, double kappa, double c_sw, int mem,
                    void *stream);
 
-/* Precision code of double-float arithmetic on FP64 data: each value is the
- * unevaluated sum of two FP32 numbers (about 48 significant bits), computed
- * with the error-free transformations TwoSum and TwoProduct on the FP32
- * pipes.  The mixed-precision solvers (precision 32 and 16) evaluate their
- * FP64-accuracy operator (prepare, true residual, reconstruction) this way;
- * precision 64 is plain FP64 throughout. */
-#define LQCD_PREC_DFLOAT 65
-
 /* out = D_L in (dagger = 0) or D_L^dag in (dagger = 1) for the slab dom
  * (NULL: the whole lattice, with the lattice's time BC) on field `field`,
- * evaluated in `precision` (64, LQCD_PREC_DFLOAT, 32 or 16) through the
- * even-odd packed data.
+ * evaluated in `precision` (64, 32 or 16) through the even-odd packed data.
  * in / out: device slab vectors (see "slab" above) in complex128.
  * Sec. 3 eq. block_inverse: D_L is the sub-block of D on the slab's sites. */
 int lqcd_dslash(lqcd_lattice *lat, int field, const lqcd_slab *dom, int dagger, int precision, const double *in,

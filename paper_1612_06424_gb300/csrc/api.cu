@@ -225,10 +225,6 @@ int solve_core(lqcd_lattice* L, BatchStore& B, bool dag, const lqcd_solver_param
   Batch& b = B.b;
   const int n = b.nsys;
   const int P = prm.precision == 16 ? 16 : prm.precision == 32 ? 32 : 64;
-  // the FP64-accuracy operator of the defect correction (prepare, true residual,
-  // reconstruction): FP64 for the FP64 solver, double-float arithmetic on FP64
-  // data (about 48 significant bits, on the FP32 pipes) for the mixed ones
-  const int PD = P == 64 ? 64 : 65;
   const bool clov = L->csw != 0.0;
   const double tol = prm.tol > 0 ? prm.tol : 1e-10;
   const int max_iter = prm.max_iter > 0 ? prm.max_iter : 100000;
@@ -258,6 +254,8 @@ int solve_core(lqcd_lattice* L, BatchStore& B, bool dag, const lqcd_solver_param
   DBuf dcnt;
   RC(dcnt.alloc(sizeof(int), st));
   VecP none;
+  const int PC = P == 64 ? 64 : 32;  // precision of the CGNR fallback's vectors
+  PoolP cgp;                         // its vectors, allocated when a system first needs them
 
   // stencil variant for this batch shape (autotuned once per shape)
   b.hop_variant = lq_tune_hop(L, b, P, clov, te, p, v, st);
@@ -283,8 +281,8 @@ int solve_core(lqcd_lattice* L, BatchStore& B, bool dag, const lqcd_solver_param
   RC(B.push_sc(st));
 
   // prepare: bh_o = b_o + 1/2 H_oe A_ee^{-1} b_e
-  RC(lq_hop_clinv(PD, dag, clov, L, b, none, v64(b_e), v64(t64), 0.0, 1.0, st));
-  RC(lq_hop_lin(PD, dag, clov, lq::RED_NONE, L, b, 1, v64(t64), none, v64(b_o), none, v64(bh_o), 0.5, 0.0, 1.0, st));
+  RC(lq_hop_clinv(64, dag, clov, L, b, none, v64(b_e), v64(t64), 0.0, 1.0, st));
+  RC(lq_hop_lin(64, dag, clov, lq::RED_NONE, L, b, 1, v64(t64), none, v64(b_o), none, v64(bh_o), 0.5, 0.0, 1.0, st));
   if (!guess) CK(cudaMemsetAsync(x_o, 0, sizeof(double2) * (size_t)b.total * 12, st));
 
   std::vector<int> outer(n, 1);
@@ -293,6 +291,12 @@ int solve_core(lqcd_lattice* L, BatchStore& B, bool dag, const lqcd_solver_param
   std::vector<double> prev_rr(n, INFINITY);
   std::vector<double> last_rr(n, 0.0);  // last FP64 residual |bh_o - Dhat x_o|^2 of each system
   std::vector<int> stall(n, 0);
+  // Krylov method per system: BiCGStab, or CG on the normal equations
+  // Dhat^dag Dhat e = Dhat^dag r once BiCGStab has stalled for 6 cycles (or for
+  // every system with LQCD_KRYLOV=cgnr).  CGNR converges on any nonsingular
+  // Dhat, at the price of the squared condition number.
+  static const bool force_cg = getenv("LQCD_KRYLOV") && std::string(getenv("LQCD_KRYLOV")) == "cgnr";
+  std::vector<int> use_cg(n, force_cg ? 1 : 0);
   for (int cycle = 0;; cycle++) {
     // true residual of the preconditioned system: r64 = bh_o - Dhat x_o (FP64);
     // at the first cycle without a guess x_o = 0 and r64 = bh_o needs no operator
@@ -303,8 +307,8 @@ int solve_core(lqcd_lattice* L, BatchStore& B, bool dag, const lqcd_solver_param
       RC(lq_norm2_64(b, r64, st));
       RC(lq_finalize(lq::FIN_NORM, b, 0, 0, 12, st));
     } else {
-      RC(lq_hop_clinv(PD, dag, clov, L, b, v64(x_o), none, v64(t64), 1.0, 0.0, st));
-      RC(lq_hop_lin(PD, dag, clov, lq::RED_NORM, L, b, 1, v64(t64), v64(x_o), v64(bh_o), none, v64(r64), 0.25, -1.0,
+      RC(lq_hop_clinv(64, dag, clov, L, b, v64(x_o), none, v64(t64), 1.0, 0.0, st));
+      RC(lq_hop_lin(64, dag, clov, lq::RED_NORM, L, b, 1, v64(t64), v64(x_o), v64(bh_o), none, v64(r64), 0.25, -1.0,
                     1.0, st));
       RC(lq_finalize(lq::FIN_NORM, b, 0, 0, 1, st));
     }
@@ -329,7 +333,12 @@ int solve_core(lqcd_lattice* L, BatchStore& B, bool dag, const lqcd_solver_param
       } else {
         stall[k] = rr > 0.25 * prev_rr[k] ? stall[k] + 1 : 0;
         prev_rr[k] = rr;
-        if (stall[k] >= 6) {
+        if (stall[k] >= 6 && !use_cg[k]) {  // BiCGStab stalled: continue with CGNR
+          if (verbose()) fprintf(stderr, "[lqcd] sys %d: BiCGStab stalled, switching to CGNR\n", k);
+          use_cg[k] = 1;
+          stall[k] = 0;
+          prev_rr[k] = INFINITY;
+        } else if (stall[k] >= 6) {
           out.status[k] = LQCD_ENOTCONVERGED;
           outer[k] = 0;
         }
@@ -338,94 +347,146 @@ int solve_core(lqcd_lattice* L, BatchStore& B, bool dag, const lqcd_solver_param
     }
     if (n_act == 0) break;
     const double t_in0 = now_s();
-    // inner solve of Dhat e = r64 in precision P
-    B.h_active = outer;
-    RC(B.push_active(st));
-    RC(lq_inner_init(P, b, r64, r, r0, p, xs, st));
+    std::vector<int> grp_b(n), grp_c(n);
+    int n_b = 0, n_c = 0;
+    for (int k = 0; k < n; k++) {
+      grp_b[k] = outer[k] && !use_cg[k];
+      grp_c[k] = outer[k] && use_cg[k];
+      n_b += grp_b[k];
+      n_c += grp_c[k];
+    }
     // the first FP32 cycle reduces the residual by inner_tol; later ones start
     // near the tolerance and aim 10x deeper, so one more FP64 check ends the
     // solve (FP16 cannot go deeper than inner_tol; FP64 aims at the floor)
     const double tau = (cycle == 0 || P == 16) ? inner_tol : 0.1 * inner_tol;
-    RC(lq_finalize(lq::FIN_INIT, b, tau * tau, 0.09 * tol * tol, lq_words_per_site(P), st));
     int it = 0;
     int budget = 0;
     for (int k = 0; k < n; k++)
       if (outer[k]) budget = std::max(budget, max_iter - out.iters[k]);
     budget = std::min(budget, cycle_cap);
-    // one BiCGStab iteration: 10 kernels, all scalars and flags on the device
-    auto iteration = [&](cudaStream_t s_) -> int {
-      RC(lq_hop_clinv(P, dag, clov, L, b, p, none, te, 1.0, 0.0, s_));
-      RC(lq_hop_lin(P, dag, clov, lq::RED_DOT_W, L, b, 1, te, p, none, r0, v, -0.25, 1.0, 0.0, s_));
-      RC(lq_finalize(lq::FIN_ALPHA, b, 0, 0, lq_hop_wps(P, b), s_));
-      RC(lq_bicg_s(P, b, r, v, s, s_));
-      RC(lq_hop_clinv(P, dag, clov, L, b, s, none, te, 1.0, 0.0, s_));
-      RC(lq_hop_lin(P, dag, clov, lq::RED_TS, L, b, 1, te, s, none, none, t, -0.25, 1.0, 0.0, s_));
-      RC(lq_finalize(lq::FIN_OMEGA, b, 0, 0, lq_hop_wps(P, b), s_));
-      RC(lq_bicg_xr(P, b, xs, p, s, t, r, r0, s_));
-      RC(lq_finalize(lq::FIN_BETA, b, 0, 0, lq_words_per_site(P), s_));
-      RC(lq_bicg_p(P, b, p, r, v, s_));
-      return 0;
-    };
     auto poll = [&](cudaStream_t s_) -> int {  // systems still iterating
       RC(lq_count_active(b, dcnt.as<int>(), s_));
       CK(cudaMemcpyAsync(cnt.h, dcnt.p, sizeof(int), cudaMemcpyDeviceToHost, s_));
       CK(cudaStreamSynchronize(s_));
       return 0;
     };
-    if (use_graph && budget >= 2 * check_every) {
-      // check_every iterations captured once as a CUDA graph on a private
-      // stream, replayed between host convergence checks (retired systems
-      // skip every kernel, so iterations past convergence change nothing)
-      cudaStream_t gs = L->graph_stream;
-      CK(cudaEventRecord(L->graph_event, st));
-      CK(cudaStreamWaitEvent(gs, L->graph_event, 0));
-      const long long c0 = lqcd_kernel_launches();
-      cudaGraph_t graph = nullptr;
-      CK(cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal));
-      int crc = 0;
-      for (int g = 0; g < check_every && !crc; g++) crc = iteration(gs);
-      cudaError_t ce = cudaStreamEndCapture(gs, &graph);
-      if (crc) return crc;
-      CK(ce);
-      const long long per_replay = lqcd_kernel_launches() - c0;
-      lq_count_launches(-per_replay);  // captured, not run
-      cudaGraphExec_t exec = nullptr;
-      cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
-      cudaGraphDestroy(graph);
-      CK(ie);
-      int grc = 0;
-      while (it < budget) {
-        if (cudaGraphLaunch(exec, gs) != cudaSuccess) {
-          lq_set_error("solve: CUDA graph launch failed");
-          grc = LQCD_ECUDA;
-          break;
+    if (n_b) {
+      // inner solve of Dhat e = r64 in precision P (BiCGStab)
+      B.h_active = grp_b;
+      RC(B.push_active(st));
+      RC(lq_inner_init(P, b, r64, r, r0, p, xs, st));
+      RC(lq_finalize(lq::FIN_INIT, b, tau * tau, 0.09 * tol * tol, lq_words_per_site(P), st));
+      // one BiCGStab iteration: 10 kernels, all scalars and flags on the device
+      auto iteration = [&](cudaStream_t s_) -> int {
+        RC(lq_hop_clinv(P, dag, clov, L, b, p, none, te, 1.0, 0.0, s_));
+        RC(lq_hop_lin(P, dag, clov, lq::RED_DOT_W, L, b, 1, te, p, none, r0, v, -0.25, 1.0, 0.0, s_));
+        RC(lq_finalize(lq::FIN_ALPHA, b, 0, 0, lq_hop_wps(P, b), s_));
+        RC(lq_bicg_s(P, b, r, v, s, s_));
+        RC(lq_hop_clinv(P, dag, clov, L, b, s, none, te, 1.0, 0.0, s_));
+        RC(lq_hop_lin(P, dag, clov, lq::RED_TS, L, b, 1, te, s, none, none, t, -0.25, 1.0, 0.0, s_));
+        RC(lq_finalize(lq::FIN_OMEGA, b, 0, 0, lq_hop_wps(P, b), s_));
+        RC(lq_bicg_xr(P, b, xs, p, s, t, r, r0, s_));
+        RC(lq_finalize(lq::FIN_BETA, b, 0, 0, lq_words_per_site(P), s_));
+        RC(lq_bicg_p(P, b, p, r, v, s_));
+        return 0;
+      };
+      if (use_graph && budget >= 2 * check_every) {
+        // check_every iterations captured once as a CUDA graph on a private
+        // stream, replayed between host convergence checks (retired systems
+        // skip every kernel, so iterations past convergence change nothing)
+        cudaStream_t gs = L->graph_stream;
+        CK(cudaEventRecord(L->graph_event, st));
+        CK(cudaStreamWaitEvent(gs, L->graph_event, 0));
+        const long long c0 = lqcd_kernel_launches();
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal));
+        int crc = 0;
+        for (int g = 0; g < check_every && !crc; g++) crc = iteration(gs);
+        cudaError_t ce = cudaStreamEndCapture(gs, &graph);
+        if (crc) return crc;
+        CK(ce);
+        const long long per_replay = lqcd_kernel_launches() - c0;
+        lq_count_launches(-per_replay);  // captured, not run
+        cudaGraphExec_t exec = nullptr;
+        cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        CK(ie);
+        int grc = 0;
+        while (it < budget) {
+          if (cudaGraphLaunch(exec, gs) != cudaSuccess) {
+            lq_set_error("solve: CUDA graph launch failed");
+            grc = LQCD_ECUDA;
+            break;
+          }
+          lq_count_launches(per_replay);
+          it += check_every;
+          if ((grc = poll(gs)) != 0) break;
+          if (*cnt.h == 0) break;
         }
-        lq_count_launches(per_replay);
-        it += check_every;
-        if ((grc = poll(gs)) != 0) break;
-        if (*cnt.h == 0) break;
+        cudaGraphExecDestroy(exec);
+        if (grc) return grc;
+        CK(cudaEventRecord(L->graph_event, gs));
+        CK(cudaStreamWaitEvent(st, L->graph_event, 0));
+      } else {
+        while (it < budget) {
+          RC(iteration(st));
+          it++;
+          if (it % check_every == 0 || it >= budget) {
+            RC(poll(st));
+            if (*cnt.h == 0) break;
+          }
+        }
       }
-      cudaGraphExecDestroy(exec);
-      if (grc) return grc;
-      CK(cudaEventRecord(L->graph_event, gs));
-      CK(cudaStreamWaitEvent(st, L->graph_event, 0));
-    } else {
-      while (it < budget) {
-        RC(iteration(st));
-        it++;
-        if (it % check_every == 0 || it >= budget) {
+      // x_o += e for the systems of this cycle
+      RC(B.pull_sc(st));
+      B.h_active = grp_b;
+      RC(B.push_active(st));
+      RC(lq_accum64(P, b, x_o, xs, st));
+      for (int k = 0; k < n; k++)
+        if (grp_b[k]) out.iters[k] += B.h_sc[k].iters;
+    }
+    if (n_c) {
+      // inner solve by CG on Dhat^dag Dhat e = Dhat^dag r64 (FP32 vectors for the
+      // FP32 / FP16 solvers, FP64 for the FP64 one), the same defect correction
+      if (!cgp.buf.p) RC(cgp.alloc(b, PC, 6, st));
+      VecP cxv = cgp.v(0), crv = cgp.v(1), cpv = cgp.v(2), cvv = cgp.v(3), czv = cgp.v(4), ctv = cgp.v(5);
+      B.h_active = grp_c;
+      RC(B.push_active(st));
+      RC(lq_inner_init(PC, b, r64, crv, czv, cpv, cxv, st));  // r = r64, x = 0
+      RC(lq_finalize(lq::FIN_INIT, b, tau * tau, 0.09 * tol * tol, lq_words_per_site(PC), st));
+      // z = Dhat^dag r, rho = |z|^2, p = z
+      RC(lq_hop_clinv(PC, !dag, clov, L, b, crv, none, ctv, 1.0, 0.0, st));
+      RC(lq_hop_lin(PC, !dag, clov, lq::RED_TS, L, b, 1, ctv, crv, none, none, czv, -0.25, 1.0, 0.0, st));
+      RC(lq_finalize(lq::FIN_CG_RHO, b, 0, 0, lq_hop_wps(PC, b), st));
+      RC(lq_cg_p(PC, b, cpv, czv, st));
+      int itc = 0;
+      while (itc < budget) {
+        // v = Dhat p, alpha = rho / |v|^2
+        RC(lq_hop_clinv(PC, dag, clov, L, b, cpv, none, ctv, 1.0, 0.0, st));
+        RC(lq_hop_lin(PC, dag, clov, lq::RED_TS, L, b, 1, ctv, cpv, none, none, cvv, -0.25, 1.0, 0.0, st));
+        RC(lq_finalize(lq::FIN_CG_ALPHA, b, 0, 0, lq_hop_wps(PC, b), st));
+        // x += alpha p, r -= alpha v
+        RC(lq_cg_xr(PC, b, cxv, cpv, crv, cvv, st));
+        RC(lq_finalize(lq::FIN_CG_R, b, 0, 0, lq_words_per_site(PC), st));
+        // z = Dhat^dag r, beta = |z|^2 / rho, p = z + beta p
+        RC(lq_hop_clinv(PC, !dag, clov, L, b, crv, none, ctv, 1.0, 0.0, st));
+        RC(lq_hop_lin(PC, !dag, clov, lq::RED_TS, L, b, 1, ctv, crv, none, none, czv, -0.25, 1.0, 0.0, st));
+        RC(lq_finalize(lq::FIN_CG_BETA, b, 0, 0, lq_hop_wps(PC, b), st));
+        RC(lq_cg_p(PC, b, cpv, czv, st));
+        itc++;
+        if (itc % check_every == 0 || itc >= budget) {
           RC(poll(st));
           if (*cnt.h == 0) break;
         }
       }
+      RC(B.pull_sc(st));
+      B.h_active = grp_c;
+      RC(B.push_active(st));
+      RC(lq_accum64(PC, b, x_o, cxv, st));
+      for (int k = 0; k < n; k++)
+        if (grp_c[k]) out.iters[k] += B.h_sc[k].iters;
+      it = std::max(it, itc);
     }
-    // x_o += e for the systems of this cycle
-    RC(B.pull_sc(st));
-    B.h_active = outer;
-    RC(B.push_active(st));
-    RC(lq_accum64(P, b, x_o, xs, st));
-    for (int k = 0; k < n; k++)
-      if (outer[k]) out.iters[k] += B.h_sc[k].iters;
     if (verbose()) fprintf(stderr, "[lqcd] cycle %d: inner %d its in %.2f ms\n", cycle, it, 1e3 * (now_s() - t_in0));
   }
   // reconstruct x_e = A_ee^{-1}(b_e + 1/2 H_eo x_o).  Then the even half of
@@ -433,7 +494,7 @@ int solve_core(lqcd_lattice* L, BatchStore& B, bool dag, const lqcd_solver_param
   // the true FP64 residual is the one the last cycle recomputed from x_o.
   std::fill(B.h_active.begin(), B.h_active.end(), 1);
   RC(B.push_active(st));
-  RC(lq_hop_clinv(PD, dag, clov, L, b, v64(x_o), v64(b_e), v64(x_e), 0.5, 1.0, st));
+  RC(lq_hop_clinv(64, dag, clov, L, b, v64(x_o), v64(b_e), v64(x_e), 0.5, 1.0, st));
   for (int k = 0; k < n; k++) {
     out.res[k] = bb[k] > 0 ? std::sqrt(last_rr[k] / bb[k]) : 0.0;
     if (out.status[k] == 0 && !(out.res[k] <= tol)) out.status[k] = std::isfinite(out.res[k]) ? LQCD_ENOTCONVERGED : LQCD_ENAN;
@@ -771,7 +832,7 @@ extern "C" int lqcd_set_gauge(lqcd_lattice* L, int n_fields, const double* U, do
 extern "C" int lqcd_dslash(lqcd_lattice* L, int field, const lqcd_slab* dom, int dagger, int precision,
                            const double* in, double* out, void* stream) {
   RC(check_lat(L));
-  if (!in || !out || (precision != 64 && precision != 65 && precision != 32 && precision != 16)) {
+  if (!in || !out || (precision != 64 && precision != 32 && precision != 16)) {
     lq_set_error("dslash: bad arguments");
     return LQCD_EBADARG;
   }
@@ -789,7 +850,7 @@ extern "C" int lqcd_dslash(lqcd_lattice* L, int field, const lqcd_slab* dom, int
   RC(lq_nat_to_eo(L, b, ptr.as<const double2*>(), e.v(0), e.v(1), st));
   const bool clov = L->csw != 0.0;
   VecP none;
-  if (precision == 64 || precision == 65) {
+  if (precision == 64) {
     RC(lq_hop_lin(precision, dagger, clov, lq::RED_NONE, L, b, 0, v64(e.v(1)), v64(e.v(0)), none, none, v64(e.v(2)),
                   -0.5, 1.0, 0.0, st));
     RC(lq_hop_lin(precision, dagger, clov, lq::RED_NONE, L, b, 1, v64(e.v(0)), v64(e.v(1)), none, none, v64(e.v(3)),

@@ -214,6 +214,52 @@ __global__ void __launch_bounds__(128) k_bicg_p_h(VecArgs va, void* p, float* pn
   Prec<16>::store(sys_ptr_w<16>(p, sd.off), nrm_ptr_w(pn, sd.off), sd.n, j, pv);
 }
 
+// CG on the normal equations (the fallback for systems whose BiCGStab
+// stalls): x += alpha p, r -= alpha v (v = D^ p), partial |r|^2 (slot 2).
+// alpha is real (stored in alpha.x).
+template <int P>
+__global__ void __launch_bounds__(128) k_cg_xr_w(VecArgs va, void* x, const void* p, void* r, const void* v) {
+  typedef Word<P> W;
+  typedef typename W::R R;
+  LQ_WORD_PROLOGUE(P)
+  R red[3] = {0, 0, 0};
+  if (valid) {
+    const R al = (R)va.sc[s].alpha.x;
+    cx<R> xv[W::NC], pv[W::NC], rv[W::NC], vv[W::NC];
+    W::get(wptr<P>(x, sd.off), i, xv);
+    W::get(wptr<P>(p, sd.off), i, pv);
+    W::get(wptr<P>(r, sd.off), i, rv);
+    W::get(wptr<P>(v, sd.off), i, vv);
+#pragma unroll
+    for (int k = 0; k < W::NC; k++) {
+      xv[k] = xv[k] + al * pv[k];
+      rv[k] = rv[k] - al * vv[k];
+      red[2] += rv[k].re * rv[k].re + rv[k].im * rv[k].im;
+    }
+    W::put(wptr_w<P>(x, sd.off), i, xv);
+    W::put(wptr_w<P>(r, sd.off), i, rv);
+  }
+  block_reduce_store<3, R>(red, va.partial + ((long long)s * va.pstride + by) * 4);
+}
+
+// p = z + beta p (beta real, in beta.x); beta = 0 copies z.
+template <int P>
+__global__ void __launch_bounds__(128) k_cg_p_w(VecArgs va, void* p, const void* z) {
+  typedef Word<P> W;
+  typedef typename W::R R;
+  LQ_WORD_PROLOGUE(P)
+  if (!valid) return;
+  const R be = (R)va.sc[s].beta.x;
+  cx<R> pv[W::NC], zv[W::NC];
+  W::get(wptr<P>(z, sd.off), i, zv);
+  if (be != (R)0) {
+    W::get(wptr<P>(p, sd.off), i, pv);
+#pragma unroll
+    for (int k = 0; k < W::NC; k++) zv[k] = zv[k] + be * pv[k];
+  }
+  W::put(wptr_w<P>(p, sd.off), i, zv);
+}
+
 // Word i = q*n + j of a precision-P system vector holds the complex numbers
 // q*NC .. q*NC+NC-1 of site j; complex c of site j is FP64 word c*n + j.
 LQ_DI void split_word(int i, int n, int& q, int& j) {
@@ -365,6 +411,11 @@ LQ_DI bool finite2(double2 a) { return isfinite(a.x) && isfinite(a.y); }
 //             on breakdown, NaN or divergence (rr > 1e8 rr0); else
 //             beta = (rho'/rho)(alpha/omega)
 //  FIN_NORM : rr = |r|^2 only
+//  CG on the normal equations (real scalars in .x):
+//  FIN_CG_RHO  : rho = |z|^2 (z = D^dag r), beta = 0 (the first direction is z)
+//  FIN_CG_ALPHA: alpha = rho / |v|^2 (v = D^ p); breakdown if |v|^2 is not positive
+//  FIN_CG_R    : rr = |r|^2; stop the system when rr <= target2, on NaN or divergence
+//  FIN_CG_BETA : beta = |z|^2 / rho, rho = |z|^2
 // tau2 / floor_rel2 are per call (FIN_INIT); floor_rel2 is relative to bb.
 // wps: words per site of the kernel that wrote the partials (1: one site per
 // thread), so that the system used ceil(n * wps / bdim) blocks.
@@ -427,6 +478,37 @@ __global__ void k_finalize(int mode, int nsys, const SysDesc* sys, int* active, 
     }
     case FIN_NORM:
       c.rr = v[2];
+      break;
+    case FIN_CG_RHO:
+      c.rho = make_double2(v[2], 0.0);
+      c.beta = make_double2(0.0, 0.0);
+      break;
+    case FIN_CG_ALPHA:
+      if (!(v[2] > 0.0) || !isfinite(v[2]) || !(c.rho.x > 0.0)) {
+        c.status = 1;
+        active[s] = 0;
+      } else {
+        c.alpha = make_double2(c.rho.x / v[2], 0.0);
+      }
+      break;
+    case FIN_CG_R:
+      c.iters += 1;
+      c.rr = v[2];
+      if (!isfinite(v[2]) || v[2] > 1e8 * c.rr0) {
+        c.status = 2;
+        active[s] = 0;
+      } else if (v[2] <= c.target2) {
+        active[s] = 0;
+      }
+      break;
+    case FIN_CG_BETA:
+      if (!(c.rho.x > 0.0) || !isfinite(v[2])) {
+        c.status = 1;
+        active[s] = 0;
+      } else {
+        c.beta = make_double2(v[2] / c.rho.x, 0.0);
+        c.rho = make_double2(v[2], 0.0);
+      }
       break;
   }
   sc[s] = c;

@@ -21,7 +21,9 @@
 // FP64 keeping all 18 reals (9 x double2: FP64 is ALU-bound on this GPU, so
 // rebuilding the third row would cost more than the bytes it saves) and
 // FP32 / FP16 the first two rows (12 reals: 3 x float4 or 3 x uint2); the
-// third row is conj(row0 x row1), rebuilt in registers.
+// third row is conj(row0 x row1), rebuilt in registers (storing all 18 FP32
+// reals measured 8-24% slower: the extra loads and registers cost more than
+// the rebuild).
 //
 // Clover blocks.  In the chiral basis gamma_5 = diag(1,1,-1,-1) commutes
 // with sigma_mu_nu, so A(x) is two 6x6 Hermitian blocks (spins {0,1} and
@@ -34,10 +36,6 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
-
-#include <type_traits>
-
-#include "dfloat.h"
 
 #define LQ_DI __device__ __forceinline__
 #define LQ_HDI __host__ __device__ __forceinline__
@@ -179,7 +177,8 @@ struct SolverScal {
 
 // Fused reductions of the hop kernels and modes of the scalar finalize.
 enum { RED_NONE = 0, RED_DOT_W = 1, RED_TS = 2, RED_NORM = 3 };
-enum { FIN_ALPHA = 0, FIN_OMEGA = 1, FIN_BETA = 2, FIN_INIT = 3, FIN_NORM = 4 };
+enum { FIN_ALPHA = 0, FIN_OMEGA = 1, FIN_BETA = 2, FIN_INIT = 3, FIN_NORM = 4,
+       FIN_CG_RHO = 5, FIN_CG_ALPHA = 6, FIN_CG_R = 7, FIN_CG_BETA = 8 };
 
 // ------------------------------------------------------------ precision I/O
 template <int P>
@@ -202,29 +201,6 @@ struct Prec<64> {
     double2* p = (double2*)base;
 #pragma unroll
     for (int k = 0; k < 12; k++) p[k * n + j] = make_double2(s[k].re, s[k].im);
-  }
-};
-
-// FP64 storage read and written as double-float (dfloat.h): the precision of
-// the mixed-precision solvers' FP64-accuracy operator (prepare, true
-// residual, reconstruction), whose arithmetic runs on the FP32 pipes.
-template <>
-struct Prec<65> {
-  typedef dfloat R;
-  static constexpr int NV = 12;  // double2 words per spinor, as Prec<64>
-  LQ_DI static void load(cx<dfloat> s[12], const void* base, const float*, int n, int j) {
-    const double2* p = (const double2*)base;
-#pragma unroll
-    for (int k = 0; k < 12; k++) {
-      double2 v = __ldg(p + k * n + j);
-      s[k] = {dfloat(v.x), dfloat(v.y)};
-    }
-  }
-  LQ_DI static void quantize(cx<dfloat>*) {}
-  LQ_DI static void store(void* base, float*, int n, int j, const cx<dfloat> s[12]) {
-    double2* p = (double2*)base;
-#pragma unroll
-    for (int k = 0; k < 12; k++) p[k * n + j] = make_double2(s[k].re.to_double(), s[k].im.to_double());
   }
 };
 
@@ -345,20 +321,6 @@ struct LinkIO<64> {
 };
 
 template <>
-struct LinkIO<65> {
-  LQ_DI static su3<dfloat> load(const FieldPtrs& f, int p, int mu, int Vh, int cb) {
-    const double2* b = f.U64 + (p * 4 + mu) * 9 * Vh + cb;
-    su3<dfloat> u;
-#pragma unroll
-    for (int k = 0; k < 9; k++) {
-      double2 v = __ldg(b + k * Vh);
-      u.m[k / 3][k % 3] = {dfloat(v.x), dfloat(v.y)};
-    }
-    return u;
-  }
-};
-
-template <>
 struct LinkIO<32> {
   LQ_DI static su3<float> load(const FieldPtrs& f, int p, int mu, int Vh, int cb) {
     const float4* b = f.U32 + (p * 4 + mu) * 3 * Vh + cb;
@@ -439,21 +401,6 @@ struct ClovIO<64> {
       a[2 * k + 1] = v.y;
     }
     ClovIO<32>::herm6_apply<double>(a, in, out);
-  }
-};
-
-template <>
-struct ClovIO<65> {
-  typedef dfloat R;
-  LQ_DI static void apply(const double2* base, int Vh, int cb, const cx<dfloat> in[6], cx<dfloat> out[6]) {
-    dfloat a[36];
-#pragma unroll
-    for (int k = 0; k < 18; k++) {
-      double2 v = __ldg(base + k * Vh + cb);
-      a[2 * k] = dfloat(v.x);
-      a[2 * k + 1] = dfloat(v.y);
-    }
-    ClovIO<32>::herm6_apply<dfloat>(a, in, out);
   }
 };
 

@@ -567,10 +567,10 @@ LQ_DI void hop_sum(const Geom& g, const SysDesc& sd, const FieldPtrs& f, int pou
 template <int P>
 LQ_DI void clover_apply(const FieldPtrs& f, bool inverse, int p, int Vh, int cb, const cx<typename Prec<P>::R> in[12],
                         cx<typename Prec<P>::R> out[12]) {
-  if constexpr (P == 64 || P == 65) {
+  if constexpr (P == 64) {
     const double2* base = inverse ? f.Ai64 : f.A64 + p * 36 * Vh;
-    ClovIO<P>::apply(base, Vh, cb, in, out);
-    ClovIO<P>::apply(base + 18 * Vh, Vh, cb, in + 6, out + 6);
+    ClovIO<64>::apply(base, Vh, cb, in, out);
+    ClovIO<64>::apply(base + 18 * Vh, Vh, cb, in + 6, out + 6);
   } else {
     const float4* base = inverse ? f.Ai32 : f.A32 + p * 18 * Vh;
     ClovIO<32>::apply(base, Vh, cb, in, out);
@@ -614,9 +614,9 @@ enum { EPI_X = 1, EPI_Y = 2, EPI_Z = 4 };
 template <int P>
 struct HopMinBlocks {
 #ifdef LQ_HOP_MINB
-  static constexpr int value = (P == 64 || P == 65) ? 1 : LQ_HOP_MINB;
+  static constexpr int value = P == 64 ? 1 : LQ_HOP_MINB;
 #else
-  static constexpr int value = (P == 64 || P == 65) ? 1 : P == 32 ? 4 : 5;
+  static constexpr int value = P == 64 ? 1 : P == 32 ? 4 : 5;
 #endif
 };
 
@@ -648,9 +648,6 @@ struct HopCfg<16, 2> {
 constexpr int kHopCfgs = 3;
 
 struct HopArgs;
-// the double-float (P = 65) stencil kernels (hop_df.cu)
-int hop_lin_df(bool dag, bool clov, int red, int epi, dim3 gr, const HopArgs& a, cudaStream_t st);
-int hop_clinv_df(bool dag, bool clov, int epi, dim3 gr, const HopArgs& a, cudaStream_t st);
 // alternative configurations of the forward stencil (hop_tuned*.cu), cfg 1 or 2
 template <int P>
 int hop_lin_tuned(int cfg, bool clov, int red, int epi, dim3 gr, const HopArgs& a, cudaStream_t st);
@@ -683,20 +680,6 @@ LQ_DI void block_reduce_store(A v[NQ], double* dst) {
       for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
       if (lane == 0) dst[q] = t;
     }
-  }
-}
-
-// block_reduce_store for the kernel's own type: double-float partial sums
-// are widened to FP64 first.
-template <int NQ, typename A>
-LQ_DI void reduce_store(A v[NQ], double* dst) {
-  if constexpr (std::is_same<A, dfloat>::value) {
-    double d[NQ];
-#pragma unroll
-    for (int q = 0; q < NQ; q++) d[q] = v[q].to_double();
-    block_reduce_store<NQ, double>(d, dst);
-  } else {
-    block_reduce_store<NQ, A>(v, dst);
   }
 }
 
@@ -788,7 +771,7 @@ __global__ void __launch_bounds__(128, (HopCfg<P, CFG>::minb)) k_hop_lin(HopArgs
       }
     }
   }
-  if (RED != RED_NONE) reduce_store<3, R>(red, a.partial + ((long long)s * a.pstride + by) * 4);
+  if (RED != RED_NONE) block_reduce_store<3, R>(red, a.partial + ((long long)s * a.pstride + by) * 4);
 }
 
 // out = A^{-1} (alpha * D_hop x + beta * y) on even sites (pout = 0), terms

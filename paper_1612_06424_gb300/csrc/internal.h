@@ -79,6 +79,9 @@ int lq_bicg_s(int P, const Batch& b, VecP r, VecP v, VecP s, cudaStream_t st);
 int lq_bicg_xr(int P, const Batch& b, VecP x, VecP p, VecP s, VecP t, VecP r, VecP r0, cudaStream_t st);
 int lq_bicg_p(int P, const Batch& b, VecP p, VecP r, VecP v, cudaStream_t st);
 int lq_inner_init(int P, const Batch& b, const double2* r64, VecP r, VecP r0, VecP p, VecP x, cudaStream_t st);
+// CG on the normal equations (P = 64 or 32): x += alpha p, r -= alpha v (|r|^2); p = z + beta p
+int lq_cg_xr(int P, const Batch& b, VecP x, VecP p, VecP r, VecP v, cudaStream_t st);
+int lq_cg_p(int P, const Batch& b, VecP p, VecP z, cudaStream_t st);
 int lq_accum64(int P, const Batch& b, double2* x64, VecP x, cudaStream_t st);
 int lq_norm2_64(const Batch& b, const double2* v, cudaStream_t st);
 int lq_finalize(int mode, const Batch& b, double tau2, double floor_rel2, int wps, cudaStream_t st);

@@ -72,7 +72,7 @@ static int forced_variant() {
 }
 
 static int variant_of(int P, const Batch& b) {
-  if (P == 64 || P == 65) return 1;
+  if (P == 64) return 1;
   const int f = forced_variant();
   const int v = f ? f : b.hop_variant;
   if (v == 2) return P == 32 ? 2 : 1;
@@ -149,9 +149,7 @@ int lq_hop_lin(int P, bool dag, bool clov, int red, const lqcd_lattice* L, const
   }
   const int v = variant_of(P, b);
   int rc;
-  if (P == 65)
-    rc = hop_lin_df(dag, clov, red, epi, gr, a, st);
-  else if (!dag && v >= 3)
+  if (!dag && v >= 3)
     rc = P == 32 ? hop_lin_tuned<32>(v - 2, clov, red, epi, gr, a, st) : hop_lin_tuned<16>(v - 2, clov, red, epi, gr, a, st);
   else
     rc = P == 64 ? launch_lin_p<64>(dag, clov, red, epi, gr, a, st)
@@ -200,9 +198,7 @@ int lq_hop_clinv(int P, bool dag, bool clov, const lqcd_lattice* L, const Batch&
   }
   const int v = variant_of(P, b);
   int rc;
-  if (P == 65)
-    rc = hop_clinv_df(dag, clov, epi, gr, a, st);
-  else if (!dag && v >= 3)
+  if (!dag && v >= 3)
     rc = P == 32 ? hop_clinv_tuned<32>(v - 2, clov, epi, gr, a, st) : hop_clinv_tuned<16>(v - 2, clov, epi, gr, a, st);
   else
     rc = P == 64 ? launch_clinv_p<64>(dag, clov, epi, gr, a, st)
@@ -263,6 +259,22 @@ int lq_bicg_p(int P, const Batch& b, VecP p, VecP r, VecP v, cudaStream_t st) {
   if (P == 64) k_bicg_p_w<64><<<grid_words(b, 64), LQ_BLOCK, 0, st>>>(va, p.d, r.d, v.d);
   else if (P == 32) k_bicg_p_w<32><<<grid_words(b, 32), LQ_BLOCK, 0, st>>>(va, p.d, r.d, v.d);
   else k_bicg_p_h<<<grid_of(b), LQ_BLOCK, 0, st>>>(va, p.d, p.nrm, r.d, r.nrm, v.d, v.nrm);
+  return launched();
+}
+
+int lq_cg_xr(int P, const Batch& b, VecP x, VecP p, VecP r, VecP v, cudaStream_t st) {
+  VecArgs va = vec_args(b);
+  if (P == 64) k_cg_xr_w<64><<<grid_words(b, 64), LQ_BLOCK, 0, st>>>(va, x.d, p.d, r.d, v.d);
+  else if (P == 32) k_cg_xr_w<32><<<grid_words(b, 32), LQ_BLOCK, 0, st>>>(va, x.d, p.d, r.d, v.d);
+  else return LQCD_EBADARG;
+  return launched();
+}
+
+int lq_cg_p(int P, const Batch& b, VecP p, VecP z, cudaStream_t st) {
+  VecArgs va = vec_args(b);
+  if (P == 64) k_cg_p_w<64><<<grid_words(b, 64), LQ_BLOCK, 0, st>>>(va, p.d, z.d);
+  else if (P == 32) k_cg_p_w<32><<<grid_words(b, 32), LQ_BLOCK, 0, st>>>(va, p.d, z.d);
+  else return LQCD_EBADARG;
   return launched();
 }
 
@@ -574,7 +586,7 @@ void tune_store(int P, int n, long long m, int v) {
 }  // namespace
 
 int lq_tune_hop(const lqcd_lattice* L, const Batch& b, int P, bool clov, VecP x, VecP y, VecP out, cudaStream_t st) {
-  if (P == 64 || P == 65) return 1;
+  if (P == 64) return 1;
   if (forced_variant()) return forced_variant();
   const auto key = std::make_tuple(P, b.nsys, b.max_n);
   {

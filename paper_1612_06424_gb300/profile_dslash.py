@@ -5,7 +5,11 @@
   python -m paper_1612_06424_gb300.profile_dslash --factorized --precision 32
 
 Prints ms per launch, algorithmic GB/s and TFLOP/s.  Each launch is one
-k_hop_lin (out_o = A_oo y_o - 1/4 D_hop x_e) over every system of the batch.
+kernel of the solver's BiCGStab iteration over every system of the batch
+(--kernels, numbered as lqcd_stencil_bench: 0 plain second half of D^,
+1 clover-inverse first half, 2 / 3 second half with the fused reductions,
+4-6 the vector updates); the default is 0 (k_hop_lin, out_o = A_oo y_o -
+1/4 D_hop x_e).
 With --factorized it instead runs one 12-source factorized propagator with
 correction on the 16^3x32 workload (Gamma 0..13, DeltaGamma 14..17, Gamma*
 14..31, source (2,0,0,0)), i.e. every kernel of the solver.  With
@@ -29,6 +33,8 @@ def main():
     ap.add_argument("--slabs", nargs="+", default=["0:17x12", "0:13x12"],
                     help="t0:t1xN = N systems on slab t0..t1 (all on field 0)")
     ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--kernels", type=int, nargs="+", default=[0])
+    ap.add_argument("--field-seed", type=int, default=1)
     ap.add_argument("--kappa", type=float, default=0.13)
     ap.add_argument("--csw", type=float, default=1.0)
     ap.add_argument("--factorized", action="store_true")
@@ -66,7 +72,10 @@ def main():
               f"{fl / ms / 1e9:.2f} TFLOP/s (8 flop per complex FMA of the (x, c) contraction)")
         lat.close()
         return
-    U = inputs.random_su3_field(tuple(a.dims), 0.4, 1)
+    if a.dims[0] * a.dims[1] * a.dims[2] * a.dims[3] > 2_000_000:
+        U = inputs.random_su3_field_device(tuple(a.dims), 0.4, a.field_seed, device="cuda", rng="device")
+    else:
+        U = inputs.random_su3_field(tuple(a.dims), 0.4, a.field_seed)
     lat = lqcd.Lattice(tuple(a.dims), "open")
     lat.set_gauge(U, a.kappa, a.csw)
     if a.factorized:
@@ -82,9 +91,11 @@ def main():
               {k: (v["iters"], v["true_residual"]) for k, v in st.items()})
         lat.close()
         return
-    ms, by, fl = lat.dslash_bench(doms, [0] * len(doms), a.precision, a.reps)
-    print(f"dims={a.dims} P={a.precision} systems={len(doms)}: {ms:.4f} ms/launch, "
-          f"{by / ms / 1e6:.1f} GB/s algorithmic ({by / 1e6:.1f} MB/launch), {fl / ms / 1e9:.2f} TFLOP/s")
+    del U
+    for k in a.kernels:
+        ms, by, fl = lat.stencil_bench(doms, [0] * len(doms), a.precision, k, a.reps)
+        print(f"dims={a.dims} P={a.precision} systems={len(doms)} kernel={k}: {ms:.4f} ms/launch, "
+              f"{by / ms / 1e6:.1f} GB/s algorithmic ({by / 1e6:.1f} MB/launch), {fl / ms / 1e9:.2f} TFLOP/s")
     lat.close()
 
 

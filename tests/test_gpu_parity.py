@@ -52,32 +52,6 @@ def test_dslash_fp64_matches_oracle(dims, bc, csw):
             assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max(), (dom, dag)
 
 
-@pytest.mark.parametrize("bc", ["open", "antiperiodic"])
-@pytest.mark.parametrize("csw", [0.0, 1.0])
-def test_dslash_double_float_matches_oracle(bc, csw):
-    """The double-float operator (LQCD_PREC_DFLOAT: FP64 data, FP32-pair arithmetic) that the
-    mixed-precision solvers use for their true residuals.  Its inputs round to 2^-48 and each
-    operation adds at most about 2^-45 relative; an output element is a chain of some thirty
-    operations, so 1e-12 of the largest element bounds it (the same check at FP32 precision
-    fails by six orders of magnitude)."""
-    lqcd = _lq()
-    dims = (8, 6, 6, 4)
-    U = inputs.random_su3_field(dims, 0.4, 3)
-    lat = lqcd.Lattice(dims, bc)
-    lat.set_gauge(U, 0.13, csw)
-    op = oracle.Operator(dims, U, 0.13, csw, BCS[bc])
-    psi = inputs.gaussian_spinor(dims, 4)[0]
-    T = dims[0]
-    for dom in [None, (1, T - 2), (0, T // 2 - 1)]:
-        for dag in (False, True):
-            t0, t1 = dom if dom else (0, T - 1)
-            sl = inputs.slab_sites(dims, t0, t1)
-            ref = op.apply(op.masked(psi, t0, t1), t0, t1, dagger=dag)[sl]
-            got = lat.dslash(_cuda(psi[sl]), 0, dom, dag, 65).cpu().numpy()
-            assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max(), (dom, dag)
-    lat.close()
-
-
 @pytest.mark.parametrize("prec,tol", [(32, 2e-6), (16, 3e-3)])
 @pytest.mark.parametrize("bc", ["open", "antiperiodic"])
 def test_dslash_reduced_precision(prec, tol, bc):

@@ -10,7 +10,7 @@ library), so each case runs in a child process:
      4 / 3 and 6 / 1); dagger launches keep the default.
 Each child applies the FP32 / FP16 operator on the whole lattice and on
 Dirichlet slabs (D and D^dag; tolerances of tests/test_gpu_parity.py) and
-solves a batch of five systems on mixed slabs in FP32 and FP16 to true
+solves a batch of five systems on mixed slabs in FP32, FP16 and FP64 to true
 residual 1e-10, checked with the oracle's operator.  8x6x6x4: 576 sites per
 parity, several blocks and a ragged tail for every variant.
 """
@@ -52,7 +52,7 @@ for prec, tol in ((32, 2e-6), (16, 3e-3)):
 doms = [(0, 3), (2, 7), (0, 7), (4, 7), (1, 5)]
 srcs = inputs.gaussian_spinor(dims, 8, len(doms))
 packed = np.concatenate([srcs[k][inputs.slab_sites(dims, *d)] for k, d in enumerate(doms)])
-for prec in (32, 16):
+for prec in (32, 16, 64):
     sol, stats = lat.solve_block(torch.from_numpy(packed).cuda(), doms, [0] * len(doms),
                                  lqcd.SolverParams(tol=1e-10, precision=prec))
     sol = sol.cpu().numpy()
@@ -74,6 +74,19 @@ print("variant ok")
 def test_stencil_variant_parity(variant):
     env = dict(os.environ, LQCD_HOP_VARIANT=variant)
     env.pop("LQCD_HOP_SPLIT", None)
+    r = subprocess.run([sys.executable, "-c", CHILD.replace("ROOT", repr(ROOT))], env=env, capture_output=True,
+                       text=True, timeout=900)
+    assert r.returncode == 0 and "variant ok" in r.stdout, r.stdout[-2000:] + r.stderr[-4000:]
+
+
+def test_cgnr_fallback_parity():
+    """The Krylov fallback (CG on the normal equations, which the solver switches a system to
+    once BiCGStab has stalled for six defect-correction cycles), forced for every system with
+    LQCD_KRYLOV=cgnr: FP32, FP16 and FP64 solves of five systems on mixed slabs reach the true
+    residual 1e-10, checked with the oracle's operator (same child as the stencil variants)."""
+    env = dict(os.environ, LQCD_KRYLOV="cgnr")
+    env.pop("LQCD_HOP_SPLIT", None)
+    env.pop("LQCD_HOP_VARIANT", None)
     r = subprocess.run([sys.executable, "-c", CHILD.replace("ROOT", repr(ROOT))], env=env, capture_output=True,
                        text=True, timeout=900)
     assert r.returncode == 0 and "variant ok" in r.stdout, r.stdout[-2000:] + r.stderr[-4000:]
