@@ -355,10 +355,11 @@ int solve_core(lqcd_lattice* L, BatchStore& B, bool dag, const lqcd_solver_param
       n_b += grp_b[k];
       n_c += grp_c[k];
     }
-    // the first FP32 cycle reduces the residual by inner_tol; later ones start
-    // near the tolerance and aim 10x deeper, so one more FP64 check ends the
-    // solve (FP16 cannot go deeper than inner_tol; FP64 aims at the floor)
-    const double tau = (cycle == 0 || P == 16) ? inner_tol : 0.1 * inner_tol;
+    // the first FP32 cycle from x = 0 reduces the residual by inner_tol; later
+    // ones, and the first one from a starting iterate (whose residual is already
+    // small), aim 10x deeper, so that one more FP64 check ends the solve (FP16
+    // cannot go deeper than inner_tol; FP64 aims at the floor)
+    const double tau = ((cycle == 0 && !guess) || P == 16) ? inner_tol : 0.1 * inner_tol;
     int it = 0;
     int budget = 0;
     for (int k = 0; k < n; k++)

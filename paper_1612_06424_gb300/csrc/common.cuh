@@ -290,6 +290,33 @@ LQ_DI void grid_pos(int nsys, int& s, int& by) {
   by = (int)(blockIdx.x / (unsigned)nsys);
 }
 
+// Time-tiled order of a (system, block) grid of nsys x nby blocks for the
+// stencil: the blocks of tb consecutive site blocks (a few time slices) of every
+// system run together, then the next tile.  Within a tile the systems follow one
+// another, so a site row and its neighbour rows in time are read within a
+// window of tb blocks of one system (they stay in L2), while links and clover
+// are shared by the systems of the tile.  tb <= 0 (or >= nby) gives grid_pos.
+// A bijection of [0, nsys * nby) onto the (system, block) pairs.
+LQ_HDI void grid_pos_tiled(int bid, int nsys, int nby, int tb, int& s, int& by) {
+  if (tb <= 0 || tb >= nby) {
+    s = bid % nsys;
+    by = bid / nsys;
+    return;
+  }
+  const int per_tile = nsys * tb;
+  const int full = nby / tb;  // tiles of tb blocks; the last one holds the rest
+  if (bid < full * per_tile) {
+    const int t = bid / per_tile, w = bid - t * per_tile;
+    s = w / tb;
+    by = t * tb + (w - s * tb);
+  } else {
+    const int r = nby - full * tb;
+    const int w = bid - full * per_tile;
+    s = w / r;
+    by = full * tb + (w - s * r);
+  }
+}
+
 // ------------------------------------------------------------------- links
 template <typename R>
 struct su3 {

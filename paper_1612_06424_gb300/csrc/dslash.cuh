@@ -600,6 +600,8 @@ struct HopArgs {
   double* partial;                  // [nsys][pstride][4]
   int pstride;
   int nsys;                         // systems of the (linearised) grid
+  int nby;                          // site blocks per system in the grid
+  int tile;                         // blocks per time tile of the grid order (0: systems fastest)
 };
 
 // Epilogue terms present (compile time): D_hop x, A y, z.
@@ -703,7 +705,8 @@ template <int P, bool DAG, bool CLOV, int RED, int EPI, int CFG = 0>
 __global__ void __launch_bounds__(128, (HopCfg<P, CFG>::minb)) k_hop_lin(HopArgs a) {
   typedef typename Prec<P>::R R;
   int s, by;
-  grid_pos(a.nsys, s, by);
+  grid_pos_tiled((int)blockIdx.x, a.nsys, a.nby, a.tile, s, by);
+  if (s >= a.nsys) return;
   if (a.active && !a.active[s]) return;
   const SysDesc sd = a.sys[s];
   const int j0 = by * blockDim.x;
@@ -780,7 +783,8 @@ template <int P, bool DAG, bool CLOV, int EPI, int CFG = 0>
 __global__ void __launch_bounds__(128, (HopCfg<P, CFG>::minb)) k_hop_clinv(HopArgs a) {
   typedef typename Prec<P>::R R;
   int s, by;
-  grid_pos(a.nsys, s, by);
+  grid_pos_tiled((int)blockIdx.x, a.nsys, a.nby, a.tile, s, by);
+  if (s >= a.nsys) return;
   if (a.active && !a.active[s]) return;
   const SysDesc sd = a.sys[s];
   const int j0 = by * blockDim.x;
@@ -884,7 +888,8 @@ LQ_DI void hop_pair32(const HopArgs& a, const SysDesc& sd, const FieldPtrs& f, i
 template <bool DAG, bool CLOV, int RED, int EPI>
 __global__ void __launch_bounds__(128, LQ_HOP2_MINB) k_hop2_lin(HopArgs a) {
   int s, by;
-  grid_pos(a.nsys, s, by);
+  grid_pos_tiled((int)blockIdx.x, a.nsys, a.nby, a.tile, s, by);
+  if (s >= a.nsys) return;
   if (a.active && !a.active[s]) return;
   const SysDesc sd = a.sys[s];
   if (by * 64 >= sd.n) return;
@@ -953,7 +958,8 @@ __global__ void __launch_bounds__(128, LQ_HOP2_MINB) k_hop2_lin(HopArgs a) {
 template <bool DAG, bool CLOV, int EPI>
 __global__ void __launch_bounds__(128, LQ_HOP2_MINB) k_hop2_clinv(HopArgs a) {
   int s, by;
-  grid_pos(a.nsys, s, by);
+  grid_pos_tiled((int)blockIdx.x, a.nsys, a.nby, a.tile, s, by);
+  if (s >= a.nsys) return;
   if (a.active && !a.active[s]) return;
   const SysDesc sd = a.sys[s];
   if (by * 64 >= sd.n) return;

@@ -27,7 +27,8 @@ struct Batch {
   int nsys = 0;
   int nby = 0;               // site blocks (one site per thread) of the largest system
   int pstride = 0;           // partial-buffer blocks per system (>= any kernel's grid.y)
-  int hop_variant = 1;       // FP32 stencil: 1 = one thread per site, 2 = two threads per site
+  int hop_variant = 1;       // stencil variant (lq_tune_hop): launch configuration / threads per site
+  int hop_tile = 0;          // time slices per tile of the stencil's block order (0: systems fastest)
   long long max_n = 0;
   long long total = 0;       // sum of n over systems (sites per parity)
   const lq::SysDesc* sys = nullptr;

@@ -40,6 +40,24 @@ static inline int launched() {
   return 0;
 }
 
+// Time slices per tile of the stencil's block order: LQCD_HOP_TILE forces a
+// value for every batch, else the batch's (chosen by lq_tune_hop).
+static int tile_of(const Batch& b) {
+  static int forced = -2;
+  if (forced == -2) {
+    const char* e = getenv("LQCD_HOP_TILE");
+    forced = e ? atoi(e) : -1;
+  }
+  return forced >= 0 ? forced : b.hop_tile;
+}
+
+// site blocks per system and blocks per time tile for blocks of `sites_per_block` sites
+static void set_grid_order(HopArgs& a, const lqcd_lattice* L, const Batch& b, int sites_per_block) {
+  a.nby = (int)((b.max_n + sites_per_block - 1) / sites_per_block);
+  const int h = tile_of(b);
+  a.tile = h > 0 ? (int)((h * L->S3h + sites_per_block - 1) / sites_per_block) : 0;
+}
+
 static HopArgs hop_args(const lqcd_lattice* L, const Batch& b, int pout) {
   HopArgs a{};
   a.g = L->g;
@@ -51,6 +69,7 @@ static HopArgs hop_args(const lqcd_lattice* L, const Batch& b, int pout) {
   a.pstride = b.pstride;
   a.nsys = b.nsys;
   a.diag = 1.0 / (2.0 * L->kappa);
+  set_grid_order(a, L, b, LQ_BLOCK);
   return a;
 }
 
@@ -139,6 +158,7 @@ int lq_hop_lin(int P, bool dag, bool clov, int red, const lqcd_lattice* L, const
   dim3 gr = grid_of(b);
   if (variant_of(P, b) == 2) {
     const dim3 g2 = grid_lin(b, (b.max_n + 63) / 64);
+    set_grid_order(a, L, b, 64);
     int rc = dag ? (clov ? launch_lin2<true, true>(red, epi, g2, a, st) : launch_lin2<true, false>(red, epi, g2, a, st))
                  : (clov ? launch_lin2<false, true>(red, epi, g2, a, st) : launch_lin2<false, false>(red, epi, g2, a, st));
     if (rc) {
@@ -188,6 +208,7 @@ int lq_hop_clinv(int P, bool dag, bool clov, const lqcd_lattice* L, const Batch&
   dim3 gr = grid_of(b);
   if (variant_of(P, b) == 2) {
     const dim3 g2 = grid_lin(b, (b.max_n + 63) / 64);
+    set_grid_order(a, L, b, 64);
     int rc = dag ? (clov ? launch_clinv2<true, true>(epi, g2, a, st) : launch_clinv2<true, false>(epi, g2, a, st))
                  : (clov ? launch_clinv2<false, true>(epi, g2, a, st) : launch_clinv2<false, false>(epi, g2, a, st));
     if (rc) {
