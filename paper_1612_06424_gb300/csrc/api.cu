@@ -136,6 +136,9 @@ struct BatchStore {
     b.nsys = n;
     b.max_n = maxn;
     b.total = off;
+    b.tblk_ok = L->S3h % 32 == 0 ? 1 : 0;
+    for (int k = 0; k < n; k++)
+      if ((doms[k].t1 - doms[k].t0 + 1) % 4 != 0) b.tblk_ok = 0;
     b.nby = (int)((maxn + LQ_BLOCK - 1) / LQ_BLOCK);
     b.pstride = (int)((12 * maxn + LQ_BLOCK - 1) / LQ_BLOCK);
     if ((long long)n * b.pstride >= (1LL << 31)) {

@@ -378,11 +378,15 @@ __global__ void __launch_bounds__(128) k_convert(VecArgs va, const void* in, con
 }
 
 // ---------------------------------------------------------------- finalize
-// Sum of the block partials of system s, in a fixed order (one warp).
-LQ_DI void warp_sum_partials(const double* partial, int pstride, int nb, int s, double out[3]) {
-  const int lane = threadIdx.x & 31;
+// Sum of the block partials of system s = blockIdx.x, in a fixed order: each
+// thread of the block sums a strided subset, the warps reduce by shuffles and
+// warp 0 adds the warp sums in warp order.  Thread 0 receives the result.
+constexpr int FIN_THREADS = 512;
+LQ_DI void block_sum_partials(const double* partial, int pstride, int nb, int s, double out[3]) {
+  __shared__ double sh[FIN_THREADS / 32][3];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   double v[3] = {0.0, 0.0, 0.0};
-  for (int b = lane; b < nb; b += 32) {
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
     const double* q = partial + ((long long)s * pstride + b) * 4;
     v[0] += q[0];
     v[1] += q[1];
@@ -392,7 +396,18 @@ LQ_DI void warp_sum_partials(const double* partial, int pstride, int nb, int s, 
   for (int q = 0; q < 3; q++) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
-    out[q] = v[q];
+  }
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < 3; q++) sh[wid][q] = v[q];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = blockDim.x >> 5;
+    for (int q = 0; q < 3; q++) {
+      double t = 0.0;
+      for (int w = 0; w < nw; w++) t += sh[w][q];
+      out[q] = t;
+    }
   }
 }
 
@@ -403,7 +418,7 @@ LQ_DI double2 cdiv(double2 a, double2 b) {
 LQ_DI double2 cmul2(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 LQ_DI bool finite2(double2 a) { return isfinite(a.x) && isfinite(a.y); }
 
-// One warp per system: fold the block partials into the iteration scalars.
+// One block per system: fold the block partials into the iteration scalars.
 //  FIN_INIT : rr = rho = |r|^2, rr0 = rr, iters = 0, target2 = max(tau2*rr, floor2)
 //  FIN_ALPHA: alpha = rho / <r0, v>
 //  FIN_OMEGA: omega = <t, s> / |t|^2
@@ -421,13 +436,13 @@ LQ_DI bool finite2(double2 a) { return isfinite(a.x) && isfinite(a.y); }
 // thread), so that the system used ceil(n * wps / bdim) blocks.
 __global__ void k_finalize(int mode, int nsys, const SysDesc* sys, int* active, SolverScal* sc, const double* partial,
                            int pstride, int wps, int bdim, double tau2, double floor_rel2) {
-  const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int s = blockIdx.x;
   if (s >= nsys) return;
-  if (active && !active[s]) return;
+  if (active && !active[s]) return;  // uniform over the block
   const int nb = (sys[s].n * wps + bdim - 1) / bdim;
   double v[3];
-  warp_sum_partials(partial, pstride, nb, s, v);
-  if ((threadIdx.x & 31) != 0) return;
+  block_sum_partials(partial, pstride, nb, s, v);
+  if (threadIdx.x != 0) return;
   SolverScal c = sc[s];
   const double2 d = make_double2(v[0], v[1]);
   switch (mode) {

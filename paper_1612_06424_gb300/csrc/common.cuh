@@ -317,6 +317,20 @@ LQ_HDI void grid_pos_tiled(int bid, int nsys, int nby, int tb, int& s, int& by) 
   }
 }
 
+// Site (within the system's slab, one parity) of thread t of block `by` of a
+// 128-thread stencil block.  Plain: 128 consecutive sites.  Time-blocked
+// (tblk): warp w covers 32 consecutive sites of time slice 4*g + w, the four
+// warps the same 32 positions of four consecutive slices, so a block reads
+// most of its own time-direction neighbours (x0 -+ 1) itself.  Time-blocked
+// order needs S3h % 32 == 0 and every slab's slice count % 4 == 0 (checked on
+// the host); it maps the blocks 0 .. n/128 - 1 onto the same n sites.
+LQ_HDI int site_of_block(int tblk, int S3h, int by, int t) {
+  if (!tblk) return by * 128 + t;
+  const int nchunk = S3h >> 5;
+  const int g = by / nchunk, chunk = by - g * nchunk;
+  return ((g << 2) + (t >> 5)) * S3h + (chunk << 5) + (t & 31);
+}
+
 // ------------------------------------------------------------------- links
 template <typename R>
 struct su3 {

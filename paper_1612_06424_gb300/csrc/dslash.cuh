@@ -602,6 +602,7 @@ struct HopArgs {
   int nsys;                         // systems of the (linearised) grid
   int nby;                          // site blocks per system in the grid
   int tile;                         // blocks per time tile of the grid order (0: systems fastest)
+  int tblk;                         // 1: a block covers 32 sites x 4 time slices (site_of_block)
 };
 
 // Epilogue terms present (compile time): D_hop x, A y, z.
@@ -709,9 +710,8 @@ __global__ void __launch_bounds__(128, (HopCfg<P, CFG>::minb)) k_hop_lin(HopArgs
   if (s >= a.nsys) return;
   if (a.active && !a.active[s]) return;
   const SysDesc sd = a.sys[s];
-  const int j0 = by * blockDim.x;
-  if (j0 >= sd.n) return;  // whole block beyond this system
-  const int j = j0 + threadIdx.x;
+  if (by * (int)blockDim.x >= sd.n) return;  // whole block beyond this system
+  const int j = site_of_block(a.tblk, a.g.S3h, by, threadIdx.x);
   const FieldPtrs f = a.fields[sd.field];
   R red[3] = {0, 0, 0};
   if (j < sd.n) {
@@ -787,9 +787,8 @@ __global__ void __launch_bounds__(128, (HopCfg<P, CFG>::minb)) k_hop_clinv(HopAr
   if (s >= a.nsys) return;
   if (a.active && !a.active[s]) return;
   const SysDesc sd = a.sys[s];
-  const int j0 = by * blockDim.x;
-  if (j0 >= sd.n) return;
-  const int j = j0 + threadIdx.x;
+  if (by * (int)blockDim.x >= sd.n) return;
+  const int j = site_of_block(a.tblk, a.g.S3h, by, threadIdx.x);
   const FieldPtrs f = a.fields[sd.field];
   if (j >= sd.n) return;
   const int cb = sd.cb0 + j;

@@ -29,6 +29,8 @@ struct Batch {
   int pstride = 0;           // partial-buffer blocks per system (>= any kernel's grid.y)
   int hop_variant = 1;       // stencil variant (lq_tune_hop): launch configuration / threads per site
   int hop_tile = 0;          // time slices per tile of the stencil's block order (0: systems fastest)
+  int hop_tblk = 1;          // 1: time-blocked sites (32 sites x 4 slices per block) where allowed
+  int tblk_ok = 0;           // every slab has a multiple of 4 slices and S3h % 32 == 0
   long long max_n = 0;
   long long total = 0;       // sum of n over systems (sites per parity)
   const lq::SysDesc* sys = nullptr;

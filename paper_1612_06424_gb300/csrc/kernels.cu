@@ -52,10 +52,22 @@ static int tile_of(const Batch& b) {
 }
 
 // site blocks per system and blocks per time tile for blocks of `sites_per_block` sites
+// Time-blocked sites: LQCD_HOP_TBLK=0|1 forces, else the batch's choice; only
+// for 128-site blocks of batches whose slabs allow it.
+static int tblk_of(const Batch& b) {
+  static int forced = -2;
+  if (forced == -2) {
+    const char* e = getenv("LQCD_HOP_TBLK");
+    forced = e ? atoi(e) : -1;
+  }
+  return b.tblk_ok && (forced >= 0 ? forced : b.hop_tblk) ? 1 : 0;
+}
+
 static void set_grid_order(HopArgs& a, const lqcd_lattice* L, const Batch& b, int sites_per_block) {
   a.nby = (int)((b.max_n + sites_per_block - 1) / sites_per_block);
   const int h = tile_of(b);
   a.tile = h > 0 ? (int)((h * L->S3h + sites_per_block - 1) / sites_per_block) : 0;
+  a.tblk = sites_per_block == LQ_BLOCK ? tblk_of(b) : 0;
 }
 
 static HopArgs hop_args(const lqcd_lattice* L, const Batch& b, int pout) {
@@ -322,9 +334,8 @@ int lq_norm2_64(const Batch& b, const double2* v, cudaStream_t st) {
 }
 
 int lq_finalize(int mode, const Batch& b, double tau2, double floor_rel2, int wps, cudaStream_t st) {
-  const int warps = 8;
-  k_finalize<<<(b.nsys + warps - 1) / warps, warps * 32, 0, st>>>(mode, b.nsys, b.sys, b.active, b.sc, b.partial,
-                                                                  b.pstride, wps, LQ_BLOCK, tau2, floor_rel2);
+  k_finalize<<<b.nsys, FIN_THREADS, 0, st>>>(mode, b.nsys, b.sys, b.active, b.sc, b.partial, b.pstride, wps, LQ_BLOCK,
+                                             tau2, floor_rel2);
   return launched();
 }
 

@@ -22,7 +22,7 @@ def test_strip_comments():
 def fake_root(tmp_path, monkeypatch):
     d = tmp_path / "paper_1612_06424_gb300" / "csrc"
     d.mkdir(parents=True)
-    for f in ("common.cuh", "dslash.cuh"):
+    for f in bench.KERNEL_SOURCES:
         shutil.copy(os.path.join(CSRC, f), d / f)
     (tmp_path / "profiles").mkdir()
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))

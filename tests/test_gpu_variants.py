@@ -135,3 +135,69 @@ def test_tuner_decisions_cached(tmp_path):
     assert r.returncode == 0 and "tune ok" in r.stdout, r.stdout[-2000:] + r.stderr[-4000:]
     assert f"stencil variant {planted} for P=32 nsys=3 max_n={n_sites}" in r.stderr, r.stderr[-3000:]
     assert cache.read_text().strip() == f"32 3 {n_sites} {planted}"  # read, not re-timed
+
+
+TBLK_CHILD = r"""
+import sys
+import numpy as np
+import torch
+sys.path.insert(0, ROOT)
+import oracle
+from paper_1612_06424_gb300 import build, inputs
+build.build()
+from paper_1612_06424_gb300 import lqcd
+
+dims = (12, 8, 4, 4)
+for bc in ("open", "antiperiodic"):
+    U = inputs.random_su3_field(dims, 0.4, 15)
+    lat = lqcd.Lattice(dims, bc)
+    lat.set_gauge(U, 0.13, 1.0)
+    op = oracle.Operator(dims, U, 0.13, 1.0, oracle.BC_OPEN if bc == "open" else oracle.BC_ANTIPERIODIC)
+    psi = inputs.gaussian_spinor(dims, 16)[0]
+    for prec, tol in ((32, 2e-6), (16, 3e-3)):
+        for dom in (None, (0, 3), (4, 11), (8, 11)):
+            for dag in (False, True):
+                t0, t1 = dom if dom else (0, 11)
+                sl = inputs.slab_sites(dims, t0, t1)
+                ref = op.apply(op.masked(psi, t0, t1), t0, t1, dagger=dag)[sl] if dom else op.apply(psi, dagger=dag)
+                got = lat.dslash(torch.from_numpy(np.ascontiguousarray(psi[sl])).cuda(), 0, dom, dag, prec).cpu().numpy()
+                err = np.abs(got - ref).max() / np.abs(ref).max()
+                assert err <= tol, (bc, prec, dom, dag, err)
+    doms = [(0, 3), (4, 11), (0, 11), (8, 11)]
+    srcs = inputs.gaussian_spinor(dims, 18, len(doms))
+    packed = np.concatenate([srcs[k][inputs.slab_sites(dims, *d)] for k, d in enumerate(doms)])
+    for prec in (32, 16, 64):
+        sol, stats = lat.solve_block(torch.from_numpy(packed).cuda(), doms, [0] * len(doms),
+                                     lqcd.SolverParams(tol=1e-10, precision=prec))
+        sol = sol.cpu().numpy()
+        off = 0
+        for k, d in enumerate(doms):
+            sl = inputs.slab_sites(dims, *d)
+            n = sl.stop - sl.start
+            got = np.zeros((op.V, 4, 3), complex)
+            got[sl] = sol[off:off + n]
+            off += n
+            if d == (0, 11):
+                b = srcs[k]
+                res = np.linalg.norm(b - op.apply(got)) / np.linalg.norm(b)
+            else:
+                b = op.masked(srcs[k], *d)
+                res = np.linalg.norm(b - op.apply(got, *d)) / np.linalg.norm(b)
+            assert res <= 1.5e-10 and stats[k]["status"] == 0, (bc, prec, d, res, stats[k])
+    lat.close()
+print("tblk ok")
+"""
+
+
+@pytest.mark.parametrize("variant,tblk", [("1", "1"), ("3", "1"), ("4", "1"), ("1", "0")])
+def test_time_blocked_sites_parity(variant, tblk):
+    """LQCD_HOP_TBLK=1 (the default where allowed): each 128-thread block of the one-thread
+    stencils covers 32 sites of four consecutive time slices; LQCD_HOP_TBLK=0: 128 consecutive
+    sites.  12x8x4x4 (64 sites per slice and parity: two 32-site chunks), slabs of 4, 8 and 12
+    slices, open and antiperiodic (wrapping) time boundary; operator and solves against the
+    oracle as above."""
+    env = dict(os.environ, LQCD_HOP_VARIANT=variant, LQCD_HOP_TBLK=tblk)
+    env.pop("LQCD_HOP_SPLIT", None)
+    r = subprocess.run([sys.executable, "-c", TBLK_CHILD.replace("ROOT", repr(ROOT))], env=env,
+                       capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0 and "tblk ok" in r.stdout, r.stdout[-2000:] + r.stderr[-4000:]
