@@ -145,6 +145,9 @@ int lq_force(const lqcd_lattice* L, int field, const lqcd_slab& dom, const doubl
 int lq_fill64(double2* p, long long n, unsigned seed, cudaStream_t st);
 // nucleon point correlators W[p][t] = (W1, W2) of propagators prop[p] ([12][V][12] double2)
 // over slices t0..t0+n_t-1; partial: lq_nucleon_point_partial_words(...) double2 of scratch
+// nucleon blocks on the tensor cores (nucleon_tc.cu); returns after the kernel finished
+int lq_nucleon_blocks_tc(int n, long long nsite, const double2* s, int conj, int S3, long long lo0, int n_t,
+                         double2* B, cudaStream_t st);
 int lq_nucleon_point(const lqcd_lattice* L, int n_prop, const double2* prop, int t0, int n_t, double2* partial,
                      double2* W, cudaStream_t st);
 long long lq_nucleon_point_partial_words(const lqcd_lattice* L, int n_prop, int n_t);

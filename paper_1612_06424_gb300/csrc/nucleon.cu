@@ -380,6 +380,13 @@ __global__ void k_nucleon_point_sum(int nblk, int n_t, int n_prop, const double2
   W[2 * i + 1] = r2;
 }
 
+// LQCD_NUCLEON_TC=0 selects the FP32-FMA block kernel, 1 the tensor-core one (nucleon_tc.cu);
+// read at every call
+bool use_tensor_cores() {
+  const char* e = getenv("LQCD_NUCLEON_TC");
+  return e ? atoi(e) != 0 : false;
+}
+
 }  // namespace
 
 int lq_nucleon_point(const lqcd_lattice* L, int n_prop, const double2* prop, int t0, int n_t, double2* partial,
@@ -436,6 +443,9 @@ extern "C" int lqcd_nucleon_blocks(lqcd_lattice* L, const lqcd_slab* slab, int n
   }
   const int S3 = (int)L->S3;
   const long long nsite = (long long)(slab->t1 - slab->t0 + 1) * S3;
+  if (use_tensor_cores())
+    return lq_nucleon_blocks_tc(n, nsite, (const double2*)s, conj, S3, (long long)(t0 - slab->t0) * S3, n_t,
+                                (double2*)B, (cudaStream_t)stream);
   const int nti = (n + TI - 1) / TI, ntj = (n + TJ - 1) / TJ, ntk = (n + TK - 1) / TK;
   {
     // static + dynamic shared memory exceed the 48 KB default: opt in once per device

@@ -34,16 +34,20 @@ def _cuda(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def _bound(s, t):
-    a = np.abs(s[:, t * S3:(t + 1) * S3])                              # (N, S3, 4, 3)
+def _bound(s, t, s3=S3):
+    a = np.abs(s[:, t * s3:(t + 1) * s3])                              # (N, S3, 4, 3)
     cg5 = np.abs(oracle.charge_conjugation() @ oracle.gamma(4))
     eps = np.abs(oracle.EPS3)
     d = np.einsum("abc,ixma,mn,jxnb->ijxc", eps, a, cg5, a)
     return np.einsum("ijxc,kxdc->ijkd", d, a)
 
 
+@pytest.mark.parametrize("kernel", ["fma", "tc"])
 @pytest.mark.parametrize("n,conj", [(10, False), (17, True)])
-def test_blocks_match_oracle(n, conj):
+def test_blocks_match_oracle(n, conj, kernel, monkeypatch):
+    """Both block kernels: FP32 FMA (k_nucleon_block) and tensor cores (k_nucleon_block_tc,
+    TF32 three-pass split, accumulated per 64 sites in TMEM); LQCD_NUCLEON_TC selects."""
+    monkeypatch.setenv("LQCD_NUCLEON_TC", "1" if kernel == "tc" else "0")
     lqcd = _lq()
     U = inputs.random_su3_field(DIMS, 0.4, 9)
     lat = lqcd.Lattice(DIMS, "open")
@@ -62,6 +66,35 @@ def test_blocks_match_oracle(n, conj):
         bnd = _bound(src, t)
         assert np.all(np.abs(B[q] - ref) <= 3e-5 * bnd + 1e-300), t
         assert np.abs(ref).max() > 1e-3 * bnd.max()       # values far above the tolerance
+
+
+@pytest.mark.parametrize("conj", [False, True])
+def test_tensor_core_blocks_many_tiles(conj, monkeypatch):
+    """The tensor-core kernel on 4 x 8^3 (512 sites per slice: 128 chunks of 4 sites, 8 inner
+    accumulations of 64 sites folded into the running sums) with N = 40 fields (5 x 3 row tiles
+    of 8 x 16 (i, j), 3 column tiles of 16 k, ragged in j and k), two slices: against the
+    oracle within the bound above, and against the FP32-FMA kernel."""
+    lqcd = _lq()
+    dims = (4, 8, 8, 8)
+    s3 = 512
+    n = 40
+    U = inputs.random_su3_field(dims, 0.4, 3)
+    lat = lqcd.Lattice(dims, "open")
+    lat.set_gauge(U, 0.12, 0.0)
+    op = oracle.Operator(dims, U, 0.12, 0.0)
+    rng = np.random.default_rng(40 + conj)
+    s = rng.standard_normal((n, 4 * s3, 4, 3)) + 1j * rng.standard_normal((n, 4 * s3, 4, 3))
+    got = {}
+    for kernel in ("1", "0"):
+        monkeypatch.setenv("LQCD_NUCLEON_TC", kernel)
+        got[kernel] = lat.nucleon_blocks(_cuda(s), (0, 3), 1, 2, conj=conj).cpu().numpy()   # slices 1, 2
+    src = np.conj(s) if conj else s
+    for q, t in enumerate((1, 2)):
+        ref = oracle.nucleon_block(op, src, t)
+        bnd = _bound(src, t, s3)
+        assert np.all(np.abs(got["1"][q] - ref) <= 3e-5 * bnd + 1e-300), t
+        assert np.all(np.abs(got["1"][q] - got["0"][q]) <= 6e-5 * bnd + 1e-300), t
+        assert np.abs(ref).max() > 1e-3 * bnd.max()
 
 
 def test_contract_matches_oracle_sums():
