@@ -19,20 +19,26 @@
 // into one TMEM accumulator, which is then added into FP32 running sums held in a second TMEM
 // region; the result is written in FP64.
 //
-// One CTA (256 threads, 8 warps): 128 rows (i, j) = 8 i x 16 j of one slice and 64 complex
-// columns (16 k x 4 alpha) = 128 real columns.  Per chunk of 4 sites (24 real K values,
-// three MMA K-steps of 8) all threads stage the 40 spinors of the chunk from global FP64 into
-// FP32 shared memory (prefetched one chunk ahead), build the split operands of A and Bt into
-// one of two operand buffers in the canonical K-major layout without swizzle, and one thread
-// issues 9 MMAs (3 K-steps x 3 products) and commits them to the buffer's mbarrier.  The
-// building of chunk c+1 overlaps the MMAs of chunk c.
+// The fields of the requested slices are first converted once to FP32 (conjugated for the xi
+// side) by k_slices_f32, slice by slice into a scratch array [slice][field][site][12] whose
+// sites are padded to a multiple of 4 with zeros.
+//
+// One CTA per SM (512 threads, 16 warps): 128 rows (i, j) = 8 i x 16 j of one slice and 128
+// complex columns (32 k x 4 alpha) = 256 real columns, so the accumulator fills the 512 TMEM
+// columns (256 inner + 256 running sums).  Per chunk of 4 sites (24 real K values, three MMA
+// K-steps of 8) all threads stage the 56 spinors of the chunk (FP32, 16-byte loads prefetched
+// one chunk ahead) in shared memory; warps 0-7 build the split diquark operand A (128 rows) and
+// warps 8-15 the split operand Bt (256 rows) into one of two operand buffers in the canonical
+// K-major layout without swizzle, and one thread issues 9 MMAs (3 K-steps x 3 products, each
+// M 128 x N 256 x K 8) and commits them to the buffer's mbarrier.  The building of chunk c+1
+// overlaps the MMAs of chunk c.
 //
 // Operand layout (no swizzle, K-major): a core matrix is 8 rows x 16 bytes (4 TF32).  One
-// 128-row x 8-value operand of one K-step is 16 row groups x 2 core matrices:
+// R-row x 8-value operand of one K-step is R/8 row groups x 2 core matrices:
 //   byte offset of (row r, value q) = ((r / 8) * 2 + q / 4) * 128 + (r % 8) * 16 + (q % 4) * 4,
 // i.e. leading-dimension byte offset (between the two core matrices along K) 128 and
-// stride-dimension byte offset (between row groups) 256.  Each operand occupies its own
-// 4096-byte block, so every address the descriptor can form lies inside that block.
+// stride-dimension byte offset (between row groups) 256.  Each operand occupies its own block
+// of R * 32 bytes, so every address the descriptor can form lies inside that block.
 //
 // Every wait on an mbarrier is bounded (about one second of clock cycles); on expiry the CTA
 // records the failure in `status`, stops issuing, and still frees its TMEM.
@@ -47,22 +53,24 @@ using namespace lq;
 
 namespace {
 
-constexpr int TI = 8, TJ = 16, TK = 16;  // tile: 8 x 16 (i, j) rows, 16 k (64 complex columns)
+constexpr int TI = 8, TJ = 16, TK = 32;  // tile: 8 x 16 (i, j) rows, 32 k (128 complex columns)
 constexpr int NSLOT = TI + TJ + TK;      // spinors per site of a tile
 constexpr int XS = 4;                    // sites per chunk
 constexpr int NSTEP = XS * 6 / 8;        // MMA K-steps per chunk (K = 8 TF32 per step)
 constexpr int GROUP = 16;                // chunks per inner accumulation (64 sites)
-constexpr int NT = 256;
-constexpr int MAT = 4096;                    // bytes of one 128 x 8 operand
-constexpr int BUF = NSTEP * 4 * MAT;         // one chunk: per step A hi, A lo, Bt hi, Bt lo
-constexpr int STG = XS * NSLOT * 13 * 8;     // FP32 staging: [site][slot][13 float2]
-constexpr int SMEM = 2 * BUF + STG + 64;     // + 2 mbarriers and the TMEM address
-constexpr int TMEM_COLS = 256;               // inner accumulator (0..127) + running sums (128..255)
-constexpr int NLOAD = (XS * NSLOT * 12 + NT - 1) / NT;  // staged complex values per thread
+constexpr int NT = 512;
+constexpr int MAT_A = 4096;                   // bytes of the 128-row x 8 operand A of one step
+constexpr int MAT_B = 8192;                   // bytes of the 256-row x 8 operand Bt of one step
+constexpr int STEP = 2 * MAT_A + 2 * MAT_B;   // one K-step: A hi, A lo, Bt hi, Bt lo
+constexpr int BUF = NSTEP * STEP;             // one chunk
+constexpr int STG = XS * NSLOT * 13 * 8;      // FP32 staging: [site][slot][13 float2]
+constexpr int SMEM = 2 * BUF + STG + 64;      // + 2 mbarriers, the TMEM address and a flag
+constexpr int TMEM_COLS = 512;                // inner accumulator (0..255) + running sums (256..511)
+constexpr int NPRE = 4;                       // 16-byte staging loads per thread and chunk
 
 // instruction descriptor of kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32 (bits 7-9 and
 // 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28
-constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
 
 LQ_DI uint64_t smem_desc(uint32_t addr) {
   // start address >> 4 (bits 0-13), leading byte offset 128 >> 4 (16-29), stride byte offset
@@ -150,21 +158,22 @@ LQ_DI float2 cg5_pair_tc(const float2* si, const float2* tj, int a, int b) {
   return r;
 }
 
-// store the hi / lo split of four consecutive K values of row r into K-block beta (0..5)
-LQ_DI void put4(unsigned char* buf, int which, int r, int beta, float4 v) {
+// store the hi / lo split of four consecutive K values of row r into K-block beta (0..5) of
+// the operand at byte offset `hi_off` of a step (lo at hi_off + mat)
+LQ_DI void put4(unsigned char* buf, int hi_off, int mat, int r, int beta, float4 v) {
   float4 h, l;
   split_tf32(v.x, h.x, l.x);
   split_tf32(v.y, h.y, l.y);
   split_tf32(v.z, h.z, l.z);
   split_tf32(v.w, h.w, l.w);
-  const int step = beta >> 1, kc = beta & 1;
-  const int off = ((r >> 3) * 2 + kc) * 128 + (r & 7) * 16;
-  *reinterpret_cast<float4*>(buf + (step * 4 + which) * MAT + off) = h;
-  *reinterpret_cast<float4*>(buf + (step * 4 + which + 1) * MAT + off) = l;
+  const int kc = beta & 1;
+  const int off = (beta >> 1) * STEP + hi_off + ((r >> 3) * 2 + kc) * 128 + (r & 7) * 16;
+  *reinterpret_cast<float4*>(buf + off) = h;
+  *reinterpret_cast<float4*>(buf + off + mat) = l;
 }
 
-// 128-thread TMEM readout helpers: warp w reads lanes 32 (w % 4) .. + 31 and real columns
-// 64 (w / 4) .. + 63 of the inner accumulator and adds them into the running sums.
+// TMEM readout: warp w reads lanes 32 (w % 4) .. + 31 and real columns 64 (w / 4) .. + 63 of
+// the inner accumulator and adds them into the running sums (columns + 256).
 LQ_DI void fold_group(uint32_t tmem, int warp, bool first) {
   const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
   const int c0 = 64 * (warp >> 2);
@@ -173,17 +182,38 @@ LQ_DI void fold_group(uint32_t tmem, int warp, bool first) {
     float a[16], s[16];
     tmem_ld16(tmem + lane_base + (uint32_t)(c0 + 16 * q), a);
     if (!first) {
-      tmem_ld16(tmem + lane_base + (uint32_t)(128 + c0 + 16 * q), s);
+      tmem_ld16(tmem + lane_base + (uint32_t)(256 + c0 + 16 * q), s);
 #pragma unroll
       for (int e = 0; e < 16; e++) a[e] += s[e];
     }
-    tmem_st16(tmem + lane_base + (uint32_t)(128 + c0 + 16 * q), a);
+    tmem_st16(tmem + lane_base + (uint32_t)(256 + c0 + 16 * q), a);
   }
 }
 
-__global__ void __launch_bounds__(NT, 2) k_nucleon_block_tc(int n, long long nsite, const double2* s, int conj,
-                                                             int S3, long long lo0, int t_stride_sites, double2* B,
-                                                             int* status) {
+// sf[((ts * n + f) * S3p + x) * 12 + comp] = s[(f * nsite + lo + ts * S3 + x) * 12 + comp] in FP32
+// (imaginary part negated for conj), zero for the padding sites x >= S3
+__global__ void k_slices_f32(int n, long long nsite, const double2* s, int conj, int S3, int S3p, long long lo,
+                             int nts, float2* sf) {
+  const long long total = (long long)nts * n * S3p * 12;
+  const float cs = conj ? -1.f : 1.f;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int comp = (int)(e % 12);
+    const long long r = e / 12;
+    const int x = (int)(r % S3p);
+    const long long q = r / S3p;
+    const int f = (int)(q % n), ts = (int)(q / n);
+    float2 v = make_float2(0.f, 0.f);
+    if (x < S3) {
+      const double2 d = s[((long long)f * nsite + lo + (long long)ts * S3 + x) * 12 + comp];
+      v = make_float2((float)d.x, cs * (float)d.y);
+    }
+    sf[e] = v;
+  }
+}
+
+__global__ void __launch_bounds__(NT, 1) k_nucleon_block_tc(int n, int S3p, const float2* sf, int t_base,
+                                                             double2* B, int* status) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* buf0 = smem;
   float2* stg = reinterpret_cast<float2*>(smem + 2 * BUF);  // [XS][NSLOT][13]
@@ -195,9 +225,8 @@ __global__ void __launch_bounds__(NT, 2) k_nucleon_block_tc(int n, long long nsi
   const int ntj = (n + TJ - 1) / TJ;
   const int i0 = (int)(blockIdx.x / ntj) * TI, j0 = (int)(blockIdx.x % ntj) * TJ;
   const int k0 = blockIdx.y * TK;
-  const int t = blockIdx.z;
-  const long long lo = lo0 + (long long)t * t_stride_sites;
-  const float cs = conj ? -1.f : 1.f;
+  const int ts = blockIdx.z;  // slice within this launch's scratch array
+  const int t = t_base + ts;  // slice within the output
 
   const uint32_t bar0 = (uint32_t)__cvta_generic_to_shared(&bars[0]);
   const uint32_t bar1 = (uint32_t)__cvta_generic_to_shared(&bars[1]);
@@ -218,36 +247,38 @@ __global__ void __launch_bounds__(NT, 2) k_nucleon_block_tc(int n, long long nsi
   fence_after();
   const uint32_t tmem = *tmem_holder;
 
-  // staged value e of a chunk: comp = e % 12, site x = (e / 12) % XS, slot = e / (12 XS)
-  double2 pre[NLOAD];
+  // staging loads: thread t moves float4 q = t % 8 (two complex components; q < 6) of site
+  // x = (t / 8) % 4 of slots (t / 32) + 16 r, r < NPRE
+  const int pq = tid & 7, px = (tid >> 3) & 3, pslot0 = tid >> 5;
+  const float4* sf4 = reinterpret_cast<const float4*>(sf);
+  long long gbase[NPRE];  // float4 index of (slot, site 0 of the slice), or -1
+#pragma unroll
+  for (int r = 0; r < NPRE; r++) {
+    const int slot = pslot0 + 16 * r;
+    const int f = slot < TI ? i0 + slot : (slot < TI + TJ ? j0 + slot - TI : k0 + slot - TI - TJ);
+    gbase[r] = (pq < 6 && slot < NSLOT && f < n) ? (((long long)ts * n + f) * S3p + px) * 6 + pq : -1;
+  }
+  float4 pre[NPRE];
   auto prefetch = [&](int x0) {
 #pragma unroll
-    for (int r = 0; r < NLOAD; r++) {
-      const int e = tid + NT * r;
-      pre[r] = make_double2(0.0, 0.0);
-      if (e < XS * NSLOT * 12) {
-        const int comp = e % 12, rest = e / 12;
-        const int x = rest % XS, slot = rest / XS;
-        const int f = slot < TI ? i0 + slot : (slot < TI + TJ ? j0 + slot - TI : k0 + slot - TI - TJ);
-        if (f < n && x0 + x < S3) pre[r] = s[((long long)f * nsite + lo + x0 + x) * 12 + comp];
-      }
-    }
+    for (int r = 0; r < NPRE; r++)
+      pre[r] = gbase[r] >= 0 ? sf4[gbase[r] + (long long)x0 * 6] : make_float4(0.f, 0.f, 0.f, 0.f);
   };
-  const int nchunk = (S3 + XS - 1) / XS;
+  const int nchunk = S3p / XS;
   prefetch(0);
   bool ok = true;
   int issued = -1;  // last chunk whose MMAs were committed
   for (int c = 0; c < nchunk; c++) {
     const int b = c & 1;
     unsigned char* buf = buf0 + b * BUF;
-    // staging <- chunk c (FP64 -> FP32, conjugated for the xi side); then prefetch chunk c + 1
+    // staging <- chunk c; then prefetch chunk c + 1
 #pragma unroll
-    for (int r = 0; r < NLOAD; r++) {
-      const int e = tid + NT * r;
-      if (e < XS * NSLOT * 12) {
-        const int comp = e % 12, rest = e / 12;
-        const int x = rest % XS, slot = rest / XS;
-        stg[(x * NSLOT + slot) * 13 + comp] = make_float2((float)pre[r].x, cs * (float)pre[r].y);
+    for (int r = 0; r < NPRE; r++) {
+      const int slot = pslot0 + 16 * r;
+      if (pq < 6 && slot < NSLOT) {
+        float2* d = &stg[(px * NSLOT + slot) * 13 + 2 * pq];
+        d[0] = make_float2(pre[r].x, pre[r].y);
+        d[1] = make_float2(pre[r].z, pre[r].w);
       }
     }
     if (c + 1 < nchunk) prefetch((c + 1) * XS);
@@ -258,8 +289,8 @@ __global__ void __launch_bounds__(NT, 2) k_nucleon_block_tc(int n, long long nsi
       ok = false;
       break;
     }
-    // A: row m = 16 ii + jj, sites 2h, 2h + 1 (h = tid / 128): K values 12h .. 12h + 11
-    {
+    if (warp < 8) {
+      // A: row m = 16 ii + jj, sites 2h, 2h + 1 (h = tid / 128): K values 12h .. 12h + 11
       const int m = tid & 127, h = tid >> 7;
       const int ii = m >> 4, jj = m & 15;
       float v[12];
@@ -283,26 +314,29 @@ __global__ void __launch_bounds__(NT, 2) k_nucleon_block_tc(int n, long long nsi
         }
       }
 #pragma unroll
-      for (int q = 0; q < 3; q++) put4(buf, 0, m, 3 * h + q, make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
-    }
-    // Bt: rows 2 nc (Re S, -Im S) and 2 nc + 1 (Im S, Re S), nc = 4 kk + alpha; K-block beta
-    // holds the (x, c) pairs 2 beta and 2 beta + 1 (x = pair / 3, c = pair % 3)
+      for (int q = 0; q < 3; q++)
+        put4(buf, 0, MAT_A, m, 3 * h + q, make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
+    } else {
+      // Bt: rows 2 nc (Re S, -Im S) and 2 nc + 1 (Im S, Re S), nc = 4 kk + alpha; K-block
+      // beta holds the (x, c) pairs 2 beta and 2 beta + 1 (x = pair / 3, c = pair % 3)
+      const int u0 = tid - 256;
 #pragma unroll
-    for (int r = 0; r < 3; r++) {
-      const int e = tid + NT * r;
-      const int row = e & 127, beta = e >> 7;
-      const int nc = row >> 1, q = row & 1;
-      const int kk = nc >> 2, al = nc & 3;
-      float vv[4];
+      for (int r = 0; r < 6; r++) {
+        const int e = u0 + 256 * r;
+        const int row = e & 255, beta = e >> 8;
+        const int nc = row >> 1, q = row & 1;
+        const int kk = nc >> 2, al = nc & 3;
+        float vv[4];
 #pragma unroll
-      for (int u = 0; u < 2; u++) {
-        const int pr = 2 * beta + u;
-        const int x = pr / 3, cc = pr % 3;
-        const float2 sv = stg[(x * NSLOT + TI + TJ + kk) * 13 + al * 3 + cc];
-        vv[2 * u] = q ? sv.y : sv.x;
-        vv[2 * u + 1] = q ? sv.x : -sv.y;
+        for (int uu = 0; uu < 2; uu++) {
+          const int pr = 2 * beta + uu;
+          const int x = pr / 3, cc = pr % 3;
+          const float2 sv = stg[(x * NSLOT + TI + TJ + kk) * 13 + al * 3 + cc];
+          vv[2 * uu] = q ? sv.y : sv.x;
+          vv[2 * uu + 1] = q ? sv.x : -sv.y;
+        }
+        put4(buf, 2 * MAT_A, MAT_B, row, beta, make_float4(vv[0], vv[1], vv[2], vv[3]));
       }
-      put4(buf, 2, row, beta, make_float4(vv[0], vv[1], vv[2], vv[3]));
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
@@ -311,8 +345,9 @@ __global__ void __launch_bounds__(NT, 2) k_nucleon_block_tc(int n, long long nsi
       const uint32_t base = (uint32_t)__cvta_generic_to_shared(buf);
 #pragma unroll
       for (int st = 0; st < NSTEP; st++) {
-        const uint64_t ah = smem_desc(base + (st * 4 + 0) * MAT), al = smem_desc(base + (st * 4 + 1) * MAT);
-        const uint64_t bh = smem_desc(base + (st * 4 + 2) * MAT), bl = smem_desc(base + (st * 4 + 3) * MAT);
+        const uint32_t sb = base + st * STEP;
+        const uint64_t ah = smem_desc(sb), al = smem_desc(sb + MAT_A);
+        const uint64_t bh = smem_desc(sb + 2 * MAT_A), bl = smem_desc(sb + 2 * MAT_A + MAT_B);
         const uint32_t acc = (c % GROUP != 0 || st > 0) ? 1u : 0u;
         mma_tf32(tmem, ah, bh, acc);
         mma_tf32(tmem, ah, bl, 1u);
@@ -346,7 +381,7 @@ __global__ void __launch_bounds__(NT, 2) k_nucleon_block_tc(int n, long long nsi
 #pragma unroll 1
     for (int q = 0; q < 4; q++) {
       float v[16];
-      tmem_ld16(tmem + lane_base + (uint32_t)(128 + 64 * (warp >> 2) + 16 * q), v);
+      tmem_ld16(tmem + lane_base + (uint32_t)(256 + 64 * (warp >> 2) + 16 * q), v);
       if (i < n && j < n) {
 #pragma unroll
         for (int e = 0; e < 8; e++) {
@@ -392,21 +427,34 @@ int lq_nucleon_blocks_tc(int n, long long nsite, const double2* s, int conj, int
       opted.push_back(dev);
     }
   }
+  // FP32 scratch of the fields on a group of slices (at most about 2 GB)
+  const int S3p = (S3 + XS - 1) / XS * XS;
+  const long long slice_words = (long long)n * S3p * 12;  // float2 per slice
+  const int g = (int)std::max(1LL, std::min((long long)n_t, (2LL << 30) / (slice_words * 8)));
   int* status = nullptr;
-  if (cudaMallocAsync(&status, sizeof(int), st) != cudaSuccess) {
+  float2* sf = nullptr;
+  if (cudaMallocAsync(&status, sizeof(int), st) != cudaSuccess ||
+      cudaMallocAsync(&sf, sizeof(float2) * slice_words * g, st) != cudaSuccess) {
     cudaGetLastError();
+    if (status) cudaFreeAsync(status, st);
     lq_set_error("nucleon_blocks: device allocation failed");
     return LQCD_ENOMEM;
   }
   cudaMemsetAsync(status, 0, sizeof(int), st);
   const int nti = (n + TI - 1) / TI, ntj = (n + TJ - 1) / TJ, ntk = (n + TK - 1) / TK;
-  k_nucleon_block_tc<<<dim3((unsigned)(nti * ntj), (unsigned)ntk, (unsigned)n_t), NT, SMEM, st>>>(
-      n, nsite, s, conj, S3, lo0, S3, B, status);
-  lq_count_launch();
+  for (int t0 = 0; t0 < n_t; t0 += g) {
+    const int nts = std::min(g, n_t - t0);
+    k_slices_f32<<<152 * 8, 256, 0, st>>>(n, nsite, s, conj, S3, S3p, lo0 + (long long)t0 * S3, nts, sf);
+    lq_count_launch();
+    k_nucleon_block_tc<<<dim3((unsigned)(nti * ntj), (unsigned)ntk, (unsigned)nts), NT, SMEM, st>>>(n, S3p, sf, t0,
+                                                                                                   B, status);
+    lq_count_launch();
+  }
   cudaError_t e = cudaGetLastError();
   int h_status = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFreeAsync(sf, st);
   cudaFreeAsync(status, st);
   if (e != cudaSuccess) {
     lq_set_error(std::string("nucleon_blocks (tensor cores): ") + cudaGetErrorString(e));
