@@ -380,11 +380,11 @@ __global__ void k_nucleon_point_sum(int nblk, int n_t, int n_prop, const double2
   W[2 * i + 1] = r2;
 }
 
-// LQCD_NUCLEON_TC=0 selects the FP32-FMA block kernel, 1 the tensor-core one (nucleon_tc.cu);
-// read at every call
+// The tensor-core block kernel (nucleon_tc.cu) unless LQCD_NUCLEON_TC=0 selects the FP32-FMA
+// one; read at every call
 bool use_tensor_cores() {
   const char* e = getenv("LQCD_NUCLEON_TC");
-  return e ? atoi(e) != 0 : false;
+  return e ? atoi(e) != 0 : true;
 }
 
 }  // namespace
