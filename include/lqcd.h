@@ -427,10 +427,9 @@ int lqcd_fma_peak(int bits, double *tflops, void *stream);
  * The first call on a device looks up the array's device address (with that
  * device current) and caches it.  All calls share the one array and it
  * keeps the last call's contents (every word a call reads is written by
- * that call first): calls
- * that overlap on the GPU -- on different streams or host threads without
- * ordering between them -- race and must not be issued.  Stream-ordered; does
- * not synchronise.  Errors: LQCD_EBADARG, LQCD_ENOFIELD, LQCD_ECUDA. */
+ * that call first): calls that overlap on the GPU -- on different streams
+ * or host threads without ordering between them -- race and must not be
+ * issued.  Stream-ordered; does not synchronise.  Errors: LQCD_EBADARG, LQCD_ENOFIELD, LQCD_ECUDA. */
 int lqcd_dslash_noalloc(lqcd_lattice *lat, int field, const lqcd_slab *dom, int dagger, const double *in, double *out,
                         void *stream);
 
