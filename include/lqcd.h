@@ -90,7 +90,8 @@ typedef struct {
   int precision;         /* 64: FP64 throughout; 32: FP32 inner solves with FP64
                             defect correction; 16: FP16 vectors (per-site FP32 norm)
                             and FP16 links in the inner solves, FP64 correction      */
-  double inner_tol;      /* relative residual reduction per inner cycle (0: default) */
+  double inner_tol;      /* relative residual reduction per inner cycle (0: default,
+                            3e-6 for FP32, 2e-2 for FP16) */
   int check_every;       /* iterations between host convergence checks (0: default) */
   int max_wave;          /* systems solved together at most (0: as many as fit in free
                             device memory; larger batches run in consecutive waves)  */
