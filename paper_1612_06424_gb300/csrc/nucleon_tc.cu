@@ -63,7 +63,11 @@ constexpr int MAT_A = 4096;                   // bytes of the 128-row x 8 operan
 constexpr int MAT_B = 8192;                   // bytes of the 256-row x 8 operand Bt of one step
 constexpr int STEP = 2 * MAT_A + 2 * MAT_B;   // one K-step: A hi, A lo, Bt hi, Bt lo
 constexpr int BUF = NSTEP * STEP;             // one chunk
-constexpr int STG = XS * NSLOT * 13 * 8;      // FP32 staging: [site][slot][13 float2]
+// FP32 staging per site: the 24 (i, j) spinors at a stride of 13 float2 (the 16 j of a warp's A rows
+// on distinct banks), then the 32 k spinors at a stride of 12 (16-byte aligned; the (k, alpha) reads
+// of a warp's Bt rows on distinct banks)
+constexpr int SITE_STG = (TI + TJ) * 13 + TK * 12;  // float2 per site
+constexpr int STG = XS * SITE_STG * 8;
 constexpr int SMEM = 2 * BUF + STG + 64;      // + 2 mbarriers, the TMEM address and a flag
 constexpr int TMEM_COLS = 512;                // inner accumulator (0..255) + running sums (256..511)
 constexpr int NPRE = 4;                       // 16-byte staging loads per thread and chunk
@@ -216,7 +220,7 @@ __global__ void __launch_bounds__(NT, 1) k_nucleon_block_tc(int n, int S3p, cons
                                                              double2* B, int* status) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* buf0 = smem;
-  float2* stg = reinterpret_cast<float2*>(smem + 2 * BUF);  // [XS][NSLOT][13]
+  float2* stg = reinterpret_cast<float2*>(smem + 2 * BUF);  // [XS][SITE_STG]
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * BUF + STG);
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(smem + 2 * BUF + STG + 16);
   int* fail = reinterpret_cast<int*>(smem + 2 * BUF + STG + 20);
@@ -276,9 +280,13 @@ __global__ void __launch_bounds__(NT, 1) k_nucleon_block_tc(int n, int S3p, cons
     for (int r = 0; r < NPRE; r++) {
       const int slot = pslot0 + 16 * r;
       if (pq < 6 && slot < NSLOT) {
-        float2* d = &stg[(px * NSLOT + slot) * 13 + 2 * pq];
-        d[0] = make_float2(pre[r].x, pre[r].y);
-        d[1] = make_float2(pre[r].z, pre[r].w);
+        if (slot < TI + TJ) {
+          float2* d = &stg[px * SITE_STG + slot * 13 + 2 * pq];
+          d[0] = make_float2(pre[r].x, pre[r].y);
+          d[1] = make_float2(pre[r].z, pre[r].w);
+        } else {
+          *reinterpret_cast<float4*>(&stg[px * SITE_STG + (TI + TJ) * 13 + (slot - TI - TJ) * 12 + 2 * pq]) = pre[r];
+        }
       }
     }
     if (c + 1 < nchunk) prefetch((c + 1) * XS);
@@ -297,8 +305,8 @@ __global__ void __launch_bounds__(NT, 1) k_nucleon_block_tc(int n, int S3p, cons
 #pragma unroll
       for (int q = 0; q < 2; q++) {
         const int x = 2 * h + q;
-        const float2* u = &stg[(x * NSLOT + ii) * 13];
-        const float2* w = &stg[(x * NSLOT + TI + jj) * 13];
+        const float2* u = &stg[x * SITE_STG + ii * 13];
+        const float2* w = &stg[x * SITE_STG + (TI + jj) * 13];
         float2 uu[12], ww[12];
 #pragma unroll
         for (int e = 0; e < 12; e++) {
@@ -331,7 +339,7 @@ __global__ void __launch_bounds__(NT, 1) k_nucleon_block_tc(int n, int S3p, cons
         for (int uu = 0; uu < 2; uu++) {
           const int pr = 2 * beta + uu;
           const int x = pr / 3, cc = pr % 3;
-          const float2 sv = stg[(x * NSLOT + TI + TJ + kk) * 13 + al * 3 + cc];
+          const float2 sv = stg[x * SITE_STG + (TI + TJ) * 13 + kk * 12 + al * 3 + cc];
           vv[2 * uu] = q ? sv.y : sv.x;
           vv[2 * uu + 1] = q ? sv.x : -sv.y;
         }
