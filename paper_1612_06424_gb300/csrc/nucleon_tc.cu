@@ -63,10 +63,11 @@ constexpr int MAT_A = 4096;                   // bytes of the 128-row x 8 operan
 constexpr int MAT_B = 8192;                   // bytes of the 256-row x 8 operand Bt of one step
 constexpr int STEP = 2 * MAT_A + 2 * MAT_B;   // one K-step: A hi, A lo, Bt hi, Bt lo
 constexpr int BUF = NSTEP * STEP;             // one chunk
-// FP32 staging per site: the 24 (i, j) spinors at a stride of 13 float2 (the 16 j of a warp's A rows
-// on distinct banks), then the 32 k spinors at a stride of 12 (16-byte aligned; the (k, alpha) reads
-// of a warp's Bt rows on distinct banks)
-constexpr int SITE_STG = (TI + TJ) * 13 + TK * 12;  // float2 per site
+// FP32 staging per site: the 24 (i, j) spinors at a stride of 14 float2 (16-byte aligned; the
+// 16-byte reads of 8 consecutive j by a quarter warp's A rows on distinct banks), then the 32 k
+// spinors at a stride of 12 (16-byte aligned; the (k, alpha) reads of a warp's Bt rows on distinct
+// banks)
+constexpr int SITE_STG = (TI + TJ) * 14 + TK * 12;  // float2 per site
 constexpr int STG = XS * SITE_STG * 8;
 constexpr int SMEM = 2 * BUF + STG + 64;      // + 2 mbarriers, the TMEM address and a flag
 constexpr int TMEM_COLS = 512;                // inner accumulator (0..255) + running sums (256..511)
@@ -280,13 +281,8 @@ __global__ void __launch_bounds__(NT, 1) k_nucleon_block_tc(int n, int S3p, cons
     for (int r = 0; r < NPRE; r++) {
       const int slot = pslot0 + 16 * r;
       if (pq < 6 && slot < NSLOT) {
-        if (slot < TI + TJ) {
-          float2* d = &stg[px * SITE_STG + slot * 13 + 2 * pq];
-          d[0] = make_float2(pre[r].x, pre[r].y);
-          d[1] = make_float2(pre[r].z, pre[r].w);
-        } else {
-          *reinterpret_cast<float4*>(&stg[px * SITE_STG + (TI + TJ) * 13 + (slot - TI - TJ) * 12 + 2 * pq]) = pre[r];
-        }
+        const int off = slot < TI + TJ ? slot * 14 : (TI + TJ) * 14 + (slot - TI - TJ) * 12;
+        *reinterpret_cast<float4*>(&stg[px * SITE_STG + off + 2 * pq]) = pre[r];
       }
     }
     if (c + 1 < nchunk) prefetch((c + 1) * XS);
@@ -305,13 +301,16 @@ __global__ void __launch_bounds__(NT, 1) k_nucleon_block_tc(int n, int S3p, cons
 #pragma unroll
       for (int q = 0; q < 2; q++) {
         const int x = 2 * h + q;
-        const float2* u = &stg[x * SITE_STG + ii * 13];
-        const float2* w = &stg[x * SITE_STG + (TI + jj) * 13];
+        const float4* u = reinterpret_cast<const float4*>(&stg[x * SITE_STG + ii * 14]);
+        const float4* w = reinterpret_cast<const float4*>(&stg[x * SITE_STG + (TI + jj) * 14]);
         float2 uu[12], ww[12];
 #pragma unroll
-        for (int e = 0; e < 12; e++) {
-          uu[e] = u[e];
-          ww[e] = w[e];
+        for (int e = 0; e < 6; e++) {
+          const float4 a4 = u[e], b4 = w[e];
+          uu[2 * e] = make_float2(a4.x, a4.y);
+          uu[2 * e + 1] = make_float2(a4.z, a4.w);
+          ww[2 * e] = make_float2(b4.x, b4.y);
+          ww[2 * e + 1] = make_float2(b4.z, b4.w);
         }
 #pragma unroll
         for (int cc = 0; cc < 3; cc++) {
@@ -339,7 +338,7 @@ __global__ void __launch_bounds__(NT, 1) k_nucleon_block_tc(int n, int S3p, cons
         for (int uu = 0; uu < 2; uu++) {
           const int pr = 2 * beta + uu;
           const int x = pr / 3, cc = pr % 3;
-          const float2 sv = stg[x * SITE_STG + (TI + TJ) * 13 + kk * 12 + al * 3 + cc];
+          const float2 sv = stg[x * SITE_STG + (TI + TJ) * 14 + kk * 12 + al * 3 + cc];
           vv[2 * uu] = q ? sv.y : sv.x;
           vv[2 * uu + 1] = q ? sv.x : -sv.y;
         }
