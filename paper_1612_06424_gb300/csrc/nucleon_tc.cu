@@ -20,8 +20,8 @@
 // region; the result is written in FP64.
 //
 // The fields of the requested slices are first converted once to FP32 (conjugated for the xi
-// side) by k_slices_f32, slice by slice into a scratch array [slice][field][site][12] whose
-// sites are padded to a multiple of 4 with zeros.
+// side) by k_slices_f32, a group of slices at a time (at most about 2 GB of scratch), into an
+// array [slice][field][site][12] whose sites are padded to a multiple of 4 with zeros.
 //
 // One CTA per SM (512 threads, 16 warps): 128 rows (i, j) = 8 i x 16 j of one slice and 128
 // complex columns (32 k x 4 alpha) = 256 real columns, so the accumulator fills the 512 TMEM
