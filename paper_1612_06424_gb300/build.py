@@ -22,7 +22,7 @@ LIB = os.path.join(OUT_DIR, "liblqcd.so")
 EXTRA = os.environ.get("LQCD_NVCC_FLAGS", "").split()
 SOURCES = ["api.cu", "kernels.cu", "hop_tuned32.cu", "hop_tuned16.cu", "gauge.cu", "force.cu", "disconnected.cu",
            "projection.cu", "nucleon.cu", "nucleon_tc.cu", "noalloc.cu", "peak.cu"]
-HEADERS = ["common.cuh", "dslash.cuh", "blas.cuh", "hop_tuned.cuh", "internal.h"]
+HEADERS = ["common.cuh", "dslash.cuh", "blas.cuh", "hop_tuned.cuh", "internal.h", "tc_layout.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-Xptxas", "-O3", "--expt-relaxed-constexpr"]

@@ -48,12 +48,13 @@
 #include <vector>
 
 #include "internal.h"
+#include "tc_layout.cuh"
 
 using namespace lq;
 
 namespace {
 
-constexpr int TI = 8, TJ = 16, TK = 32;  // tile: 8 x 16 (i, j) rows, 32 k (128 complex columns)
+constexpr int TI = TC_TI, TJ = TC_TJ, TK = TC_TK;  // tile: 8 x 16 (i, j) rows, 32 k (128 complex columns)
 constexpr int NSLOT = TI + TJ + TK;      // spinors per site of a tile
 constexpr int XS = 4;                    // sites per chunk
 constexpr int NSTEP = XS * 6 / 8;        // MMA K-steps per chunk (K = 8 TF32 per step)
@@ -63,11 +64,11 @@ constexpr int MAT_A = 4096;                   // bytes of the 128-row x 8 operan
 constexpr int MAT_B = 8192;                   // bytes of the 256-row x 8 operand Bt of one step
 constexpr int STEP = 2 * MAT_A + 2 * MAT_B;   // one K-step: A hi, A lo, Bt hi, Bt lo
 constexpr int BUF = NSTEP * STEP;             // one chunk
-// FP32 staging per site: the 24 (i, j) spinors at a stride of 14 float2 (16-byte aligned; the
-// 16-byte reads of 8 consecutive j by a quarter warp's A rows on distinct banks), then the 32 k
-// spinors at a stride of 12 (16-byte aligned; the (k, alpha) reads of a warp's Bt rows on distinct
-// banks)
-constexpr int SITE_STG = (TI + TJ) * 14 + TK * 12;  // float2 per site
+// FP32 staging per site (tc_stage_index): the 24 (i, j) spinors at a stride of 14 float2
+// (16-byte aligned; the 16-byte reads of 8 consecutive j by a quarter warp's A rows on distinct
+// banks), then the 32 k spinors at a stride of 12 (16-byte aligned; the (k, alpha) reads of a
+// warp's Bt rows on distinct banks)
+constexpr int SITE_STG = TC_SITE_STG;  // float2 per site
 constexpr int STG = XS * SITE_STG * 8;
 constexpr int SMEM = 2 * BUF + STG + 64;      // + 2 mbarriers, the TMEM address and a flag
 constexpr int TMEM_COLS = 512;                // inner accumulator (0..255) + running sums (256..511)
@@ -80,7 +81,7 @@ constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((256u >> 3) << 
 LQ_DI uint64_t smem_desc(uint32_t addr) {
   // start address >> 4 (bits 0-13), leading byte offset 128 >> 4 (16-29), stride byte offset
   // 256 >> 4 (32-45), descriptor version 1 (bit 46), base offset 0, no swizzle (61-63 = 0)
-  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(256 >> 4) << 32) |
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(TC_LBO >> 4) << 16) | ((uint64_t)(TC_SBO >> 4) << 32) |
          (1ull << 46);
 }
 
@@ -171,8 +172,7 @@ LQ_DI void put4(unsigned char* buf, int hi_off, int mat, int r, int beta, float4
   split_tf32(v.y, h.y, l.y);
   split_tf32(v.z, h.z, l.z);
   split_tf32(v.w, h.w, l.w);
-  const int kc = beta & 1;
-  const int off = (beta >> 1) * STEP + hi_off + ((r >> 3) * 2 + kc) * 128 + (r & 7) * 16;
+  const int off = (beta >> 1) * STEP + hi_off + tc_operand_offset(r, 4 * (beta & 1));
   *reinterpret_cast<float4*>(buf + off) = h;
   *reinterpret_cast<float4*>(buf + off + mat) = l;
 }
@@ -281,8 +281,7 @@ __global__ void __launch_bounds__(NT, 1) k_nucleon_block_tc(int n, int S3p, cons
     for (int r = 0; r < NPRE; r++) {
       const int slot = pslot0 + 16 * r;
       if (pq < 6 && slot < NSLOT) {
-        const int off = slot < TI + TJ ? slot * 14 : (TI + TJ) * 14 + (slot - TI - TJ) * 12;
-        *reinterpret_cast<float4*>(&stg[px * SITE_STG + off + 2 * pq]) = pre[r];
+        *reinterpret_cast<float4*>(&stg[tc_stage_index(px, slot, 2 * pq)]) = pre[r];
       }
     }
     if (c + 1 < nchunk) prefetch((c + 1) * XS);
@@ -301,8 +300,8 @@ __global__ void __launch_bounds__(NT, 1) k_nucleon_block_tc(int n, int S3p, cons
 #pragma unroll
       for (int q = 0; q < 2; q++) {
         const int x = 2 * h + q;
-        const float4* u = reinterpret_cast<const float4*>(&stg[x * SITE_STG + ii * 14]);
-        const float4* w = reinterpret_cast<const float4*>(&stg[x * SITE_STG + (TI + jj) * 14]);
+        const float4* u = reinterpret_cast<const float4*>(&stg[tc_stage_index(x, ii, 0)]);
+        const float4* w = reinterpret_cast<const float4*>(&stg[tc_stage_index(x, TI + jj, 0)]);
         float2 uu[12], ww[12];
 #pragma unroll
         for (int e = 0; e < 6; e++) {
@@ -338,7 +337,7 @@ __global__ void __launch_bounds__(NT, 1) k_nucleon_block_tc(int n, int S3p, cons
         for (int uu = 0; uu < 2; uu++) {
           const int pr = 2 * beta + uu;
           const int x = pr / 3, cc = pr % 3;
-          const float2 sv = stg[x * SITE_STG + (TI + TJ) * 14 + kk * 12 + al * 3 + cc];
+          const float2 sv = stg[tc_stage_index(x, TI + TJ + kk, al * 3 + cc)];
           vv[2 * uu] = q ? sv.y : sv.x;
           vv[2 * uu + 1] = q ? sv.x : -sv.y;
         }
