@@ -312,12 +312,21 @@ int lqcd_projected_propagator(lqcd_lattice *lat, const lqcd_split *split, int n_
  * time slices t0 .. t0+n_t-1 (inside the slab):
  *   B[t][i][j][k][alpha] = sum_{xvec} eps^{abc} {[s_i^T]^a(x) C g5 [s_j]^b(x)} [s_k]^c_alpha(x)
  * with C = g0 g2 (C g_mu C^{-1} = -g_mu^T in the basis above).  B: device
- * [n_t][n][n][n][4] complex128, overwritten.  Arithmetic: the diquark and the
- * (x, c) contraction in FP32 (inputs rounded from FP64), summed in two
- * levels (partial sums over 64 sites, then their running sum; relative error
- * about (200 + L1 L2 L3 / 64) 2^-24 of the sum of |terms|), stored as FP64.
- * 1 <= n <= 1024.  Stream-ordered, no
- * synchronisation.  Errors: LQCD_EBADARG, LQCD_ECUDA. */
+ * [n_t][n][n][n][4] complex128, overwritten.  Arithmetic (default, the tensor
+ * cores): the inputs rounded to FP32 once, the diquark in FP32, the (x, c)
+ * contraction as a real GEMM on tcgen05 in three TF32 passes (hi*hi + hi*lo +
+ * lo*hi of each operand's split into an 11-bit head and an FP32 remainder),
+ * accumulated in FP32 per 64 sites and then in FP32 running sums; relative
+ * error at most about (16 + 288 + L1 L2 L3 / 64) 2^-24 of the sum of |terms|;
+ * stored as FP64.  Scratch: one FP32 copy of the fields on up to about 2 GB
+ * worth of slices at a time (stream-ordered allocation).  The call waits for
+ * its kernels (it reads back the status of their bounded waits on the tensor
+ * pipeline).  With the environment variable LQCD_NUCLEON_TC=0: the FP32-FMA
+ * kernel (partial sums over 64 sites, then their running sum; relative error
+ * about (200 + L1 L2 L3 / 64) 2^-24 of the sum of |terms|), stream-ordered,
+ * no synchronisation.  1 <= n <= 1024.
+ * Errors: LQCD_EBADARG, LQCD_ENOMEM, LQCD_ECUDA (also when a tensor-core
+ * wait timed out). */
 int lqcd_nucleon_blocks(lqcd_lattice *lat, const lqcd_slab *slab, int n, const double *s, int conj, int t0, int n_t,
                         double *B, void *stream);
 
