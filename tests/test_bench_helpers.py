@@ -78,3 +78,15 @@ def test_clock_summary_without_samples():
     s = c.summary()
     os.unlink(c.f.name)
     assert s["reasons"] == ["unsampled"] and s["sm_mhz"] is None
+
+
+def test_nucleon_roofline_counts_three_tf32_passes(fake_root):
+    """The tensor-core block contraction is reported against the TF32 peak derived from the
+    measured bf16 peak (x 1.1 / 2.25), with three TF32 passes per contraction flop."""
+    (fake_root / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6000.0, "bf16_tflops": 2250.0}))
+    r = bench._nucleon_roofline(1.0e14, 1.0, 77.0, 120, 41, 13824)
+    assert r["bound"] == "tensor" and r["peak"] == pytest.approx(1100.0)
+    assert r["contraction_tflops"] == pytest.approx(100.0)
+    assert r["achieved"] == pytest.approx(300.0) and r["frac"] == pytest.approx(300.0 / 1100.0, rel=1e-3)
+    (fake_root / "MEASURED_PEAKS.json").unlink()
+    assert bench._tf32_peak()[1].startswith("fallback")
