@@ -3,6 +3,10 @@
 - C = gamma_0 gamma_2 is a charge-conjugation matrix of this basis: C gamma_mu C^{-1} = -gamma_mu^T;
 - the block B is the eps/C-gamma_5 contraction written out site by site and index by index in plain
   loops on a tiny case;
+- symmetries that the block's definition fixes, independent of how it is written: invariance under a
+  colour rotation s(x) -> g(x) s(x) with g(x) in SU(3) (eps^{abc} g g g = det g eps), symmetry
+  under i <-> j (eps and C g5 are both antisymmetric), and covariance under spin rotations
+  s -> R s with R^T C g5 R = C g5 (R = exp(theta [g_mu, g_nu] / 4)): B -> R B in its spinor index;
 - the factorized W1, W2 equal the propagator form of the two nucleon Wick contractions evaluated with
   the projected propagator S(y,x)[a,b] = -sum_i eta_i(y)[a] xi_i^T(x)[b] for every pair (x, y) of
   the two slices (substituting S into the contraction gives the block form, so any index slip in the
@@ -135,3 +139,49 @@ def test_multilevel_estimator_special_cases():
     want = np.mean([np.mean([A[i, j] @ Bm[i, k] for j in range(n1) for k in range(n1)], axis=0)
                     for i in range(n0)], axis=0)
     assert np.abs(got - want).max() < 1e-13
+
+
+def _fields(n, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((n, 4 * S3, 4, 3)) + 1j * rng.standard_normal((n, 4 * S3, 4, 3))
+
+
+def test_block_is_colour_gauge_invariant():
+    """B(t) is a colour singlet: rotating the colour of every field at each site by the same SU(3)
+    matrix g(x) (a different one per site) leaves it unchanged."""
+    op = _op()
+    s = _fields(3, 5)
+    g = inputs.random_su3_field(DIMS, 0.9, 77)[:, 0]                  # one SU(3) matrix per site
+    sg = np.einsum("xab,ixsb->ixsa", g, s)
+    for t in range(DIMS[0]):
+        B, Bg = oracle.nucleon_block(op, s, t), oracle.nucleon_block(op, sg, t)
+        assert np.abs(Bg - B).max() < 1e-12 * np.abs(B).max()
+    # a colour rotation that is not in SU(3) (det = e^{i phi}) multiplies B by det g
+    ph = np.exp(0.7j)
+    assert np.abs(oracle.nucleon_block(op, ph ** (1 / 3) * s, 1) - ph * oracle.nucleon_block(op, s, 1)).max() \
+        < 1e-12 * np.abs(oracle.nucleon_block(op, s, 1)).max()
+
+
+def test_block_is_symmetric_in_the_diquark_pair():
+    op = _op()
+    s = _fields(4, 6)
+    for t in (0, 3):
+        B = oracle.nucleon_block(op, s, t)
+        assert np.abs(B - B.transpose(1, 0, 2, 3)).max() < 1e-12 * np.abs(B).max()
+        assert np.abs(B - B.transpose(2, 1, 0, 3)).max() > 1e-3 * np.abs(B).max()   # not symmetric in (i, k)
+
+
+def test_block_is_covariant_under_spin_rotations():
+    from scipy.linalg import expm
+
+    op = _op()
+    s = _fields(3, 7)
+    cg5 = oracle.charge_conjugation() @ oracle.gamma(4)
+    for mu, nu, th in ((0, 1, 0.4), (1, 2, 1.1), (2, 3, -0.8)):
+        G = oracle.gamma(mu) @ oracle.gamma(nu) - oracle.gamma(nu) @ oracle.gamma(mu)
+        R = expm(0.25 * th * G)
+        assert np.abs(R.T @ cg5 @ R - cg5).max() < 1e-13                 # R preserves the diquark form
+        sr = np.einsum("st,ixtc->ixsc", R, s)
+        B, Br = oracle.nucleon_block(op, s, 2), oracle.nucleon_block(op, sr, 2)
+        assert np.abs(Br - np.einsum("st,ijkt->ijks", R, B)).max() < 1e-12 * np.abs(B).max()
+
