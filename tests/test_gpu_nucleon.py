@@ -9,7 +9,8 @@ i.e. 1.2e-5 * bound here and 2.4e-5 * bound for a 24^3 slice.  The tensor-core k
 sums 64 sites per TMEM accumulation with one rounding of the partial sum per MMA (3 passes per 8 real
 K values: 144 per 64 sites, at most 2 u32 each if the tensor core truncates) and takes TF32 hi/lo
 splits that lose at most 2^-21 per product (16 u32), so its bound, (16 + 2 * 144 + S3/64) u32, is
-1.8e-5 * bound here and 2.6e-5 * bound for a 24^3 slice, below the same tolerance; with
+1.8e-5 * bound here (below the same tolerance) and 3.1e-5 * bound for a 24^3 slice (the full-size
+test in tests/test_gpu_fullsize.py allows 3.5e-5 there); with
 bound = sum_{x,c} sum_{ab} |eps| sum_{mn} |s_i| |C g5| |s_j| |s_k| computed here from |s|;
 the test allows 3e-5 * bound.  Because |B| is of order bound / sqrt(#terms), a wrong index or sign
 moves B by far more than that.  The contraction kernel is FP64: 1e-12 on identical blocks.
