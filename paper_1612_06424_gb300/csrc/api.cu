@@ -57,7 +57,7 @@ struct DBuf {
     if (e == cudaErrorMemoryAllocation) {
       // The pool keeps the blocks of earlier waves mapped; when they are too
       // small for this request they only block it.  Wait for every pending
-      // free, hand the pool's unused memory back to the driver and retry.
+      // free, hand the pool's unused memory back to the CUDA driver and retry.
       cudaGetLastError();
       int dev = 0;
       cudaMemPool_t pool;
